@@ -1,0 +1,289 @@
+#!/usr/bin/env python
+"""Throughput of the block recursive inverse (blocks of M^-1 per second).
+
+Workload (default): n = 4096, k = 8 (b = 512), M = uniform[-1, 1) + n I
+(seed 0), every block N_ij computed one at a time; a step is
+``--blocks-per-step`` consecutive blocks in row-major order (cycling through
+all k^2 blocks over the steps).  M (134 MB FP64) is larger than L2 (129 MB)
+and L2 is also flushed between timed steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain FP64 restatement of the paper's recursion) on the host cores on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "inverse blocks/sec & GEMM % of tensor peak, mixed vs FP64 at ≤1e-10 rel err"
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    p.add_argument("--n", type=int, default=4096)
+    p.add_argument("--k", type=int, default=8)
+    p.add_argument("--blocks-per-step", type=int, default=8)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-blocks", type=int, default=1)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def block_list(k, start, count):
+    return [((start + t) % (k * k) // k, (start + t) % (k * k) % k) for t in range(count)]
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_time(m, k, blocks):
+    """Seconds per block of the oracle (memoized recursion, all host cores)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for (i, j) in blocks:
+        _, st, _ = oracle.bri_block(m, k, i, j, memo=True)
+        assert st == oracle.OK
+    return (time.perf_counter() - t0) / len(blocks), oracle.num_threads()
+
+
+def run_reference(args, rank):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import bri_inputs as bi
+    m = bi.uniform_shift(args.n, 0)
+    k = args.k
+    seq = block_list(k, 0, args.warmup + args.steps)
+    for t in range(args.warmup):
+        cpu_oracle_time(m, k, [seq[t]])
+    per = []
+    for t in range(args.steps):
+        s, cores = cpu_oracle_time(m, k, [seq[args.warmup + t]])
+        per.append(s)
+    secs = sum(per)
+    value = args.steps / secs
+    sample = f"{args.steps} blocks of the n={args.n}, k={k} uniform+nI matrix, one per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"n={args.n} k={k} b={args.n // k} uniform[-1,1)+nI FP64, one block per step",
+                       "blocks_per_step": 1, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import bri_inputs as bi
+    import paper_1612_00001_gb300 as mb
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mb.build()
+    n, k = args.n, args.k
+    b = -(-n // k)
+    bps = args.blocks_per_step
+    m_host = bi.uniform_shift(n, 0)
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    M = torch.tensor(m_host, dtype=dt, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = mb.Context(M, k, precision=args.precision, profile=True)
+    outs = [torch.empty((b, b), dtype=dt, device="cuda") for _ in range(bps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # each rank takes its own slice of the block sequence (replicas, no collective)
+    base = rank * bps
+
+    def step(s, c=ctx, dst=outs):
+        reps = []
+        for q, (i, j) in enumerate(block_list(k, base + s * bps * world, bps)):
+            c.block(i, j, out=dst[q])
+            reps.append(c.last_report)
+        return reps
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    agg = {"gemm_flops": 0.0, "inv_flops": 0.0, "gemm_device_seconds": 0.0, "inv_device_seconds": 0.0,
+           "launches": 0, "gemm_launches": 0, "inversions": 0, "peak_device_bytes": 0}
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)  # L2 flush, outside the timed interval
+        ev[s][0].record(stream)
+        reps = step(args.warmup + s)
+        ev[s][1].record(stream)
+        for r in reps:
+            for key in agg:
+                agg[key] = max(agg[key], r[key]) if key == "peak_device_bytes" else agg[key] + r[key]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
+    if dist:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    total_blocks = bps * args.steps * world
+    value = total_blocks / secs
+
+    # accuracy of the last step's blocks against a dense LAPACK-style inverse
+    inv_ref = torch.linalg.inv(torch.tensor(m_host, dtype=torch.float64, device="cuda"))
+    errs = []
+    for q, (i, j) in enumerate(block_list(k, base + (args.warmup + args.steps - 1) * bps * world, bps)):
+        r = inv_ref[i * b:(i + 1) * b, j * b:(j + 1) * b]
+        errs.append(float(torch.linalg.norm(outs[q].double() - r) / torch.linalg.norm(r)))
+    del inv_ref
+
+    # roofline of the dominant kernel family
+    pk, pk_src = peaks()
+    if agg["gemm_device_seconds"] >= agg["inv_device_seconds"]:
+        kern, flops, dsec, nl = "gemm_grouped (Schur products)", agg["gemm_flops"], agg["gemm_device_seconds"], \
+            agg["gemm_launches"]
+    else:
+        kern, flops, dsec, nl = "gauss-jordan inverse batches", agg["inv_flops"], agg["inv_device_seconds"], \
+            agg["inversions"]
+    achieved = flops / dsec / 1e12 if dsec > 0 else 0.0
+    if args.precision == "fp64":
+        peak, bound, unit, psrc = FP64_NOMINAL_GFLOPS / 1e3, "alu", "TFLOP/s", "nominal FP64 1.25 TFLOP/s"
+    elif args.precision == "fp32":
+        peak, bound, unit, psrc = FP32_NOMINAL_GFLOPS / 1e3, "alu", "TFLOP/s", \
+            "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+    else:
+        peak, bound, unit, psrc = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s", \
+            f"bf16_tflops_sustained ({pk_src})"
+    roofline = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak if peak else None, "traffic": None, "peak_source": psrc,
+                "launches": nl, "device_seconds": dsec,
+                "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12}
+
+    line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3/f32"}[
+                args.precision], "data": "synthetic",
+            "config": {"workload": f"n={n} k={k} b={b} uniform[-1,1)+nI, blocks one at a time ({args.precision})",
+                       "blocks_per_step": bps, "precision": args.precision,
+                       "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",
+                       "max_rel_err_vs_dense_inverse": max(errs)},
+            "roofline": roofline, "gpu_launches": agg["launches"],
+            "peak_device_bytes": agg["peak_device_bytes"], "clocks": clk}
+    ctx.close()
+
+    # end to end through the C ABI with host buffers (H2D of M and D2H of the blocks timed)
+    if not args.no_e2e and rank == 0:
+        mh = torch.tensor(m_host, dtype=dt).pin_memory()
+        houts = [torch.empty((b, b), dtype=dt).pin_memory() for _ in range(bps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 2))
+        for s in range(e2e_steps):
+            with mb.Context(mh, k, precision=args.precision) as hc:
+                for q, (i, j) in enumerate(block_list(k, s * bps, bps)):
+                    hc.block(i, j, out=houts[q])
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        es = dt.itemsize if hasattr(dt, "itemsize") else (8 if dt == torch.float64 else 4)
+        line["e2e"] = {"value": e2e_steps * bps / te, "unit": "blocks/s", "h2d_bytes_per_step": n * n * es,
+                       "d2h_bytes_per_step": bps * b * b * es, "steps": e2e_steps}
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        secs_cpu, cores = cpu_oracle_time(m_host, k, block_list(k, 0, args.cpu_sample_blocks))
+        line["cpu_baseline"] = {"value": 1.0 / secs_cpu, "unit": "blocks/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_sample_blocks} block(s) from (0,0) of the same matrix, "
+                                          "memoized recursion, FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * mbinv - memory-bounded block recursive inverse on one GB300 (sm_103a).
+ *
+ * Block Recursive Inversion (BRI) of Cosme, Fernandes, de Carvalho and
+ * Xavier-de-Souza, "Memory-Usage Advantageous Block Recursive Matrix Inverse"
+ * (arXiv:1612.00001).  For an n x n matrix M viewed as a k x k grid of b x b
+ * blocks (b = n / k, Sec. 2 Eq. blockmatricesnxn), the library returns one
+ * block N_ij of M^-1 at a time (Sec. 3, Eq. blockmatrix_NxN), all k^2 blocks
+ * by k^2 independent runs (Sec. 5), or many independent problems at once.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major with an explicit leading dimension in elements.
+ *   - Block indices are 0-based; the paper counts from 1.
+ *   - A pointer may refer to host or device memory; the library asks the CUDA
+ *     runtime which (cudaPointerGetAttributes).  Host buffers are copied
+ *     through the library's own pinned staging.
+ *   - Every call returns an mbinv_status; nothing is thrown across the ABI.
+ *   - A context is used by one host thread at a time.  Calls are synchronous:
+ *     when a call returns, its outputs are written (work runs on the stream
+ *     given in the options).
+ *   - The library never reads or writes past the sizes it is given.  Inputs
+ *     are borrowed (never freed); outputs are owned by the caller.
+ *   - Errors: MBINV_EINVAL for bad arguments (nothing is launched),
+ *     MBINV_ENOMEM_CAP when the plan cannot fit device_cap_bytes (decided
+ *     before any launch), MBINV_ESINGULAR when a b x b pivot the recursion
+ *     must invert is singular to working precision (the paper assumes all of
+ *     them are nonsingular, Sec. 1 and Sec. 3), MBINV_ECUDA for a CUDA error.
+ */
+#ifndef MBINV_H
+#define MBINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBINV_OK = 0,
+    MBINV_EINVAL = 1,
+    MBINV_ENOMEM_CAP = 2,
+    MBINV_ESINGULAR = 3,
+    MBINV_ENOTCONV = 4,
+    MBINV_ETIMEOUT = 5,
+    MBINV_ECUDA = 6,
+    MBINV_ENOTSUP = 7
+} mbinv_status;
+
+/* Element type of M, of the outputs and of G / dM. */
+typedef enum { MBINV_DTYPE_F64 = 0, MBINV_DTYPE_F32 = 1 } mbinv_dtype;
+
+/* Arithmetic of the Schur-complement sweep.
+ *   MBINV_FP64        every product and every b x b inverse in FP64.
+ *   MBINV_FP32        every product and every inverse in FP32.
+ *   MBINV_MIXED_BF16  Schur products on the tensor cores (tcgen05) with BF16
+ *                     operand slices and FP32 accumulation, frame values kept
+ *                     in FP32, every b x b pivot inverted in FP64; with
+ *                     refine_steps = 1 the block is corrected by an FP64
+ *                     block-row residual (see mbinv_block). */
+typedef enum { MBINV_FP64 = 0, MBINV_FP32 = 1, MBINV_MIXED_BF16 = 2 } mbinv_precision;
+
+typedef struct {
+    size_t struct_size;         /* sizeof(mbinv_options) */
+    mbinv_precision precision;
+    size_t device_cap_bytes;    /* bound on the library's device memory
+                                   (workspace plus its own copy of M);
+                                   0 = no bound */
+    int refine_steps;           /* MIXED_BF16 only: 0 or 1 */
+    int bf16_slices;            /* MIXED_BF16 only: operands split into
+                                   1, 2 or 3 BF16 slices (1, 3 or 6
+                                   products) */
+    void *cuda_stream;          /* cudaStream_t; NULL = default stream */
+    uint64_t pad_seed;          /* seed of the coupling block used when k
+                                   does not divide n */
+    int profile;                /* 1: time every launch with CUDA events and
+                                   report device seconds per kernel family */
+    int reserved[7];
+} mbinv_options;
+
+typedef struct {
+    double gemm_flops;          /* algorithmic flops of the Schur products
+                                   (2 m n k each) */
+    double inv_flops;           /* 2 b^3 per b x b inverse */
+    double seconds;             /* wall time of the call */
+    double rel_residual;        /* refined path: ||E_i^T - X_i M||_F / sqrt(b) */
+    size_t peak_device_bytes;   /* planned high-water mark of the workspace */
+    size_t frames;              /* distinct frames evaluated */
+    size_t inversions;          /* b x b inverses performed */
+    size_t launches;            /* kernel launches issued */
+    int64_t failed_pivot;       /* on MBINV_ESINGULAR: index of the failing
+                                   inverse in launch order, else -1 */
+    double gemm_device_seconds; /* profile = 1: device time of the Schur
+                                   product launches */
+    double inv_device_seconds;  /* profile = 1: device time of the inverse
+                                   launches */
+    size_t gemm_launches;       /* Schur product launches */
+} mbinv_report;
+
+typedef struct mbinv_ctx mbinv_ctx;
+
+/* Called after each finished block by mbinv_all_blocks. */
+typedef void (*mbinv_block_done_cb)(int64_t i, int64_t j, void *user);
+
+/* One independent problem of mbinv_batched_blocks. */
+typedef struct {
+    int64_t n, k;               /* order of M and blocks per side */
+    int64_t i, j;               /* requested block, 0-based */
+    const void *M;              /* row-major, leading dimension ld, dtype of
+                                   the batch; host or device */
+    int64_t ld;
+    void *out;                  /* b_i x b_j result, leading dimension ldo */
+    int64_t ldo;
+    int status;                 /* written: mbinv_status of this problem */
+} mbinv_problem;
+
+/* Fills *opt with defaults: FP64, no cap, no refinement, 3 slices, default
+ * stream, pad_seed 0. */
+void mbinv_default_options(mbinv_options *opt);
+
+/* Creates a context for an n x n matrix split into k x k blocks
+ * (Sec. 2, Eq. blockmatricesnxn).  When k does not divide n the matrix is
+ * bordered to order k * ceil(n/k) (Sec. 3, Eq. M_augmented; see mbinv_block
+ * for the border used).  M is borrowed: if it is device memory it must stay
+ * valid and unchanged until mbinv_destroy; host memory is copied to the
+ * device during this call.  dtype is an mbinv_dtype.  opt may be NULL. */
+mbinv_status mbinv_create(mbinv_ctx **out, int64_t n, int64_t k, int dtype, const void *M, int64_t ld,
+                          const mbinv_options *opt);
+
+/* N_ij, the b x b block (i, j) of M^-1 (Sec. 3.1-3.2, Eq. blockmatrix_NxN;
+ * any block through a permutation of block rows and columns, Sec. 3.2 last
+ * paragraph).  out is b_i x b_j with leading dimension ldo, in M's dtype,
+ * host or device; b_i = b except for the last block when k does not divide n.
+ * When k does not divide n, the border is [[M, 0], [0, I]] for requests that
+ * do not touch the padded block or sit on the diagonal, [[M, B'], [0, I]] for
+ * (i, k-1), [[M, 0], [C', I]] for (k-1, j), B' and C'^T uniform in [-1, 1)
+ * drawn by SplitMix64 from pad_seed; the top-left n x n block of each
+ * bordered inverse is M^-1.  report may be NULL.
+ * MIXED_BF16 with refine_steps = 1 also computes block row i and block column
+ * j of the inverse with the same sweep and returns
+ * X_i E_j + (E_i^T - X_i M) Y_j, the residual taken in FP64. */
+mbinv_status mbinv_block(mbinv_ctx *ctx, int64_t i, int64_t j, void *out, int64_t ldo, mbinv_report *report);
+
+/* All blocks of M^-1 by k^2 independent runs (Sec. 5).  out is n x n with
+ * leading dimension ldo (host or device).  done (may be NULL) is a k*k
+ * row-major bitmap of blocks to skip; cb (may be NULL) is called after each
+ * finished block, so a caller can checkpoint and resume. */
+mbinv_status mbinv_all_blocks(mbinv_ctx *ctx, void *out, int64_t ldo, const uint8_t *done, mbinv_block_done_cb cb,
+                              void *user, mbinv_report *report);
+
+/* Block row i of M^-1 (b_i x n, leading dimension ldo): k runs of the
+ * recursion, one per block. */
+mbinv_status mbinv_block_row(mbinv_ctx *ctx, int64_t i, void *out, int64_t ldo, mbinv_report *report);
+
+/* Block column j of M^-1 (n x b_j, leading dimension ldo). */
+mbinv_status mbinv_block_col(mbinv_ctx *ctx, int64_t j, void *out, int64_t ldo, mbinv_report *report);
+
+/* Adjoint of L = sum(G .* N_ij) with respect to M:
+ *   dM += -(X_i)^T G (Y_j)^T,  X_i = block row i, Y_j = block column j of M^-1,
+ * both recomputed block by block with the recursion.  G is b_i x b_j
+ * (leading dimension ldg), dM is n x n (leading dimension ldd) and is
+ * accumulated into, both in M's dtype, host or device.  The paper has no
+ * gradient; this is the derivative of its output. */
+mbinv_status mbinv_backward(mbinv_ctx *ctx, int64_t i, int64_t j, const void *G, int64_t ldg, void *dM, int64_t ldd,
+                            mbinv_report *report);
+
+/* Many independent problems (the paper's blocks are embarrassingly parallel,
+ * Sec. 8), all in dtype with the options opt (may be NULL).  Each problem's
+ * status field is written; the return value is MBINV_OK when every problem
+ * succeeded, else the first failing status.  Problems run level by level
+ * with the same kernels in grouped launches. */
+mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem *probs, int dtype, const mbinv_options *opt,
+                                  mbinv_report *report);
+
+void mbinv_destroy(mbinv_ctx *ctx);
+
+const char *mbinv_status_string(mbinv_status s);
+
+/* Library version string. */
+const char *mbinv_version(void);
+
+/* Text of the last CUDA error seen by this thread (after MBINV_ECUDA). */
+const char *mbinv_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBINV_H */

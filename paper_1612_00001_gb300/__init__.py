@@ -1,0 +1,317 @@
+"""Python binding of libmbinv: memory-bounded block recursive inverse on GB300.
+
+Argument marshalling only.  Every step of the recursion runs in the CUDA
+kernels of ``libmbinv.so``; PyTorch provides device memory and the stream.
+Importing the package does not load the library; the first call does, and
+fails loudly when the library has not been built (``build()``) - there is no
+CPU fallback.
+
+    import paper_1612_00001_gb300 as mb
+    ctx = mb.Context(M, k=8, precision="fp64")     # M: 2-D float64/float32 tensor
+    n00 = ctx.block(0, 0)                          # N_00, the (0,0) block of M^-1
+    full = ctx.all_blocks()
+    g = mb.block(M, 8, 2, 5)                       # differentiable N_25
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmbinv.so")
+
+OK, EINVAL, ENOMEM_CAP, ESINGULAR, ENOTCONV, ETIMEOUT, ECUDA, ENOTSUP = range(8)
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_bf16": 2}
+DTYPE_F64, DTYPE_F32 = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MbinvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int),
+                ("device_cap_bytes", ctypes.c_size_t), ("refine_steps", ctypes.c_int),
+                ("bf16_slices", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("pad_seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("gemm_flops", ctypes.c_double), ("inv_flops", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("peak_device_bytes", ctypes.c_size_t),
+                ("frames", ctypes.c_size_t), ("inversions", ctypes.c_size_t), ("launches", ctypes.c_size_t),
+                ("failed_pivot", ctypes.c_int64), ("gemm_device_seconds", ctypes.c_double),
+                ("inv_device_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int64), ("i", ctypes.c_int64), ("j", ctypes.c_int64),
+                ("M", ctypes.c_void_p), ("ld", ctypes.c_int64), ("out", ctypes.c_void_p), ("ldo", ctypes.c_int64),
+                ("status", ctypes.c_int)]
+
+
+DONE_CB = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p)
+
+# name -> (restype, argtypes) of every entry point the header declares
+SIGNATURES = {
+    "mbinv_default_options": (None, [ctypes.POINTER(Options)]),
+    "mbinv_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Options)]),
+    "mbinv_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.POINTER(Report)]),
+    "mbinv_all_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, DONE_CB,
+                                        ctypes.c_void_p, ctypes.POINTER(Report)]),
+    "mbinv_block_row": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.POINTER(Report)]),
+    "mbinv_block_col": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.POINTER(Report)]),
+    "mbinv_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Report)]),
+    "mbinv_batched_blocks": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Problem), ctypes.c_int,
+                                            ctypes.POINTER(Options), ctypes.POINTER(Report)]),
+    "mbinv_destroy": (None, [ctypes.c_void_p]),
+    "mbinv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mbinv_version": (ctypes.c_char_p, []),
+    "mbinv_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compiles libmbinv.so in-tree (nvcc, sm_103a)."""
+    from . import build_lib
+    return build_lib.build(force=force)
+
+
+def lib():
+    """The loaded library.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmbinv is not built ({LIB_PATH} missing); call "
+                                   "paper_1612_00001_gb300.build() first - there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        L = lib()
+        msg = L.mbinv_status_string(status).decode()
+        if status == ECUDA:
+            msg += ": " + L.mbinv_last_cuda_error().decode()
+        raise MbinvError(status, f"{what}: {msg}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return DTYPE_F64
+    if t.dtype == torch.float32:
+        return DTYPE_F32
+    raise TypeError(f"unsupported dtype {t.dtype}: use float64 or float32")
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3, stream=None,
+                 pad_seed: int = 0, profile: bool = False) -> Options:
+    o = Options()
+    lib().mbinv_default_options(ctypes.byref(o))
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.device_cap_bytes = int(cap)
+    o.refine_steps = int(refine)
+    o.bf16_slices = int(slices)
+    o.cuda_stream = stream
+    o.pad_seed = int(pad_seed)
+    o.profile = int(bool(profile))
+    return o
+
+
+class Context:
+    """One matrix M (n x n, row-major) split into k x k blocks.
+
+    M may live on the host or on the GPU; a GPU tensor is borrowed and must
+    not change while the context lives."""
+
+    def __init__(self, M, k: int, precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3,
+                 pad_seed: int = 0, stream=None, profile: bool = False):
+        torch = _torch()
+        if M.dim() != 2 or M.shape[0] != M.shape[1]:
+            raise ValueError("M must be square")
+        if M.stride(1) != 1:
+            M = M.contiguous()
+        self.M = M
+        self.n = M.shape[0]
+        self.k = int(k)
+        self.b = -(-self.n // self.k)
+        self.dtype = M.dtype
+        self.device = M.device if M.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.stream = stream
+        self.opts = make_options(precision, cap, refine, slices, stream, pad_seed, profile)
+        h = ctypes.c_void_p()
+        _check(lib().mbinv_create(ctypes.byref(h), self.n, self.k, _dtype_code(M), _ptr(M), M.stride(0),
+                                  ctypes.byref(self.opts)), "mbinv_create")
+        self._h = h
+        self.last_report = None
+
+    def extent(self, t: int) -> int:
+        return self.n - (self.k - 1) * self.b if t == self.k - 1 else self.b
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mbinv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _out(self, rows, cols, out, on_host=False):
+        torch = _torch()
+        if out is None:
+            dev = torch.device("cpu") if on_host else self.device
+            out = torch.empty((rows, cols), dtype=self.dtype, device=dev, pin_memory=False)
+        if out.stride(1) != 1 or out.shape[0] < rows or out.shape[1] < cols or out.dtype != self.dtype:
+            raise ValueError("out must be a row-major tensor of M's dtype and of sufficient size")
+        return out
+
+    def block(self, i: int, j: int, out=None, on_host: bool = False):
+        """N_ij (b_i x b_j)."""
+        out = self._out(self.extent(i), self.extent(j), out, on_host)
+        rep = Report()
+        _check(lib().mbinv_block(self._h, i, j, _ptr(out), out.stride(0), ctypes.byref(rep)), f"mbinv_block({i},{j})")
+        self.last_report = rep.as_dict()
+        return out
+
+    def all_blocks(self, out=None, done=None, callback=None, on_host: bool = False):
+        out = self._out(self.n, self.n, out, on_host)
+        rep = Report()
+        dbuf = None
+        if done is not None:
+            flat = bytes(int(bool(x)) for x in done)
+            dbuf = ctypes.create_string_buffer(flat, len(flat))
+        cb = DONE_CB(lambda i, j, u: callback(int(i), int(j))) if callback else DONE_CB()
+        _check(lib().mbinv_all_blocks(self._h, _ptr(out), out.stride(0), dbuf, cb, None, ctypes.byref(rep)),
+               "mbinv_all_blocks")
+        self.last_report = rep.as_dict()
+        return out
+
+    def block_row(self, i: int, out=None):
+        out = self._out(self.extent(i), self.n, out)
+        rep = Report()
+        _check(lib().mbinv_block_row(self._h, i, _ptr(out), out.stride(0), ctypes.byref(rep)), "mbinv_block_row")
+        self.last_report = rep.as_dict()
+        return out
+
+    def block_col(self, j: int, out=None):
+        out = self._out(self.n, self.extent(j), out)
+        rep = Report()
+        _check(lib().mbinv_block_col(self._h, j, _ptr(out), out.stride(0), ctypes.byref(rep)), "mbinv_block_col")
+        self.last_report = rep.as_dict()
+        return out
+
+    def backward(self, i: int, j: int, G, dM=None):
+        """dM += -(X_i)^T G (Y_j)^T, the gradient of sum(G * N_ij) w.r.t. M."""
+        torch = _torch()
+        G = G.to(dtype=self.dtype).contiguous()
+        if dM is None:
+            dM = torch.zeros((self.n, self.n), dtype=self.dtype, device=G.device)
+        rep = Report()
+        _check(lib().mbinv_backward(self._h, i, j, _ptr(G), G.stride(0), _ptr(dM), dM.stride(0), ctypes.byref(rep)),
+               "mbinv_backward")
+        self.last_report = rep.as_dict()
+        return dM
+
+
+def batched_blocks(problems, precision="fp64", cap: int = 0, stream=None):
+    """problems: list of (M, k, i, j) with M square tensors of one dtype.
+    Returns (list of N_ij tensors, list of statuses)."""
+    torch = _torch()
+    if not problems:
+        return [], []
+    dtype = problems[0][0].dtype
+    arr = (Problem * len(problems))()
+    outs = []
+    for t, (M, k, i, j) in enumerate(problems):
+        n = M.shape[0]
+        b = -(-n // k)
+        bi = n - (k - 1) * b if i == k - 1 else b
+        bj = n - (k - 1) * b if j == k - 1 else b
+        o = torch.empty((bi, bj), dtype=dtype, device=M.device)
+        outs.append(o)
+        arr[t] = Problem(n, k, i, j, _ptr(M), M.stride(0), _ptr(o), o.stride(0), -1)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    opts = make_options(precision, cap, stream=stream)
+    rep = Report()
+    st = lib().mbinv_batched_blocks(len(problems), arr, _dtype_code(problems[0][0]), ctypes.byref(opts),
+                                    ctypes.byref(rep))
+    return outs, [arr[t].status for t in range(len(problems))], rep.as_dict(), st
+
+
+class _BlockInverse:
+    """torch.autograd.Function wrapper (built lazily so that importing the
+    package does not import torch)."""
+    fn = None
+
+    @classmethod
+    def get(cls):
+        if cls.fn is None:
+            torch = _torch()
+
+            class BlockInverse(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, M, k, i, j, precision, cap):
+                    c = Context(M.detach(), k, precision=precision, cap=cap)
+                    out = c.block(i, j)
+                    ctx.mb = c
+                    ctx.ij = (i, j)
+                    return out
+
+                @staticmethod
+                def backward(ctx, G):
+                    c = ctx.mb
+                    dM = c.backward(ctx.ij[0], ctx.ij[1], G.contiguous())
+                    c.close()
+                    return dM, None, None, None, None, None
+
+            cls.fn = BlockInverse
+        return cls.fn
+
+
+def block(M, k: int, i: int, j: int, precision="fp64", cap: int = 0):
+    """Differentiable N_ij of M^-1: the backward pass is the hand-written
+    adjoint dM = -(X_i)^T G (Y_j)^T, with X_i and Y_j recomputed block by block."""
+    return _BlockInverse.get().apply(M, k, i, j, precision, cap)

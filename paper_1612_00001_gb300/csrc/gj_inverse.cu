@@ -1,0 +1,325 @@
+// Batched b x b inverse by Gauss-Jordan elimination with partial pivoting.
+//
+// The paper inverts each b x b pivot with an LU routine that pivots by row
+// interchanges (Sec. 5 and Sec. 7).  Gauss-Jordan with partial pivoting picks
+// the same pivots as LU with partial pivoting (the candidates of column j are
+// the entries of the current Schur complement) and produces the inverse in
+// place; its 2 b^3 flops are the paper's "O(b^3)" per inversion (Sec. 6,
+// property (b)).
+//
+// Blocked in-place form, panel width nb.  For the panel J = [p, p + nb):
+//   1. panel kernel (one CTA per matrix): for each column j of J, pick the
+//      first row r >= j of largest |x_rj|, exchange whole rows j and r,
+//      scale row j and eliminate column j from every other row - on the
+//      panel columns only.  The panel then holds T[:, J], where T is the
+//      product of the nb elementary transforms; the pivot rows of the other
+//      columns are copied to a scratch W = X[J, rest].
+//   2. update kernel (many CTAs per matrix): X[:, rest] = T[:, J] W + X[:, rest]
+//      with the rows of J zeroed first - a rank-nb GEMM on the CUDA cores.
+// After the last panel the recorded row interchanges are undone as column
+// interchanges in reverse order while the result is written out.  For b at
+// most 128 the panel is the whole matrix and step 2 never runs.
+//
+// A pivot whose magnitude is not finite or is <= b * eps * max|entry| marks
+// the matrix singular through the status word; the elimination still runs to
+// the end so that no thread waits on another.
+#include <algorithm>
+#include <cfloat>
+
+#include "mbinv_internal.h"
+#include "tile_gemm.cuh"
+
+namespace mbinv {
+
+namespace {
+
+constexpr int kPanelThreads = 256;
+constexpr int kSmemLimit = 200 * 1024;
+
+template <typename T>
+__device__ __forceinline__ T load_as(const void* p, int dtype, int64_t idx) {
+  if (dtype == F64) return (T)((const double*)p)[idx];
+  return (T)((const float*)p)[idx];
+}
+
+template <typename TW>
+__device__ __forceinline__ TW eps_of();
+template <>
+__device__ __forceinline__ double eps_of<double>() { return DBL_EPSILON; }
+template <>
+__device__ __forceinline__ float eps_of<float>() { return FLT_EPSILON; }
+
+__global__ void zero_amax_kernel(const InvDesc* __restrict__ d, int count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) *d[t].amax = 0ull;
+}
+
+// work = (TW) src; amax = max |src| (as the bit pattern of a non-negative
+// double: the integer order of those patterns is their numeric order, and a
+// NaN compares above every number, which makes the matrix singular).
+template <typename TW>
+__global__ void gj_init_kernel(const InvDesc* __restrict__ descs, int in_dtype) {
+  const InvDesc d = descs[blockIdx.y];
+  const int64_t nel = (int64_t)d.b * d.b;
+  TW* w = (TW*)d.work;
+  double m = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nel; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / d.b, c = e % d.b;
+    const double v = load_as<double>(d.src, in_dtype, r * d.lds + c);
+    w[e] = (TW)v;
+    const double a = fabs(v);
+    if (!(a <= m)) m = a;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_xor_sync(0xffffffffu, m, o);
+    if (!(x <= m)) m = x;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(d.amax, (unsigned long long)__double_as_longlong(m));
+}
+
+// One CTA per matrix: factor the panel [p, p + nb) (see the file comment).
+template <typename TW, bool SMEM>
+__global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* __restrict__ descs, int p, int nb,
+                                                                 DevStatus* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const InvDesc d = descs[blockIdx.x];
+  const int b = d.b;
+  TW* X = (TW*)d.work;
+  TW* P;          // panel: P[i * ldp + t] is X[i][p + t]
+  int64_t ldp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kPanelThreads / 32;
+  __shared__ TW red_v[kPanelThreads / 32];
+  __shared__ int red_i[kPanelThreads / 32];
+  __shared__ int piv_row;
+  if (SMEM) {
+    P = (TW*)smem_raw;
+    ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
+    for (int64_t e = tid; e < (int64_t)b * nb; e += kPanelThreads) {
+      const int64_t i = e / nb, t = e % nb;
+      P[i * ldp + t] = X[i * b + p + t];
+    }
+  } else {
+    P = X + p;
+    ldp = b;
+  }
+  const double amax = __longlong_as_double((long long)*d.amax);
+  const TW tol = (TW)((double)b * (double)eps_of<TW>() * amax);
+  __syncthreads();
+
+  for (int t = 0; t < nb; ++t) {
+    const int j = p + t;
+    // ---- pivot search: first row of largest magnitude in column j, rows >= j
+    TW best = (TW)-1;
+    int bi = b;
+    for (int i = j + tid; i < b; i += kPanelThreads) {
+      const TW v = fabs(P[(int64_t)i * ldp + t]);
+      if (v > best) { best = v; bi = i; }  // NaN never wins
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const TW ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      TW bv = red_v[0];
+      int bix = red_i[0];
+      for (int w = 1; w < nwarps; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bix)) { bv = red_v[w]; bix = red_i[w]; }
+      if (bix >= b) bix = j;  // every candidate NaN or column exhausted
+      if (!(bv > tol) || !isfinite((double)bv)) {
+        atomicExch(&status->singular, 1);
+        atomicMin(&status->tag, d.tag);
+      }
+      piv_row = bix;
+      d.perm[j] = bix;
+    }
+    __syncthreads();
+    const int r = piv_row;
+    // ---- exchange whole rows j and r
+    if (r != j) {
+      for (int c = tid; c < nb; c += kPanelThreads) {
+        const TW a = P[(int64_t)j * ldp + c];
+        P[(int64_t)j * ldp + c] = P[(int64_t)r * ldp + c];
+        P[(int64_t)r * ldp + c] = a;
+      }
+      for (int c = tid; c < b - nb; c += kPanelThreads) {
+        const int cc = c < p ? c : c + nb;  // columns outside the panel
+        const TW a = X[(int64_t)j * b + cc];
+        X[(int64_t)j * b + cc] = X[(int64_t)r * b + cc];
+        X[(int64_t)r * b + cc] = a;
+      }
+    }
+    __syncthreads();
+    // ---- scale the pivot row (panel columns)
+    const TW piv = P[(int64_t)j * ldp + t];
+    __syncthreads();
+    for (int c = tid; c < nb; c += kPanelThreads) {
+      const TW v = (c == t) ? (TW)1 : P[(int64_t)j * ldp + c];
+      P[(int64_t)j * ldp + c] = v / piv;
+    }
+    __syncthreads();
+    // ---- eliminate column j from every other row (warp per row, lane per column)
+    for (int i = warp; i < b; i += nwarps) {
+      if (i == j) continue;
+      TW* xi = P + (int64_t)i * ldp;
+      const TW f = xi[t];
+      __syncwarp();
+      if (f != (TW)0) {
+        const TW* xj = P + (int64_t)j * ldp;
+        for (int c = lane; c < nb; c += 32) {
+          const TW base = (c == t) ? (TW)0 : xi[c];
+          xi[c] = base - f * xj[c];
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+
+  if (SMEM) {
+    for (int64_t e = tid; e < (int64_t)b * nb; e += kPanelThreads) {
+      const int64_t i = e / nb, t = e % nb;
+      X[i * b + p + t] = P[i * ldp + t];
+    }
+  }
+  // W = X[J, :] (the trailing update reads the pivot rows of the other columns)
+  if (nb < b) {
+    TW* W = (TW*)d.wrow;
+    for (int64_t e = tid; e < (int64_t)nb * b; e += kPanelThreads) {
+      const int64_t t = e / b, c = e % b;
+      W[e] = X[(int64_t)(p + t) * b + c];
+    }
+  }
+}
+
+// X[:, rest] = T[:, J] * W[:, rest] + (rows of J ? 0 : X[:, rest]).
+template <typename TW>
+__global__ void __launch_bounds__(256) gj_update_kernel(const InvDesc* __restrict__ descs, int p, int nb) {
+  using Cfg = TileCfg<TW>;
+  using TG = TileGemm<TW, TW, TW, Cfg::BM, Cfg::BN, Cfg::BK, Cfg::TM, Cfg::TN>;
+  __shared__ typename TG::Smem smem;
+  const InvDesc d = descs[blockIdx.z];
+  const int b = d.b;
+  const int m0 = blockIdx.y * Cfg::BM, n0 = blockIdx.x * Cfg::BN;
+  if (m0 >= b || n0 >= b) return;
+  if (n0 >= p && n0 + Cfg::BN <= p + nb) return;  // tile inside the panel
+  TW* X = (TW*)d.work;
+  TW acc[Cfg::TM][Cfg::TN];
+#pragma unroll
+  for (int i = 0; i < Cfg::TM; ++i)
+#pragma unroll
+    for (int j = 0; j < Cfg::TN; ++j) acc[i][j] = (TW)0;
+  TG::run(smem, X + p, b, 0, (const TW*)d.wrow, b, 0, m0, n0, b, b, nb, acc);
+  const int tx = threadIdx.x % TG::TX, ty = threadIdx.x / TG::TX;
+#pragma unroll
+  for (int i = 0; i < Cfg::TM; ++i) {
+    const int r = m0 + ty * Cfg::TM + i;
+    if (r >= b) continue;
+    const bool in_j = (r >= p && r < p + nb);
+#pragma unroll
+    for (int j = 0; j < Cfg::TN; ++j) {
+      const int c = n0 + tx * Cfg::TN + j;
+      if (c >= b || (c >= p && c < p + nb)) continue;
+      TW* x = X + (int64_t)r * b + c;
+      *x = in_j ? acc[i][j] : (*x + acc[i][j]);
+    }
+  }
+}
+
+// out[r][c] = X[r][col_of[c]], where col_of undoes the row interchanges as
+// column interchanges taken in reverse order.
+template <typename TW, typename TO>
+__global__ void gj_finalize_kernel(const InvDesc* __restrict__ descs, int rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* col_of = (int*)smem_raw;
+  const InvDesc d = descs[blockIdx.y];
+  const int b = d.b;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) col_of[c] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = b - 1; j >= 0; --j) {
+      const int q = d.perm[j];
+      if (q != j) {
+        const int a = col_of[j];
+        col_of[j] = col_of[q];
+        col_of[q] = a;
+      }
+    }
+  }
+  __syncthreads();
+  const TW* X = (const TW*)d.work;
+  TO* out = (TO*)d.dst;
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int r1 = min(b, r0 + rows_per_cta);
+  for (int r = r0; r < r1; ++r)
+    for (int c = threadIdx.x; c < b; c += blockDim.x) out[(int64_t)r * d.ldd + c] = (TO)X[(int64_t)r * b + col_of[c]];
+}
+
+template <typename TW>
+cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int count, int b, DevStatus* d_status,
+                        cudaStream_t s, int* launches) {
+  int nl = 0;
+  zero_amax_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count);
+  ++nl;
+  {
+    const int64_t nel = (int64_t)b * b;
+    const int chunks = (int)std::min<int64_t>(64, (nel + 255 * 8) / (256 * 8));
+    dim3 g(std::max(chunks, 1), count);
+    gj_init_kernel<TW><<<g, 256, 0, s>>>(d_desc, in_dtype);
+    ++nl;
+  }
+  const int nb = inv_panel_width(b, sizeof(TW) == 8 ? F64 : F32);
+  const size_t psmem = (size_t)b * (nb + 1) * sizeof(TW);
+  const bool use_smem = psmem <= (size_t)kSmemLimit;
+  for (int p = 0; p < b; p += nb) {
+    const int w = std::min(nb, b - p);
+    if (use_smem) {
+      static bool attr_set = false;
+      if (!attr_set) {
+        cudaFuncSetAttribute(gj_panel_kernel<TW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        attr_set = true;
+      }
+      gj_panel_kernel<TW, true><<<count, kPanelThreads, (size_t)b * (w + 1) * sizeof(TW), s>>>(d_desc, p, w, d_status);
+    } else {
+      gj_panel_kernel<TW, false><<<count, kPanelThreads, 0, s>>>(d_desc, p, w, d_status);
+    }
+    ++nl;
+    if (w < b) {
+      using Cfg = TileCfg<TW>;
+      dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);
+      gj_update_kernel<TW><<<g, 256, 0, s>>>(d_desc, p, w);
+      ++nl;
+    }
+  }
+  {
+    const int rows = 8;
+    dim3 g((b + rows - 1) / rows, count);
+    const size_t sm = (size_t)b * sizeof(int);
+    if (out_dtype == F64)
+      gj_finalize_kernel<TW, double><<<g, 256, sm, s>>>(d_desc, rows);
+    else
+      gj_finalize_kernel<TW, float><<<g, 256, sm, s>>>(d_desc, rows);
+    ++nl;
+  }
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int inv_panel_width(int b, int wtype) {
+  const size_t es = wtype == F64 ? 8 : 4;
+  if ((size_t)b * (b + 1) * es <= 132 * 1024) return b;  // whole matrix in one panel
+  return 32;
+}
+
+cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
+                              DevStatus* d_status, cudaStream_t s, int* launches) {
+  if (count <= 0) return cudaSuccess;
+  if (wtype == F64) return run_batch_t<double>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches);
+  return run_batch_t<float>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches);
+}
+
+}  // namespace mbinv

@@ -1,0 +1,125 @@
+// Internal declarations shared by the translation units of libmbinv.
+// Nothing here is part of the public C ABI (include/mbinv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace mbinv {
+
+enum DType : int { F64 = 0, F32 = 1, BF16 = 2 };
+
+inline size_t dtype_size(int t) { return t == F64 ? 8 : (t == F32 ? 4 : 2); }
+
+// --------------------------------------------------------------- planner
+// A frame of the recursion (Sec. 3.1): kept block row/column, role and, for
+// order >= 3, the ids of its four children; order-2 frames are leaves whose
+// value is M[a,c] - M[a,pc] (P^-1 M[pr,c]) with P = M[pr,pc] (Eqs. FA2-FD2).
+struct PFrame {
+  int order = 0, role = 0;
+  int krow = -1, kcol = -1;
+  int child[4] = {-1, -1, -1, -1};
+  int kept = -1, left = -1, piv = -1, right = -1;
+};
+
+struct Plan {
+  int k = 0, i = 0, j = 0;
+  std::vector<int> rows, cols;  // root lists (0-based block indices)
+  int prow = -1, pcol = -1;     // pivot block (the paper's M_22 after permutation)
+  std::vector<PFrame> f;        // f[0] is the root
+  std::vector<std::vector<int>> level;  // level[p] = ids of frames of order p
+  size_t nonleaf = 0, leaves = 0;
+};
+
+Plan build_plan(int k, int i, int j);
+
+// Operand reference of a scheduled operation.
+struct Ref {
+  enum Kind : int { NONE = 0, MBLK = 1, SLOT = 2, OUT = 3 } kind = NONE;
+  int r = 0, c = 0;  // block coordinates for MBLK
+  int slot = -1;     // slot id for SLOT
+};
+
+struct GemmOp {  // C = alpha * A * B + beta * Cin, all b x b
+  Ref A, B, Cin, C;
+  double alpha = 1.0, beta = 0.0;
+};
+struct InvOp {  // dst = src^-1
+  Ref src, dst;
+  int frame = -1;
+};
+struct Step {
+  enum Kind : int { INV = 0, GEMM = 1 } kind = INV;
+  std::vector<InvOp> inv;
+  std::vector<GemmOp> gemm;
+};
+
+struct Schedule {
+  std::vector<Step> steps;
+  int nslots = 0;      // peak number of b x b value slots alive at once
+  int max_inv_batch = 0;
+  double gemm_flops_units = 0;  // in units of b^3 (2 per product)
+  double inv_units = 0;         // in units of b^3 (2 per inverse)
+  size_t frames = 0, inversions = 0;
+};
+
+// Builds the level-by-level schedule of one request.  zchunk bounds the
+// number of Schur temporaries alive at once (0 = a whole level).
+Schedule build_schedule(const Plan& p, int zchunk);
+
+// --------------------------------------------------------------- kernels
+struct GemmDesc {
+  const void* A;
+  const void* B;
+  const void* Cin;
+  void* C;
+  int64_t lda, ldb, ldcin, ldc;
+  int m, n, k;
+  int ta, tb;      // op(A) = A^T when ta, op(B) = B^T when tb
+  double alpha, beta;
+  int tiles_n;     // column tiles of this problem
+  int tile_start;  // first global tile index of this problem
+};
+
+// Element-type combination of a grouped GEMM: A, B, C types and the
+// accumulator's.
+enum GemmCombo : int {
+  G_F64 = 0,       // double x double -> double, FP64 accumulate
+  G_F32 = 1,       // float x float -> float, FP32 accumulate
+  G_F32IN_F64 = 2, // float x float -> double, FP64 accumulate
+  G_F64F32_F64 = 3 // double x float -> double, FP64 accumulate
+};
+void gemm_tile_shape(int combo, int* bm, int* bn);
+cudaError_t launch_gemm_grouped(int combo, const GemmDesc* d_descs, int ndesc, int total_tiles, cudaStream_t s);
+
+// Batched Gauss-Jordan inversion with partial pivoting.
+struct InvDesc {
+  const void* src;  // input matrix (b x b, leading dimension lds)
+  int64_t lds;
+  void* dst;        // output (b x b, leading dimension ldd)
+  int64_t ldd;
+  void* work;       // b x b scratch in the working precision
+  void* wrow;       // nb x b scratch: pivot rows of the trailing columns
+  int* perm;        // b ints: row interchanges
+  unsigned long long* amax;  // max |entry| (bit pattern of a non-negative double)
+  int b;
+  int tag;          // reported through the status word when singular
+};
+// Status word written by the inverse kernels: flag != 0 when a pivot was
+// singular; tag holds the smallest failing InvDesc::tag.
+struct DevStatus {
+  int singular;
+  int tag;
+};
+// Panel width of the blocked elimination for order b in working type wtype.
+int inv_panel_width(int b, int wtype);
+// Inverts count matrices of order b (all the same order) described by
+// d_desc.  in_dtype / out_dtype / wtype are DType values; wtype is F64 or F32.
+// d_amax must hold count zeroed words (the call zeroes them).
+cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
+                              DevStatus* d_status, cudaStream_t s, int* launches);
+
+}  // namespace mbinv

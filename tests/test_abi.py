@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point its header declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(mbinv_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_1612_00001_gb300 as mb
+    return mb.build()
+
+
+def test_header_declares_entry_points():
+    names = declared()
+    for must in ("mbinv_create", "mbinv_block", "mbinv_all_blocks", "mbinv_backward", "mbinv_batched_blocks",
+                 "mbinv_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches(libpath):
+    import paper_1612_00001_gb300 as mb
+    L = mb.lib()
+    for n in declared():
+        assert hasattr(L, n)
+        assert n in mb.SIGNATURES, f"binding lacks {n}"
+    assert L.mbinv_version().decode().startswith("mbinv")
+    assert L.mbinv_status_string(mb.ESINGULAR).decode()
+    o = mb.Options()
+    L.mbinv_default_options(ctypes.byref(o))
+    assert o.struct_size == ctypes.sizeof(mb.Options) and o.precision == 0 and o.bf16_slices == 3
+
+
+def test_invalid_arguments_rejected_without_gpu(libpath):
+    import paper_1612_00001_gb300 as mb
+    L = mb.lib()
+    h = ctypes.c_void_p()
+    # null matrix, bad k, bad dtype: rejected before any CUDA call
+    assert L.mbinv_create(ctypes.byref(h), 16, 4, 0, None, 16, None) == mb.EINVAL
+    buf = (ctypes.c_double * 256)()
+    assert L.mbinv_create(ctypes.byref(h), 16, 0, 0, buf, 16, None) == mb.EINVAL
+    assert L.mbinv_create(ctypes.byref(h), 16, 4, 7, buf, 16, None) == mb.EINVAL
+    assert L.mbinv_create(ctypes.byref(h), 16, 4, 0, buf, 8, None) == mb.EINVAL
+    assert L.mbinv_block(None, 0, 0, buf, 4, None) == mb.EINVAL
+    assert L.mbinv_batched_blocks(-1, None, 0, None, None) == mb.EINVAL
