@@ -66,10 +66,10 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                         ctypes.POINTER(ctypes.c_int64)]
             L.orc_bri_frame.restype = ctypes.c_int
-            L.orc_bri_block.argtypes = [dp, i64, i64, i64, i64, i64, ctypes.c_int, ctypes.c_int, dp,
+            L.orc_bri_block.argtypes = [dp, i64, i64, i64, i64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                         ctypes.POINTER(ctypes.c_int64)]
             L.orc_bri_block.restype = ctypes.c_int
-            L.orc_root_lists.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
+            L.orc_root_lists.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
             L.orc_root_lists.restype = None
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_set_num_threads.argtypes = [ctypes.c_int]
@@ -120,10 +120,10 @@ def dense_inverse(m):
     return gj_inverse(m)
 
 
-def root_lists(k: int, i: int, j: int):
+def root_lists(k: int, i: int, j: int, pad_last: bool = False):
     r = (ctypes.c_int * k)()
     c = (ctypes.c_int * k)()
-    lib().orc_root_lists(k, i, j, r, c)
+    lib().orc_root_lists(k, i, j, int(pad_last), r, c)
     return list(r), list(c)
 
 
@@ -142,8 +142,9 @@ def bri_frame(m, b: int, rows, cols, role, piv_row: int, piv_col: int, memo=Fals
     return out, st, dict(schur_ops=stats[0], inversions=stats[1], frames=stats[2], memo_hits=stats[3])
 
 
-def bri_block(m, k: int, i: int, j: int, memo: bool = True, reassoc: bool = False):
-    """N_ij by the paper's recursion.  m must be (k*b) x (k*b).  Returns
+def bri_block(m, k: int, i: int, j: int, memo: bool = True, reassoc: bool = False, pad_last: bool = False):
+    """N_ij by the paper's recursion.  m must be (k*b) x (k*b); pad_last
+    marks a matrix bordered by augment() (see root_lists).  Returns
     (N_ij, status, stats)."""
     m = _f64(m)
     n = m.shape[0]
@@ -151,7 +152,7 @@ def bri_block(m, k: int, i: int, j: int, memo: bool = True, reassoc: bool = Fals
     b = n // k
     out = np.empty((b, b))
     stats = (ctypes.c_int64 * 4)()
-    st = lib().orc_bri_block(_dp(m), n, k, b, i, j, int(memo), int(reassoc), _dp(out), stats)
+    st = lib().orc_bri_block(_dp(m), n, k, b, i, j, int(memo), int(reassoc), int(pad_last), _dp(out), stats)
     return out, st, dict(schur_ops=stats[0], inversions=stats[1], frames=stats[2], memo_hits=stats[3])
 
 
@@ -167,7 +168,10 @@ def augment(m, k: int, i: int | None = None, j: int | None = None, coupling=None
     with i != k-1 the border is [[M, B'], [0, I]] (inverse [[M^-1, -M^-1 B'],
     [0, I]]), and for (k-1, j) it is [[M, 0], [C', I]] (inverse
     [[M^-1, 0], [-C' M^-1, I]]); the top-left n x n block of the inverse is
-    M^-1 either way.  ``coupling`` is B' (n x l) or C'^T (n x l).
+    M^-1 either way.  ``coupling`` is B' (n x l) or C'^T (n x l).  Requests
+    that do not touch the last block keep the plain border and must be run
+    with pad_last=True (the padded block becomes the pivot index; with it
+    anywhere else, frames that keep the padded rows are singular).
     Returns (Gamma, b, l)."""
     m = _f64(m)
     n = m.shape[0]
@@ -221,12 +225,12 @@ def rel_fro(a, ref) -> float:
     return float(np.linalg.norm(a - ref) / (d if d > 0 else 1.0))
 
 
-def sensitivity_floor(m, k: int, i: int, j: int) -> float:
+def sensitivity_floor(m, k: int, i: int, j: int, pad_last: bool = False) -> float:
     """|O2 - O2'|_F / |O2|_F where O2' evaluates every Schur product as
     (left * pivot^-1) * right instead of left * (pivot^-1 * right): the
     method's own sensitivity to the order of rounding."""
-    a, st, _ = bri_block(m, k, i, j, memo=True, reassoc=False)
-    b_, st2, _ = bri_block(m, k, i, j, memo=True, reassoc=True)
+    a, st, _ = bri_block(m, k, i, j, memo=True, reassoc=False, pad_last=pad_last)
+    b_, st2, _ = bri_block(m, k, i, j, memo=True, reassoc=True, pad_last=pad_last)
     if st or st2:
         return float("nan")
     return rel_fro(b_, a)

@@ -27,6 +27,7 @@
  *       orc_bri_block      N_ij: root lists for block (i, j) (the permutation
  *                          of Sec. 3.2, last paragraph), then the root value
  *                          and its inverse (Eq. blockmatrix_NxN).
+ *       orc_root_lists     the permutation itself (see below).
  *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes):
@@ -34,7 +35,9 @@
  *     columns (i, common..., j), common = the other indices ascending; for
  *     i == j both lists are (i, the rest ascending).  Since
  *     (P M Q)^-1 = Q^T M^-1 P^T, the top-left block of the permuted inverse
- *     is N_ij.
+ *     is N_ij.  When the matrix was bordered to a multiple of k and the
+ *     request does not touch the last block, the last block is moved to the
+ *     second position of both lists (orc_root_lists).
  *   - A frame of order >= 3 whose first row (column) is the pivot index - the
  *     entry at position 2 of the root lists, the paper's M_22 - has its first
  *     two rows (columns) exchanged before it is split; order-2 frames are not
@@ -338,9 +341,24 @@ int orc_bri_frame(const double *M, int64_t ld, int64_t b, const int *rows, const
     return st;
 }
 
-/* Root lists for block (i, j), 0-based. */
-void orc_root_lists(int k, int i, int j, int *rows, int *cols)
+/* Root lists for block (i, j), 0-based.  pad_last = 1 when the last block
+ * row/column is partly or wholly padding (k does not divide the order, Sec. 3,
+ * Eq. M_augmented): a request that does not touch the last block then puts
+ * it second in both lists, so that it is the pivot index of every frame and
+ * is eliminated in all of them; no frame value then holds a padded row or
+ * column, and none of them is structurally singular. */
+void orc_root_lists(int k, int i, int j, int pad_last, int *rows, int *cols)
 {
+    const int last = k - 1;
+    if (pad_last && k >= 3 && i != last && j != last) {
+        int t = 2;
+        rows[0] = j; cols[0] = i;
+        rows[1] = cols[1] = last;
+        for (int x = 0; x < last; ++x)
+            if (x != i && x != j) { rows[t] = x; cols[t] = x; ++t; }
+        if (i != j) { rows[k - 1] = i; cols[k - 1] = j; }
+        return;
+    }
     if (i == j) {
         int t = 0;
         rows[t] = cols[t] = i; ++t;
@@ -357,7 +375,7 @@ void orc_root_lists(int k, int i, int j, int *rows, int *cols)
 /* N_ij, the (i, j) b x b block of M^-1 (M is (k*b) x (k*b), row-major, leading
  * dimension ld).  out is b x b contiguous.  k == 1 inverts M directly. */
 int orc_bri_block(const double *M, int64_t ld, int64_t k, int64_t b, int64_t i, int64_t j, int memo, int reassoc,
-                  double *out, int64_t *stats)
+                  int pad_last, double *out, int64_t *stats)
 {
     if (k < 1 || k > ORC_MAXK || b <= 0 || i < 0 || j < 0 || i >= k || j >= k) return ORC_EINVAL;
     if (k == 1) {
@@ -366,7 +384,7 @@ int orc_bri_block(const double *M, int64_t ld, int64_t k, int64_t b, int64_t i, 
         return st;
     }
     int rows[ORC_MAXK + 1], cols[ORC_MAXK + 1];
-    orc_root_lists((int)k, (int)i, (int)j, rows, cols);
+    orc_root_lists((int)k, (int)i, (int)j, pad_last, rows, cols);
     bri_run R;
     memset(&R, 0, sizeof R);
     R.M = M; R.ld = ld; R.b = b; R.piv_row = rows[1]; R.piv_col = cols[1];

@@ -454,7 +454,7 @@ mbinv_status block_to_device(mbinv_ctx* c, int64_t i, int64_t j, void* dst, int6
   auto key = std::make_pair((int)i, (int)j);
   auto it = c->plans.find(key);
   if (it == c->plans.end()) {
-    Plan P = build_plan((int)c->k, (int)i, (int)j);
+    Plan P = build_plan((int)c->k, (int)i, (int)j, c->l > 0);
     Schedule S;
     int ic;
     if (!fit_cap(c, P, &S, &ic)) return MBINV_ENOMEM_CAP;

@@ -34,7 +34,7 @@ struct Plan {
   size_t nonleaf = 0, leaves = 0;
 };
 
-Plan build_plan(int k, int i, int j);
+Plan build_plan(int k, int i, int j, bool pad_last);
 
 // Operand reference of a scheduled operation.
 struct Ref {

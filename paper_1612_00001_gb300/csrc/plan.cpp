@@ -96,15 +96,31 @@ struct Builder {
 
 }  // namespace
 
-Plan build_plan(int k, int i, int j) {
+Plan build_plan(int k, int i, int j, bool pad_last) {
   if (k < 2 || k > 63 || i < 0 || j < 0 || i >= k || j >= k) throw std::invalid_argument("bad plan request");
   Plan P;
   P.k = k;
   P.i = i;
   P.j = j;
   // Root lists for block (i, j): (P M Q)^-1 = Q^T M^-1 P^T, so rows start
-  // with j and columns with i; the other indices keep their order.
-  if (i == j) {
+  // with j and columns with i; the other indices keep their order.  When the
+  // last block is padding (k does not divide n) and the request does not
+  // touch it, it is placed second in both lists: it is then the pivot index,
+  // eliminated in every frame, so no frame keeps padded rows or columns.
+  const int last = k - 1;
+  if (pad_last && k >= 3 && i != last && j != last) {
+    P.rows = {j, last};
+    P.cols = {i, last};
+    for (int x = 0; x < last; ++x)
+      if (x != i && x != j) {
+        P.rows.push_back(x);
+        P.cols.push_back(x);
+      }
+    if (i != j) {
+      P.rows.push_back(i);
+      P.cols.push_back(j);
+    }
+  } else if (i == j) {
     P.rows.push_back(i);
     for (int x = 0; x < k; ++x)
       if (x != i) P.rows.push_back(x);

@@ -86,21 +86,26 @@ def test_fp64_host_buffers(mb):
 
 
 def test_fp64_padding_border(mb):
-    """n = 250, k = 4: b = 63, l = 2 (Eq. M_augmented), coupling border for
-    requests that touch the padded block."""
-    n, k, seed = 250, 4, 17
+    """n = 250, k = 4 (b = 63, l = 2) and n = 250, k = 6 (b = 42, l = 2):
+    Eq. M_augmented, coupling border for requests that touch the padded
+    block, padded block as pivot index for the others."""
+    for n, k, seed in [(250, 4, 17), (250, 6, 5)]:
+        _padding_case(mb, n, k, seed)
+
+
+def _padding_case(mb, n, k, seed):
     m = bi.uniform_shift(n, 8)
     ctx = mb.Context(dev(m), k, pad_seed=seed)
     inv = np.linalg.inv(m)
-    b = 63
+    b = -(-n // k)
     cpl = bi.pad_columns(n, k * b - n, seed)
     for i, j in itertools.product(range(k), range(k)):
         got = to_np(ctx.block(i, j))
         g, _, _ = oracle.augment(m, k, i, j, coupling=cpl)
-        ref = oracle_block(g, k, i, j)
+        ref = oracle_block(g, k, i, j, pad_last=True)
         r1, c1 = min(b, n - i * b), min(b, n - j * b)
         assert got.shape == (r1, c1)
-        tol, _ = parity_tol(g, k, i, j, TOL_FP64)
+        tol, _ = parity_tol(g, k, i, j, TOL_FP64, pad_last=True)
         assert oracle.rel_fro(got, ref[:r1, :c1]) <= tol, (i, j)
         assert oracle.rel_fro(got, inv[i * b:i * b + r1, j * b:j * b + c1]) < 1e-11
 
@@ -185,7 +190,7 @@ def test_batched_problems(mb):
         m = bi.uniform_shift(p["n"], p["seed"])
         tensors.append((dev(m), p["k"], p["i"], p["j"]))
         g, b, l = oracle.augment(m, p["k"], p["i"], p["j"], coupling=bi.pad_columns(p["n"], (-p["n"]) % p["k"], 0))
-        ref = oracle_block(g, p["k"], p["i"], p["j"])
+        ref = oracle_block(g, p["k"], p["i"], p["j"], pad_last=l > 0)
         refs.append(ref)
     outs, statuses, rep, st = mb.batched_blocks(tensors)
     assert st == mb.OK and all(s == mb.OK for s in statuses)

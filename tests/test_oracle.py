@@ -308,7 +308,7 @@ def test_augmented_matrix():
     cpl = bi.pad_columns(n, l, 1)
     for i, j in itertools.product(range(k), range(k)):
         gi, _, _ = oracle.augment(m, k, i, j, coupling=cpl)
-        n_ij, st, _ = oracle.bri_block(gi, k, i, j)
+        n_ij, st, _ = oracle.bri_block(gi, k, i, j, pad_last=True)
         assert st == oracle.OK, (i, j)
         r0, r1 = i * b, min((i + 1) * b, n)
         c0, c1 = j * b, min((j + 1) * b, n)
@@ -318,6 +318,30 @@ def test_augmented_matrix():
     assert st == oracle.SINGULAR
     _, st, _ = oracle.bri_block(g, k, 3, 0)
     assert st == oracle.SINGULAR
+
+
+@pytest.mark.parametrize("n,k", [(22, 5), (31, 6), (61, 8)])
+def test_augmented_matrix_larger_k(n, k):
+    """For k >= 5 the padded block must be the pivot index of requests that do
+    not touch it: elsewhere some inverted frame keeps padded rows, which are
+    zero, and the recursion stops on a singular pivot."""
+    m = bi.uniform_shift(n, 3)
+    ref = np.linalg.inv(m)
+    b = -(-n // k)
+    l = k * b - n
+    cpl = bi.pad_columns(n, l, 0)
+    for i, j in itertools.product(range(k), range(k)):
+        g, _, _ = oracle.augment(m, k, i, j, coupling=cpl)
+        n_ij, st, _ = oracle.bri_block(g, k, i, j, pad_last=True)
+        assert st == oracle.OK, (i, j)
+        r0, r1 = i * b, min((i + 1) * b, n)
+        c0, c1 = j * b, min((j + 1) * b, n)
+        assert oracle.rel_fro(n_ij[:r1 - r0, :c1 - c0], ref[r0:r1, c0:c1]) < 1e-10, (i, j)  # k = 8: instability floor ~1e-12
+    g, _, _ = oracle.augment(m, k)
+    _, st, _ = oracle.bri_block(g, k, 0, 1, pad_last=False)
+    assert st == oracle.SINGULAR
+    rows, cols = oracle.root_lists(k, 0, 1, pad_last=True)
+    assert rows == [1, k - 1] + list(range(2, k - 1)) + [0] and cols == [0, k - 1] + list(range(2, k - 1)) + [1]
 
 
 # -------------------------------------------- residual, refinement, adjoint
