@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,7 @@
 
 #include "../../include/mbinv.h"
 #include "mbinv_internal.h"
+#include "tc_gemm.h"
 
 using namespace mbinv;
 
@@ -88,6 +90,23 @@ __global__ void convert_kernel(const TS* src, int64_t lds, TD* dst, int64_t ldd,
   dst[r * ldd + q] = (TD)src[r * lds + q];
 }
 
+// R[r][i0 + r] += 1 for r < b: E_i^T - X_i M from -X_i M.
+__global__ void add_eye_kernel(double* R, int64_t ldr, int64_t i0, int64_t b) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < b) R[r * ldr + i0 + r] += 1.0;
+}
+
+// sum of squares of an m x n FP64 matrix into *acc (one atomic per warp)
+__global__ void sumsq_kernel(const double* R, int64_t ldr, int64_t m, int64_t n, double* acc) {
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = R[(e / n) * ldr + e % n];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -141,8 +160,10 @@ struct mbinv_ctx {
   int border_mode = -1;  // border strips currently written (-1: none yet)
   // workspace
   DevBuf slots, inv_work, inv_wrow, inv_perm, inv_amax, desc, status, outtmp, rowbuf, colbuf, resid;
+  DevBuf apk, bpk, b2pk, tcerr;  // mixed path: packed BF16 operand slabs
   HostBuf hdesc, hstage;
   std::vector<cudaEvent_t> events;  // profiling: pairs around launches
+  bool in_sweep = false;            // refinement: inner sweeps run unrefined
   size_t own_bytes = 0;  // peak of what this context holds on the device
   std::map<std::pair<int, int>, std::pair<Plan, Schedule>> plans;
 };
@@ -218,7 +239,7 @@ struct Exec {
   int inv_chunk;
   int launches = 0;
   int gemm_launches = 0;
-  double gemm_dev_s = 0, inv_dev_s = 0;
+  double gemm_dev_s = 0, inv_dev_s = 0, pack_dev_s = 0;
 };
 
 cudaError_t ensure_events(mbinv_ctx* c, size_t n) {
@@ -389,6 +410,216 @@ mbinv_status run_schedule(Exec& X) {
   return MBINV_OK;
 }
 
+// Runs a schedule on the mixed path: pivot inverses as in run_schedule (FP64
+// Gauss-Jordan, FP32 results), every Schur product on the tensor cores.  A
+// pair of GEMM steps Z = P^-1 R, X = K - L Z becomes: pack the distinct P^-1
+// (row-major slices) and every R (transposed slices), tcgen05 product with the
+// slices of Z^T written straight into the B operand of the second product,
+// pack the distinct L, tcgen05 product with the fused subtraction from K.
+mbinv_status run_schedule_mixed(Exec& X) {
+  mbinv_ctx* c = X.c;
+  const Schedule& S = *X.S;
+  const int b = (int)c->b;
+  const int T = tc::tile_rows(), KT = tc::tile_k();
+  const int rpad = (b + T - 1) / T * T, kpad = (b + KT - 1) / KT * KT;
+  const int NS = c->opt.bf16_slices;
+  const size_t slab = (size_t)NS * rpad * kpad;  // bf16 elements per packed operand
+  // pass 1: sizes
+  size_t maxA = 1, maxB = 1, need = 256;
+  for (const Step& st : S.steps) {
+    if (st.kind == Step::INV) {
+      const size_t nchunks = (st.inv.size() + X.inv_chunk - 1) / X.inv_chunk;
+      need += st.inv.size() * sizeof(InvDesc) + 256 * nchunks;
+    } else {
+      std::map<std::pair<int, int>, int> da;
+      for (const GemmOp& g : st.gemm) da[{g.A.kind == Ref::SLOT ? g.A.slot : -1 - g.A.r, g.A.c}] = 0;
+      maxA = std::max(maxA, da.size());
+      maxB = std::max(maxB, st.gemm.size());
+      need += (da.size() + st.gemm.size()) * sizeof(tc::PackDesc) + st.gemm.size() * sizeof(tc::TcProblem) + 768;
+    }
+  }
+  CU(c->apk.ensure(maxA * slab * 2));
+  CU(c->bpk.ensure(maxB * slab * 2));
+  CU(c->b2pk.ensure(maxB * slab * 2));
+  CU(c->tcerr.ensure(256));
+  CU(c->desc.ensure(need));
+  CU(c->hdesc.ensure(need));
+  char* hbase = (char*)c->hdesc.p;
+  char* dbase = (char*)c->desc.p;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  struct Launch {
+    int kind;  // 0 inverse, 1 pack A, 2 pack B, 3 tc gemm
+    size_t off;
+    int count;
+    int in_dt, out_dt;
+    int nA;  // tc gemm: slabs of A
+    int mode;
+    __nv_bfloat16 *adst, *bsrc;
+  };
+  std::vector<Launch> L;
+  const size_t ws = 8;
+  const size_t nb = (size_t)inv_panel_width(b, F64);
+  const size_t wstride = ((size_t)b * b * ws + 255) & ~(size_t)255;
+  const size_t rstride = (nb * b * ws + 255) & ~(size_t)255;
+  const size_t pstride = ((size_t)b * 4 + 255) & ~(size_t)255;
+  std::map<int, int> zslab;  // slot of a Z value -> slab in b2pk
+  int inv_tag = 0;
+  for (const Step& st : S.steps) {
+    if (st.kind == Step::INV) {
+      for (size_t c0 = 0; c0 < st.inv.size(); c0 += X.inv_chunk) {
+        const size_t c1 = std::min(st.inv.size(), c0 + (size_t)X.inv_chunk);
+        const size_t o = take((c1 - c0) * sizeof(InvDesc));
+        InvDesc* hd = (InvDesc*)(hbase + o);
+        int in_dt = -1, out_dt = -1;
+        for (size_t t = c0; t < c1; ++t) {
+          InvDesc d{};
+          int64_t ld;
+          d.src = resolve(c, st.inv[t].src, X, &ld, &in_dt);
+          d.lds = ld;
+          d.dst = (void*)resolve(c, st.inv[t].dst, X, &ld, &out_dt);
+          d.ldd = ld;
+          d.work = (char*)c->inv_work.p + (t - c0) * wstride;
+          d.wrow = (char*)c->inv_wrow.p + (t - c0) * rstride;
+          d.perm = (int*)((char*)c->inv_perm.p + (t - c0) * pstride);
+          d.amax = (unsigned long long*)((char*)c->inv_amax.p + (t - c0) * 256);
+          d.b = b;
+          d.tag = inv_tag++;
+          hd[t - c0] = d;
+        }
+        L.push_back({0, o, (int)(c1 - c0), in_dt, out_dt, 0, 0, nullptr, nullptr});
+      }
+      continue;
+    }
+    if (st.gemm.empty()) continue;
+    const bool second = st.gemm[0].Cin.kind != Ref::NONE;  // X = K - L Z
+    // distinct A operands
+    std::map<std::pair<int, int>, int> aslab;
+    std::vector<const GemmOp*> afirst;
+    for (const GemmOp& g : st.gemm) {
+      auto key = std::make_pair(g.A.kind == Ref::SLOT ? g.A.slot : -1 - g.A.r, g.A.c);
+      if (aslab.emplace(key, (int)afirst.size()).second) afirst.push_back(&g);
+    }
+    {
+      const size_t o = take(afirst.size() * sizeof(tc::PackDesc));
+      tc::PackDesc* pd = (tc::PackDesc*)(hbase + o);
+      for (size_t t = 0; t < afirst.size(); ++t) {
+        int64_t ld;
+        int dt;
+        const void* p = resolve(c, afirst[t]->A, X, &ld, &dt);
+        pd[t] = tc::PackDesc{p, ld, b, b, dt == F64 ? 1 : 0, 0, (int)t};
+      }
+      L.push_back({1, o, (int)afirst.size(), 0, 0, 0, 0, (__nv_bfloat16*)c->apk.p, nullptr});
+    }
+    if (!second) {
+      // B = R^T slices, one slab per product
+      const size_t o = take(st.gemm.size() * sizeof(tc::PackDesc));
+      tc::PackDesc* pd = (tc::PackDesc*)(hbase + o);
+      for (size_t t = 0; t < st.gemm.size(); ++t) {
+        int64_t ld;
+        int dt;
+        const void* p = resolve(c, st.gemm[t].B, X, &ld, &dt);
+        pd[t] = tc::PackDesc{p, ld, b, b, dt == F64 ? 1 : 0, 1, (int)t};
+      }
+      L.push_back({2, o, (int)st.gemm.size(), 0, 0, 0, 0, (__nv_bfloat16*)c->bpk.p, nullptr});
+    }
+    const size_t o = take(st.gemm.size() * sizeof(tc::TcProblem));
+    tc::TcProblem* pr = (tc::TcProblem*)(hbase + o);
+    for (size_t t = 0; t < st.gemm.size(); ++t) {
+      const GemmOp& g = st.gemm[t];
+      tc::TcProblem q{};
+      q.a_slab = aslab[std::make_pair(g.A.kind == Ref::SLOT ? g.A.slot : -1 - g.A.r, g.A.c)];
+      if (!second) {
+        q.b_slab = (int)t;
+        q.out_slab = (int)t;
+        zslab[g.C.slot] = (int)t;
+      } else {
+        auto it = zslab.find(g.B.slot);
+        if (g.B.kind != Ref::SLOT || it == zslab.end()) return MBINV_ENOTSUP;
+        q.b_slab = it->second;
+        int64_t ld;
+        int dt;
+        q.cin = resolve(c, g.Cin, X, &ld, &dt);
+        q.ldcin = ld;
+        q.cin_f64 = dt == F64 ? 1 : 0;
+        q.out = (void*)resolve(c, g.C, X, &ld, &dt);
+        q.ldo = ld;
+        if (dt != F32) return MBINV_ENOTSUP;
+      }
+      pr[t] = q;
+    }
+    Launch l{3, o, (int)st.gemm.size(), 0, 0, (int)afirst.size(), second ? 0 : 1, (__nv_bfloat16*)c->apk.p,
+             (__nv_bfloat16*)(second ? c->b2pk.p : c->bpk.p)};
+    L.push_back(l);
+  }
+  if (off + 2 * sizeof(DevStatus) > need) return MBINV_ENOTSUP;
+  CU(cudaMemcpyAsync(dbase, hbase, off, cudaMemcpyHostToDevice, c->stream));
+  DevStatus* hst = (DevStatus*)(hbase + need - sizeof(DevStatus) * 2);
+  hst[0] = DevStatus{0, INT_MAX};
+  CU(cudaMemcpyAsync(c->status.p, &hst[0], sizeof(DevStatus), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), c->stream));
+  const bool prof = c->opt.profile != 0;
+  if (prof) CU(ensure_events(c, 2 * L.size()));
+  tc::TcParams P{};
+  P.m = P.n = b;
+  P.kpad = kpad;
+  P.tiles_m = P.tiles_n = rpad / T;
+  P.S = NS;
+  tc::pair_table(NS, &P.npairs, P.pa, P.pb);
+  P.orows = rpad;
+  P.okpad = kpad;
+  P.opk = (__nv_bfloat16*)c->b2pk.p;
+  P.err = (int*)c->tcerr.p;
+  for (size_t q = 0; q < L.size(); ++q) {
+    const Launch& l = L[q];
+    if (prof) CU(cudaEventRecord(c->events[2 * q], c->stream));
+    switch (l.kind) {
+      case 0:
+        CU(run_inverse_batch(l.in_dt, l.out_dt, F64, (const InvDesc*)(dbase + l.off), l.count, b,
+                             (DevStatus*)c->status.p, c->stream, &X.launches));
+        break;
+      case 1:
+      case 2:
+        CU(tc::launch_pack((const tc::PackDesc*)(dbase + l.off), l.count, NS, rpad, kpad, l.adst, c->stream));
+        ++X.launches;
+        break;
+      case 3: {
+        P.mode = l.mode;
+        P.alpha = l.mode == 0 ? -1.f : 1.f;
+        P.beta = 1.f;
+        CU(tc::launch_gemm(l.adst, l.nA, rpad, l.bsrc, l.count, rpad, P, (const tc::TcProblem*)(dbase + l.off),
+                           l.count, c->stream));
+        ++X.launches;
+        ++X.gemm_launches;
+        break;
+      }
+    }
+    if (prof) CU(cudaEventRecord(c->events[2 * q + 1], c->stream));
+  }
+  int* herr = (int*)&hst[1].tag;  // reuse the pinned words
+  CU(cudaMemcpyAsync(&hst[1], c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const DevStatus st = hst[1];
+  CU(cudaMemcpyAsync(herr, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (*herr) return MBINV_ETIMEOUT;
+  if (prof) {
+    for (size_t q = 0; q < L.size(); ++q) {
+      float ms = 0;
+      CU(cudaEventElapsedTime(&ms, c->events[2 * q], c->events[2 * q + 1]));
+      if (L[q].kind == 0) X.inv_dev_s += ms * 1e-3;
+      else if (L[q].kind == 3) X.gemm_dev_s += ms * 1e-3;
+      else X.pack_dev_s += ms * 1e-3;
+    }
+  }
+  if (st.singular) return MBINV_ESINGULAR;
+  return MBINV_OK;
+}
+
 mbinv_status prepare_border(mbinv_ctx* c, int64_t i, int64_t j) {
   if (c->l == 0) return MBINV_OK;
   int mode = 0;
@@ -467,7 +698,7 @@ mbinv_status block_to_device(mbinv_ctx* c, int64_t i, int64_t j, void* dst, int6
   s = ensure_workspace(c, S, ic);
   if (s != MBINV_OK) return s;
   Exec X{c, &S, dst, ldd, c->dtype, ic};
-  s = run_schedule(X);
+  s = c->opt.precision == MBINV_MIXED_BF16 ? run_schedule_mixed(X) : run_schedule(X);
   auto t1 = std::chrono::steady_clock::now();
   fill_report(rep, c, S, X, std::chrono::duration<double>(t1 - t0).count(), c->own_bytes);
   return s;
@@ -490,6 +721,9 @@ mbinv_status copy_out(mbinv_ctx* c, const void* src, int64_t lds, void* out, int
 }  // namespace
 
 // ====================================================================== ABI
+
+extern "C" mbinv_status mbinv_refined_block_internal(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo,
+                                                     mbinv_report* rep);
 
 extern "C" {
 
@@ -607,7 +841,8 @@ void mbinv_destroy(mbinv_ctx* c) {
   else cudaDeviceSynchronize();
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   for (DevBuf* d : {&c->own_M, &c->slots, &c->inv_work, &c->inv_wrow, &c->inv_perm, &c->inv_amax, &c->desc,
-                    &c->status, &c->outtmp, &c->rowbuf, &c->colbuf, &c->resid})
+                    &c->status, &c->outtmp, &c->rowbuf, &c->colbuf, &c->resid, &c->apk, &c->bpk, &c->b2pk,
+                    &c->tcerr})
     d->release();
   c->hdesc.release();
   c->hstage.release();
@@ -622,7 +857,14 @@ mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t 
     std::memset(rep, 0, sizeof *rep);
     rep->failed_pivot = -1;
   }
-  if (c->opt.precision == MBINV_MIXED_BF16) return MBINV_ENOTSUP;
+  if (c->opt.precision == MBINV_MIXED_BF16 && c->opt.refine_steps > 0 && !c->in_sweep) {
+    auto t0 = std::chrono::steady_clock::now();
+    c->in_sweep = true;
+    mbinv_status r = mbinv_refined_block_internal(c, i, j, out, ldo, rep);
+    c->in_sweep = false;
+    if (rep) rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return r;
+  }
   const bool out_dev = is_device_ptr(out);
   mbinv_status s;
   if (out_dev && bi == c->b && bj == c->b) {
@@ -838,3 +1080,85 @@ mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem* probs, int dtype
 }
 
 }  // extern "C"
+
+namespace {
+
+// Mixed path with one two-sided refinement step:
+//   X_i = block row i, Y_j = block column j of M^-1 from the mixed sweep,
+//   R   = E_i^T - X_i M                      (FP64 accumulation)
+//   N_ij <- X_i E_j + R Y_j                  (FP64)
+// With dX, dY the errors of X_i, Y_j the result differs from N_ij by
+// -dX M dY: the error is squared when it is small.
+mbinv_status refined_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
+  const int64_t n = c->n, b = c->b;
+  const int64_t bi = block_extent(c, i), bj = block_extent(c, j);
+  // sweeps in FP32, straight into device buffers
+  CU(c->rowbuf.ensure((size_t)b * n * 4 + 256));
+  CU(c->colbuf.ensure((size_t)n * b * 4 + 256));
+  CU(c->resid.ensure((size_t)b * n * 8 + (size_t)b * b * 8 + 512));
+  const int saved_dtype = c->dtype;
+  c->dtype = F32;  // the sweeps write FP32 blocks
+  mbinv_report r1{}, r2{};
+  mbinv_status s = mbinv_block_row(c, i, c->rowbuf.p, n, &r1);
+  if (s == MBINV_OK) s = mbinv_block_col(c, j, c->colbuf.p, b, &r2);
+  c->dtype = saved_dtype;
+  if (s != MBINV_OK) return s;
+  double* R = (double*)c->resid.p;                      // bi x n
+  double* Nij = R + (size_t)b * n;                      // bi x bj
+  double* acc = Nij + (size_t)b * b;
+  const int cm = c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64;
+  // R = -X_i M, then + E_i^T
+  s = gemm1(c, cm, c->rowbuf.p, n, 0, c->dM, c->ldm, 0, nullptr, 0, R, n, (int)bi, (int)n, (int)n, -1.0, 0.0);
+  if (s != MBINV_OK) return s;
+  add_eye_kernel<<<(unsigned)((bi + 255) / 256), 256, 0, c->stream>>>(R, n, i * b, bi);
+  CU(cudaGetLastError());
+  CU(cudaMemsetAsync(acc, 0, sizeof(double), c->stream));
+  sumsq_kernel<<<64, 256, 0, c->stream>>>(R, n, bi, n, acc);
+  CU(cudaGetLastError());
+  // N_ij = X_i E_j (FP32 -> FP64) + R Y_j
+  convert_kernel<float, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+      (const float*)c->rowbuf.p + j * b, n, Nij, bj, bi, bj);
+  CU(cudaGetLastError());
+  s = gemm1(c, G_F64F32_F64, R, n, 0, c->colbuf.p, b, 0, Nij, bj, Nij, bj, (int)bi, (int)bj, (int)n, 1.0, 1.0);
+  if (s != MBINV_OK) return s;
+  double hacc = 0;
+  CU(cudaMemcpyAsync(&hacc, acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  // write out in the caller's dtype and memory
+  const bool out_dev = is_device_ptr(out);
+  const size_t es = dtype_size(c->dtype);
+  if (c->dtype == F64) {
+    CU(cudaMemcpy2DAsync(out, (size_t)ldo * es, Nij, (size_t)bj * 8, (size_t)bj * 8, (size_t)bi,
+                         out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    CU(c->outtmp.ensure((size_t)b * b * 8 + 256));
+    convert_kernel<double, float><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+        Nij, bj, (float*)c->outtmp.p, bj, bi, bj);
+    CU(cudaGetLastError());
+    CU(cudaMemcpy2DAsync(out, (size_t)ldo * es, c->outtmp.p, (size_t)bj * 4, (size_t)bj * 4, (size_t)bi,
+                         out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  if (rep) {
+    rep->gemm_flops = r1.gemm_flops + r2.gemm_flops + 2.0 * bi * n * n + 2.0 * bi * bj * n;
+    rep->inv_flops = r1.inv_flops + r2.inv_flops;
+    rep->frames = r1.frames + r2.frames;
+    rep->inversions = r1.inversions + r2.inversions;
+    rep->launches = r1.launches + r2.launches + 5;
+    rep->gemm_launches = r1.gemm_launches + r2.gemm_launches;
+    rep->gemm_device_seconds = r1.gemm_device_seconds + r2.gemm_device_seconds;
+    rep->inv_device_seconds = r1.inv_device_seconds + r2.inv_device_seconds;
+    rep->peak_device_bytes = std::max(r1.peak_device_bytes, r2.peak_device_bytes) + c->rowbuf.bytes +
+                             c->colbuf.bytes + c->resid.bytes;
+    rep->rel_residual = std::sqrt(hacc / (double)bi);
+  }
+  if (!(std::sqrt(hacc / (double)bi) < 1.0)) return MBINV_ENOTCONV;
+  return MBINV_OK;
+}
+
+}  // namespace
+
+extern "C" mbinv_status mbinv_refined_block_internal(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo,
+                                                     mbinv_report* rep) {
+  return refined_block(c, i, j, out, ldo, rep);
+}

@@ -64,6 +64,7 @@ cudaError_t launch_gemm_grouped(int combo, const GemmDesc* d_descs, int ndesc, i
     case G_F32: gemm_grouped_kernel<float, float, float, float><<<total_tiles, 256, 0, s>>>(d_descs, ndesc); break;
     case G_F32IN_F64: gemm_grouped_kernel<float, float, double, double><<<total_tiles, 256, 0, s>>>(d_descs, ndesc); break;
     case G_F64F32_F64: gemm_grouped_kernel<double, float, double, double><<<total_tiles, 256, 0, s>>>(d_descs, ndesc); break;
+    case G_F32F64_F64: gemm_grouped_kernel<float, double, double, double><<<total_tiles, 256, 0, s>>>(d_descs, ndesc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -90,7 +90,8 @@ enum GemmCombo : int {
   G_F64 = 0,       // double x double -> double, FP64 accumulate
   G_F32 = 1,       // float x float -> float, FP32 accumulate
   G_F32IN_F64 = 2, // float x float -> double, FP64 accumulate
-  G_F64F32_F64 = 3 // double x float -> double, FP64 accumulate
+  G_F64F32_F64 = 3, // double x float -> double, FP64 accumulate
+  G_F32F64_F64 = 4  // float x double -> double, FP64 accumulate
 };
 void gemm_tile_shape(int combo, int* bm, int* bn);
 cudaError_t launch_gemm_grouped(int combo, const GemmDesc* d_descs, int ndesc, int total_tiles, cudaStream_t s);
