@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
+    p.add_argument("--slices", type=int, default=3)
+    p.add_argument("--refine", type=int, default=0)
     return p.parse_args()
 
 
@@ -169,10 +171,10 @@ def main():
     b = -(-n // k)
     bps = args.blocks_per_step
     m_host = bi.uniform_shift(n, 0)
-    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    dt = torch.float64 if (args.precision == "fp64" or args.refine) else torch.float32
     M = torch.tensor(m_host, dtype=dt, device="cuda")
     stream = torch.cuda.current_stream()
-    ctx = mb.Context(M, k, precision=args.precision, profile=True)
+    ctx = mb.Context(M, k, precision=args.precision, profile=True, slices=args.slices, refine=args.refine)
     outs = [torch.empty((b, b), dtype=dt, device="cuda") for _ in range(bps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     # each rank takes its own slice of the block sequence (replicas, no collective)
@@ -224,34 +226,41 @@ def main():
         errs.append(float(torch.linalg.norm(outs[q].double() - r) / torch.linalg.norm(r)))
     del inv_ref
 
-    # roofline of the dominant kernel family
+    # roofline of each kernel family; the dominant one (most device time) heads the line
     pk, pk_src = peaks()
-    if agg["gemm_device_seconds"] >= agg["inv_device_seconds"]:
-        kern, flops, dsec, nl = "gemm_grouped (Schur products)", agg["gemm_flops"], agg["gemm_device_seconds"], \
-            agg["gemm_launches"]
+    npairs = {1: 1, 2: 3, 3: 6}[args.slices] if args.precision == "mixed" else 1
+    alu = {"fp64": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
+           "fp32": (FP32_NOMINAL_GFLOPS / 1e3, "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+           "mixed": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)")}[args.precision]
+    fams = {}
+    if args.precision == "mixed":
+        fams["tc_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * npairs,
+                                  "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
+                                  "peak": pk["bf16_tflops_sustained"],
+                                  "peak_source": f"bf16_tflops_sustained ({pk_src}), executed BF16 slice products"}
     else:
-        kern, flops, dsec, nl = "gauss-jordan inverse batches", agg["inv_flops"], agg["inv_device_seconds"], \
-            agg["inversions"]
-    achieved = flops / dsec / 1e12 if dsec > 0 else 0.0
-    if args.precision == "fp64":
-        peak, bound, unit, psrc = FP64_NOMINAL_GFLOPS / 1e3, "alu", "TFLOP/s", "nominal FP64 1.25 TFLOP/s"
-    elif args.precision == "fp32":
-        peak, bound, unit, psrc = FP32_NOMINAL_GFLOPS / 1e3, "alu", "TFLOP/s", \
-            "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-    else:
-        peak, bound, unit, psrc = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s", \
-            f"bf16_tflops_sustained ({pk_src})"
-    roofline = {"bound": bound, "kernel": kern, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak if peak else None, "traffic": None, "peak_source": psrc,
-                "launches": nl, "device_seconds": dsec,
-                "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12}
+        fams["gemm_grouped_kernel"] = {"bound": "alu", "work": agg["gemm_flops"], "dsec": agg["gemm_device_seconds"],
+                                       "launches": agg["gemm_launches"], "peak": alu[0], "peak_source": alu[1]}
+    fams["gauss_jordan_inverse"] = {"bound": "alu", "work": agg["inv_flops"], "dsec": agg["inv_device_seconds"],
+                                    "launches": agg["inversions"], "peak": alu[0] if args.precision != "fp32"
+                                    else FP32_NOMINAL_GFLOPS / 1e3, "peak_source": alu[1]}
+    kernels = {}
+    for name, f in fams.items():
+        ach = f["work"] / f["dsec"] / 1e12 if f["dsec"] > 0 else 0.0
+        kernels[name] = {"bound": f["bound"], "achieved": ach, "peak": f["peak"], "unit": "TFLOP/s",
+                         "frac": ach / f["peak"], "device_seconds": f["dsec"], "peak_source": f["peak_source"]}
+    dom = max(kernels, key=lambda k: kernels[k]["device_seconds"])
+    roofline = dict(kernels[dom])
+    roofline.update({"kernel": dom, "traffic": None, "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
+                     "families": kernels})
 
     line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3/f32"}[
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[
                 args.precision], "data": "synthetic",
             "config": {"workload": f"n={n} k={k} b={b} uniform[-1,1)+nI, blocks one at a time ({args.precision})",
-                       "blocks_per_step": bps, "precision": args.precision,
+                       "blocks_per_step": bps, "precision": args.precision, "slices": args.slices,
+                       "refine": args.refine,
                        "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",
                        "max_rel_err_vs_dense_inverse": max(errs)},
             "roofline": roofline, "gpu_launches": agg["launches"],
@@ -266,7 +275,7 @@ def main():
         t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 2))
         for s in range(e2e_steps):
-            with mb.Context(mh, k, precision=args.precision) as hc:
+            with mb.Context(mh, k, precision=args.precision, slices=args.slices, refine=args.refine) as hc:
                 for q, (i, j) in enumerate(block_list(k, s * bps, bps)):
                     hc.block(i, j, out=houts[q])
         torch.cuda.synchronize()
