@@ -174,6 +174,32 @@ mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem *probs, int dtype
 
 void mbinv_destroy(mbinv_ctx *ctx);
 
+/* Largest order accepted by mbinv_invert_noalloc. */
+#define MBINV_NOALLOC_MAX_B 512
+
+/* X = A^-1 for one b x b matrix, by the same pivoted Gauss-Jordan kernels the
+ * recursion uses for its pivots (FP64 arithmetic), for callers that cannot
+ * allocate device memory when they call: for instance code running while a
+ * framework's caching allocator holds nearly all of the GPU's memory, or code
+ * that must not pay the device-wide synchronisation of cudaFree.  The paper
+ * has no counterpart; this is an entry point of the library only.
+ *   A, X:   device pointers, row-major, leading dimensions lda, ldx >= b,
+ *           dtype MBINV_DTYPE_F64 or MBINV_DTYPE_F32 (both the same).
+ *   b:      1 <= b <= MBINV_NOALLOC_MAX_B; anything else returns
+ *           MBINV_EINVAL before any launch.
+ *   stream: cudaStream_t (NULL = default stream); the call returns once the
+ *           result is written.
+ * Returns MBINV_ESINGULAR when a pivot is singular to working precision.
+ * All scratch (about 2.2 MB) is one fixed device array per GPU, held from the
+ * library's load until the process exits; no cudaMalloc, cudaFree or other
+ * allocating routine is called.  Every call on a device shares that array and
+ * overwrites what it uses, so calls whose GPU work overlaps (two threads or
+ * two streams) race: serialise them.  The first call on a device looks up the
+ * array's device address with that device current; make it before any stream
+ * capture. */
+mbinv_status mbinv_invert_noalloc(const void *A, int64_t lda, void *X, int64_t ldx, int64_t b, int dtype,
+                                  void *stream);
+
 const char *mbinv_status_string(mbinv_status s);
 
 /* Library version string. */

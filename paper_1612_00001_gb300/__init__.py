@@ -79,6 +79,8 @@ SIGNATURES = {
     "mbinv_batched_blocks": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Problem), ctypes.c_int,
                                             ctypes.POINTER(Options), ctypes.POINTER(Report)]),
     "mbinv_destroy": (None, [ctypes.c_void_p]),
+    "mbinv_invert_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
     "mbinv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbinv_version": (ctypes.c_char_p, []),
     "mbinv_last_cuda_error": (ctypes.c_char_p, []),
