@@ -29,6 +29,8 @@
 #include "mbinv_internal.h"
 #include "tile_gemm.cuh"
 
+#include <cooperative_groups.h>
+
 namespace mbinv {
 
 namespace {
@@ -77,42 +79,51 @@ __global__ void gj_init_kernel(const InvDesc* __restrict__ descs, int in_dtype) 
   if ((threadIdx.x & 31) == 0) atomicMax(d.amax, (unsigned long long)__double_as_longlong(m));
 }
 
-// One CTA per matrix: factor the panel [p, p + nb) (see the file comment).
-template <typename TW, bool SMEM>
+// A cluster of CL CTAs per matrix factors the panel [p, p + nb) (see the file
+// comment).  CTA q of the cluster keeps rows [q R, (q+1) R) of the panel in
+// its shared memory (R = ceil(b / CL)); the CTAs exchange pivot candidates
+// and the pivot row through distributed shared memory, so that the
+// per-column work (the elimination of nb columns from every row) is spread
+// over CL SMs instead of one.  Every CTA takes the same pivot decision.
+template <typename TW>
 __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* __restrict__ descs, int p, int nb,
                                                                  DevStatus* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const InvDesc d = descs[blockIdx.x];
+  const int CL = (int)cluster.num_blocks();
+  const int q = (int)cluster.block_rank();
+  const InvDesc d = descs[blockIdx.x / CL];
   const int b = d.b;
-  TW* X = (TW*)d.work;
-  TW* P;          // panel: P[i * ldp + t] is X[i][p + t]
-  int64_t ldp;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kPanelThreads / 32;
+  const int R = (b + CL - 1) / CL;
+  const int r0 = min(b, q * R), r1 = min(b, r0 + R);
+  const int ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
+  TW* P = (TW*)smem_raw;   // P[(i - r0) * ldp + t] is X[i][p + t]
+  TW* prow = P + (size_t)R * ldp;       // pivot row before scaling (nb)
+  TW* srow = prow + ldp;                // scaled pivot row (nb)
+  TW* jrow = srow + ldp;                // old row j, for the owner of row r (nb)
+  __shared__ TW cand_v[2];
+  __shared__ int cand_i[2];
   __shared__ TW red_v[kPanelThreads / 32];
   __shared__ int red_i[kPanelThreads / 32];
-  __shared__ int piv_row;
-  if (SMEM) {
-    P = (TW*)smem_raw;
-    ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
-    for (int64_t e = tid; e < (int64_t)b * nb; e += kPanelThreads) {
-      const int64_t i = e / nb, t = e % nb;
-      P[i * ldp + t] = X[i * b + p + t];
-    }
-  } else {
-    P = X + p;
-    ldp = b;
+  TW* X = (TW*)d.work;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kPanelThreads / 32;
+  for (int e = tid; e < (r1 - r0) * nb; e += kPanelThreads) {
+    const int i = e / nb, t = e % nb;
+    P[i * ldp + t] = X[(int64_t)(r0 + i) * b + p + t];
   }
   const double amax = __longlong_as_double((long long)*d.amax);
   const TW tol = (TW)((double)b * (double)eps_of<TW>() * amax);
-  __syncthreads();
+  cluster.sync();
 
   for (int t = 0; t < nb; ++t) {
     const int j = p + t;
-    // ---- pivot search: first row of largest magnitude in column j, rows >= j
+    const int buf = t & 1;
+    // ---- local pivot candidate: first row of largest magnitude, rows >= j
     TW best = (TW)-1;
     int bi = b;
-    for (int i = j + tid; i < b; i += kPanelThreads) {
-      const TW v = fabs(P[(int64_t)i * ldp + t]);
+    for (int i = max(j, r0) + tid; i < r1; i += kPanelThreads) {
+      const TW v = fabs(P[(i - r0) * ldp + t]);
       if (v > best) { best = v; bi = i; }  // NaN never wins
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -127,71 +138,93 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
       int bix = red_i[0];
       for (int w = 1; w < nwarps; ++w)
         if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bix)) { bv = red_v[w]; bix = red_i[w]; }
-      if (bix >= b) bix = j;  // every candidate NaN or column exhausted
-      if (!(bv > tol) || !isfinite((double)bv)) {
+      cand_v[buf] = bv;
+      cand_i[buf] = bix;
+    }
+    cluster.sync();  // candidates of every CTA visible
+    // ---- global pivot: the same decision in every CTA
+    TW gv = (TW)-1;
+    int r = b;
+    for (int c = 0; c < CL; ++c) {
+      const TW v = *cluster.map_shared_rank(&cand_v[buf], c);
+      const int ix = *cluster.map_shared_rank(&cand_i[buf], c);
+      if (v > gv || (v == gv && ix < r)) { gv = v; r = ix; }
+    }
+    if (r >= b) r = j;  // every candidate NaN
+    if (q == 0 && tid == 0) {
+      if (!(gv > tol) || !isfinite((double)gv)) {
         atomicExch(&status->singular, 1);
         atomicMin(&status->tag, d.tag);
       }
-      piv_row = bix;
-      d.perm[j] = bix;
+      d.perm[j] = r;
     }
-    __syncthreads();
-    const int r = piv_row;
-    // ---- exchange whole rows j and r
-    if (r != j) {
-      for (int c = tid; c < nb; c += kPanelThreads) {
-        const TW a = P[(int64_t)j * ldp + c];
-        P[(int64_t)j * ldp + c] = P[(int64_t)r * ldp + c];
-        P[(int64_t)r * ldp + c] = a;
+    const int oj = j / R, orr = r / R;  // owners of rows j and r
+    // ---- read the pivot row (old row r) and, for the owner of r, old row j
+    {
+      const TW* src = cluster.map_shared_rank(P, orr) + (size_t)(r - orr * R) * ldp;
+      for (int c = tid; c < nb; c += kPanelThreads) prow[c] = src[c];
+      if (q == orr && r != j) {
+        const TW* sj = cluster.map_shared_rank(P, oj) + (size_t)(j - oj * R) * ldp;
+        for (int c = tid; c < nb; c += kPanelThreads) jrow[c] = sj[c];
       }
-      for (int c = tid; c < b - nb; c += kPanelThreads) {
-        const int cc = c < p ? c : c + nb;  // columns outside the panel
+    }
+    // exchange rows j and r of the columns outside the panel (global memory),
+    // each CTA its share of those columns
+    if (r != j) {
+      const int nrest = b - nb;
+      const int per = (nrest + CL - 1) / CL;
+      const int c0 = q * per, c1 = min(nrest, c0 + per);
+      for (int c = c0 + tid; c < c1; c += kPanelThreads) {
+        const int cc = c < p ? c : c + nb;
         const TW a = X[(int64_t)j * b + cc];
         X[(int64_t)j * b + cc] = X[(int64_t)r * b + cc];
         X[(int64_t)r * b + cc] = a;
       }
     }
+    cluster.sync();  // every CTA has read rows j and r
+    // ---- scaled pivot row; the owners write the exchanged rows
+    const TW piv = prow[t];
+    for (int c = tid; c < nb; c += kPanelThreads) srow[c] = ((c == t) ? (TW)1 : prow[c]) / piv;
     __syncthreads();
-    // ---- scale the pivot row (panel columns)
-    const TW piv = P[(int64_t)j * ldp + t];
+    if (q == oj)
+      for (int c = tid; c < nb; c += kPanelThreads) P[(size_t)(j - r0) * ldp + c] = srow[c];
+    if (q == orr && r != j)
+      for (int c = tid; c < nb; c += kPanelThreads) P[(size_t)(r - r0) * ldp + c] = jrow[c];
     __syncthreads();
-    for (int c = tid; c < nb; c += kPanelThreads) {
-      const TW v = (c == t) ? (TW)1 : P[(int64_t)j * ldp + c];
-      P[(int64_t)j * ldp + c] = v / piv;
-    }
-    __syncthreads();
-    // ---- eliminate column j from every other row (warp per row, lane per column)
-    for (int i = warp; i < b; i += nwarps) {
+    // ---- eliminate column j from the CTA's rows (warp per row, lane per column)
+    for (int i = r0 + warp; i < r1; i += nwarps) {
       if (i == j) continue;
-      TW* xi = P + (int64_t)i * ldp;
+      TW* xi = P + (size_t)(i - r0) * ldp;
       const TW f = xi[t];
       __syncwarp();
       if (f != (TW)0) {
-        const TW* xj = P + (int64_t)j * ldp;
         for (int c = lane; c < nb; c += 32) {
           const TW base = (c == t) ? (TW)0 : xi[c];
-          xi[c] = base - f * xj[c];
+          xi[c] = base - f * srow[c];
         }
       }
       __syncwarp();
     }
     __syncthreads();
   }
-
-  if (SMEM) {
-    for (int64_t e = tid; e < (int64_t)b * nb; e += kPanelThreads) {
-      const int64_t i = e / nb, t = e % nb;
-      X[i * b + p + t] = P[i * ldp + t];
-    }
+  // panel back to global memory
+  for (int e = tid; e < (r1 - r0) * nb; e += kPanelThreads) {
+    const int i = e / nb, t = e % nb;
+    X[(int64_t)(r0 + i) * b + p + t] = P[i * ldp + t];
   }
+  cluster.sync();  // every row exchange of the other columns is done
   // W = X[J, :] (the trailing update reads the pivot rows of the other columns)
   if (nb < b) {
     TW* W = (TW*)d.wrow;
-    for (int64_t e = tid; e < (int64_t)nb * b; e += kPanelThreads) {
-      const int64_t t = e / b, c = e % b;
-      W[e] = X[(int64_t)(p + t) * b + c];
+    const int64_t tot = (int64_t)nb * b;
+    const int64_t per = (tot + CL - 1) / CL;
+    const int64_t e0 = q * per, e1 = min(tot, e0 + per);
+    for (int64_t e = e0 + tid; e < e1; e += kPanelThreads) {
+      const int64_t tt = e / b, c = e % b;
+      W[e] = X[(int64_t)(p + tt) * b + c];
     }
   }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // X[:, rest] = T[:, J] * W[:, rest] + (rows of J ? 0 : X[:, rest]).
@@ -271,20 +304,34 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     ++nl;
   }
   const int nb = inv_panel_width(b, sizeof(TW) == 8 ? F64 : F32);
-  const size_t psmem = (size_t)b * (nb + 1) * sizeof(TW);
-  const bool use_smem = psmem <= (size_t)kSmemLimit;
+  // cluster size: spread the panel over more SMs when few matrices are batched
+  int CL = 8;
+  while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
+  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
+  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW);
+  if (psmem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   for (int p = 0; p < b; p += nb) {
     const int w = std::min(nb, b - p);
-    if (use_smem) {
-      static bool attr_set = false;
-      if (!attr_set) {
-        cudaFuncSetAttribute(gj_panel_kernel<TW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-        attr_set = true;
-      }
-      gj_panel_kernel<TW, true><<<count, kPanelThreads, (size_t)b * (w + 1) * sizeof(TW), s>>>(d_desc, p, w, d_status);
-    } else {
-      gj_panel_kernel<TW, false><<<count, kPanelThreads, 0, s>>>(d_desc, p, w, d_status);
-    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(count * CL, 1, 1);
+    cfg.blockDim = dim3(kPanelThreads, 1, 1);
+    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 3) * (w + 1) * sizeof(TW);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status);
+    if (e != cudaSuccess) return e;
     ++nl;
     if (w < b) {
       using Cfg = TileCfg<TW>;
