@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   __shared__ int cand_i[2];
   __shared__ TW red_v[kPanelThreads / 32];
   __shared__ int red_i[kPanelThreads / 32];
+  int* piv_hist = (int*)(jrow + ldp);   // pivot row of every column of the panel (nb)
   TW* X = (TW*)d.work;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kPanelThreads / 32;
   for (int e = tid; e < (r1 - r0) * nb; e += kPanelThreads) {
@@ -142,22 +143,33 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
       cand_i[buf] = bix;
     }
     cluster.sync();  // candidates of every CTA visible
-    // ---- global pivot: the same decision in every CTA
-    TW gv = (TW)-1;
-    int r = b;
-    for (int c = 0; c < CL; ++c) {
-      const TW v = *cluster.map_shared_rank(&cand_v[buf], c);
-      const int ix = *cluster.map_shared_rank(&cand_i[buf], c);
-      if (v > gv || (v == gv && ix < r)) { gv = v; r = ix; }
-    }
-    if (r >= b) r = j;  // every candidate NaN
-    if (q == 0 && tid == 0) {
-      if (!(gv > tol) || !isfinite((double)gv)) {
-        atomicExch(&status->singular, 1);
-        atomicMin(&status->tag, d.tag);
+    // ---- global pivot: the same decision in every CTA (one remote load per rank)
+    if (warp == 0) {
+      TW v = (TW)-1;
+      int ix = b;
+      if (lane < CL) {
+        v = *cluster.map_shared_rank(&cand_v[buf], lane);
+        ix = *cluster.map_shared_rank(&cand_i[buf], lane);
       }
-      d.perm[j] = r;
+      for (int o = 16; o > 0; o >>= 1) {
+        const TW ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
+      }
+      if (lane == 0) {
+        if (ix >= b) ix = j;  // every candidate NaN
+        piv_hist[t] = ix;
+        if (q == 0) {
+          if (!(v > tol) || !isfinite((double)v)) {
+            atomicExch(&status->singular, 1);
+            atomicMin(&status->tag, d.tag);
+          }
+          d.perm[j] = ix;
+        }
+      }
     }
+    __syncthreads();
+    const int r = piv_hist[t];
     const int oj = j / R, orr = r / R;  // owners of rows j and r
     // ---- read the pivot row (old row r) and, for the owner of r, old row j
     {
@@ -166,19 +178,6 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
       if (q == orr && r != j) {
         const TW* sj = cluster.map_shared_rank(P, oj) + (size_t)(j - oj * R) * ldp;
         for (int c = tid; c < nb; c += kPanelThreads) jrow[c] = sj[c];
-      }
-    }
-    // exchange rows j and r of the columns outside the panel (global memory),
-    // each CTA its share of those columns
-    if (r != j) {
-      const int nrest = b - nb;
-      const int per = (nrest + CL - 1) / CL;
-      const int c0 = q * per, c1 = min(nrest, c0 + per);
-      for (int c = c0 + tid; c < c1; c += kPanelThreads) {
-        const int cc = c < p ? c : c + nb;
-        const TW a = X[(int64_t)j * b + cc];
-        X[(int64_t)j * b + cc] = X[(int64_t)r * b + cc];
-        X[(int64_t)r * b + cc] = a;
       }
     }
     cluster.sync();  // every CTA has read rows j and r
@@ -211,6 +210,24 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   for (int e = tid; e < (r1 - r0) * nb; e += kPanelThreads) {
     const int i = e / nb, t = e % nb;
     X[(int64_t)(r0 + i) * b + p + t] = P[i * ldp + t];
+  }
+  // the row exchanges of the panel, in order, on the columns outside it (each
+  // CTA its share of those columns; they are not read during the panel)
+  {
+    const int nrest = b - nb;
+    const int per = (nrest + CL - 1) / CL;
+    const int c0 = q * per, c1 = min(nrest, c0 + per);
+    for (int c = c0 + tid; c < c1; c += kPanelThreads) {
+      const int cc = c < p ? c : c + nb;
+      for (int t = 0; t < nb; ++t) {
+        const int j = p + t, r = piv_hist[t];
+        if (r != j) {
+          const TW a = X[(int64_t)j * b + cc];
+          X[(int64_t)j * b + cc] = X[(int64_t)r * b + cc];
+          X[(int64_t)r * b + cc] = a;
+        }
+      }
+    }
   }
   cluster.sync();  // every row exchange of the other columns is done
   // W = X[J, :] (the trailing update reads the pivot rows of the other columns)
@@ -307,8 +324,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   // cluster size: spread the panel over more SMs when few matrices are batched
   int CL = 8;
   while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
-  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
-  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW);
+  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
+  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW);
   if (psmem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
@@ -321,7 +338,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * CL, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
-    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 3) * (w + 1) * sizeof(TW);
+    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -34,7 +34,7 @@ namespace tc {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int THREADS = 128;
 constexpr uint32_t TILE_A_BYTES = BM * BK * 2;  // 16 KB
 constexpr uint32_t TILE_B_BYTES = BN * BK * 2;  // 16 KB
