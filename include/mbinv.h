@@ -141,15 +141,26 @@ mbinv_status mbinv_create(mbinv_ctx **out, int64_t n, int64_t k, int dtype, cons
  * X_i E_j + (E_i^T - X_i M) Y_j, the residual taken in FP64. */
 mbinv_status mbinv_block(mbinv_ctx *ctx, int64_t i, int64_t j, void *out, int64_t ldo, mbinv_report *report);
 
-/* All blocks of M^-1 by k^2 independent runs (Sec. 5).  out is n x n with
- * leading dimension ldo (host or device).  done (may be NULL) is a k*k
- * row-major bitmap of blocks to skip; cb (may be NULL) is called after each
- * finished block, so a caller can checkpoint and resume. */
+/* Several blocks of M^-1, each by its own run of the recursion (Sec. 3.1-3.2,
+ * the k^2-runs reading of Sec. 5), the runs executed together: step t of every
+ * run goes out in the same grouped launches (the blocks are independent,
+ * Sec. 8).  ij holds count pairs (i, j); outs[t] (host or device, M's dtype)
+ * receives block (ij[2t], ij[2t+1]) with leading dimension ldos[t].  width
+ * bounds how many runs go together (0 = 8), and the cap may lower it.  With
+ * MIXED_BF16 and refine_steps = 1 every block is refined as in mbinv_block. */
+mbinv_status mbinv_blocks(mbinv_ctx *ctx, int64_t count, const int64_t *ij, void *const *outs, const int64_t *ldos,
+                          int width, mbinv_report *report);
+
+/* All blocks of M^-1 by k^2 independent runs (Sec. 5), one block row's runs
+ * together at a time.  out is n x n with leading dimension ldo (host or
+ * device).  done (may be NULL) is a k*k row-major bitmap of blocks to skip; cb
+ * (may be NULL) is called for each finished block after its block row
+ * completes, so a caller can checkpoint and resume. */
 mbinv_status mbinv_all_blocks(mbinv_ctx *ctx, void *out, int64_t ldo, const uint8_t *done, mbinv_block_done_cb cb,
                               void *user, mbinv_report *report);
 
 /* Block row i of M^-1 (b_i x n, leading dimension ldo): k runs of the
- * recursion, one per block. */
+ * recursion, one per block, executed together. */
 mbinv_status mbinv_block_row(mbinv_ctx *ctx, int64_t i, void *out, int64_t ldo, mbinv_report *report);
 
 /* Block column j of M^-1 (n x b_j, leading dimension ldo). */
@@ -167,8 +178,10 @@ mbinv_status mbinv_backward(mbinv_ctx *ctx, int64_t i, int64_t j, const void *G,
 /* Many independent problems (the paper's blocks are embarrassingly parallel,
  * Sec. 8), all in dtype with the options opt (may be NULL).  Each problem's
  * status field is written; the return value is MBINV_OK when every problem
- * succeeded, else the first failing status.  Problems run level by level
- * with the same kernels in grouped launches. */
+ * succeeded, else the first failing status.  The problems' runs are executed
+ * together, level by level, in grouped launches that mix orders b (in waves
+ * whose summed workspace fits device_cap_bytes); MIXED_BF16 with
+ * refine_steps = 1 is not supported here (MBINV_ENOTSUP). */
 mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem *probs, int dtype, const mbinv_options *opt,
                                   mbinv_report *report);
 

@@ -68,6 +68,9 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Options)]),
     "mbinv_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                    ctypes.POINTER(Report)]),
+    "mbinv_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                    ctypes.POINTER(Report)]),
     "mbinv_all_blocks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, DONE_CB,
                                         ctypes.c_void_p, ctypes.POINTER(Report)]),
     "mbinv_block_row": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
@@ -216,6 +219,20 @@ class Context:
         _check(lib().mbinv_block(self._h, i, j, _ptr(out), out.stride(0), ctypes.byref(rep)), f"mbinv_block({i},{j})")
         self.last_report = rep.as_dict()
         return out
+
+    def blocks(self, ij, outs=None, width: int = 0):
+        """Several blocks, each by its own run of the recursion, the runs
+        executed together.  ij: list of (i, j).  Returns the list of blocks."""
+        if outs is None:
+            outs = [self._out(self.extent(i), self.extent(j), None) for i, j in ij]
+        n = len(ij)
+        arr = (ctypes.c_int64 * (2 * n))(*[x for p in ij for x in p])
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        lds = (ctypes.c_int64 * n)(*[o.stride(0) for o in outs])
+        rep = Report()
+        _check(lib().mbinv_blocks(self._h, n, arr, ptrs, lds, int(width), ctypes.byref(rep)), "mbinv_blocks")
+        self.last_report = rep.as_dict()
+        return outs
 
     def all_blocks(self, out=None, done=None, callback=None, on_host: bool = False):
         out = self._out(self.n, self.n, out, on_host)

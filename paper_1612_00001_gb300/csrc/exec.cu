@@ -1,0 +1,471 @@
+// Executor of the recursion's schedules (Sec. 3.2, backward procedure).
+//
+// Every schedule has the same shape: per level one batch of pivot inverses,
+// then the Schur products Z = P^-1 R and X = K - L Z (the leaf level starts
+// from P = M_22 and blocks of M; the last step inverts the root value).  So
+// step t of any number of independent requests can go out together: one
+// batched inverse launch sequence and one grouped GEMM launch per step,
+// whatever the requests' orders b.  All descriptors of a run are written to
+// pinned host memory and copied to the device in one transfer.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <map>
+#include <tuple>
+
+#include "exec.h"
+#include "tc_gemm.h"
+
+namespace mbinv {
+
+void Env::release() {
+  for (DevBuf* d : {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr})
+    d->release();
+  hdesc.release();
+  for (cudaEvent_t e : events) cudaEventDestroy(e);
+  events.clear();
+}
+
+size_t slot_bytes_for(int b, int precision) {
+  const size_t s = (size_t)b * b * dtype_size(env_slot_type(precision));
+  return (s + 255) & ~(size_t)255;
+}
+
+namespace {
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Strides {
+  size_t work, wrow, perm;
+};
+
+Strides inv_strides(int bmax, int precision) {
+  const int wt = env_work_type(precision);
+  const size_t ws = dtype_size(wt);
+  const size_t nb = (size_t)inv_panel_width(bmax, wt);
+  return Strides{al((size_t)bmax * bmax * ws), al(nb * bmax * ws), al((size_t)bmax * 4)};
+}
+
+const void* resolve(const Job& J, const Ref& r, int64_t* ld, int* dt) {
+  switch (r.kind) {
+    case Ref::MBLK:
+      *ld = J.ldm;
+      *dt = J.mdt;
+      return (const char*)J.dM + ((size_t)r.r * J.b * J.ldm + (size_t)r.c * J.b) * dtype_size(J.mdt);
+    case Ref::SLOT:
+      *ld = J.b;
+      *dt = J.slot_dt;
+      return J.slots + (size_t)r.slot * J.slot_bytes;
+    case Ref::OUT:
+      *ld = J.ldo;
+      *dt = J.out_dt;
+      return J.out;
+    default:
+      *ld = 0;
+      *dt = -1;
+      return nullptr;
+  }
+}
+
+int combo_for(int adt, int bdt, int cdt) {
+  if (adt == F64 && bdt == F64 && cdt == F64) return G_F64;
+  if (adt == F32 && bdt == F32 && cdt == F32) return G_F32;
+  if (adt == F32 && bdt == F32 && cdt == F64) return G_F32IN_F64;
+  if (adt == F64 && bdt == F32 && cdt == F64) return G_F64F32_F64;
+  if (adt == F32 && bdt == F64 && cdt == F64) return G_F32F64_F64;
+  return -1;
+}
+
+cudaError_t ensure_events(Env& E, size_t n) {
+  while (E.events.size() < n) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    E.events.push_back(e);
+  }
+  return cudaSuccess;
+}
+
+// One launch (or launch sequence) of a run, in order.
+struct Launch {
+  enum Kind : int { INV = 0, GEMM = 1, PACK = 2, TC = 3 } kind;
+  size_t off;  // descriptors in the arena
+  int count;
+  int in_dt = 0, out_dt = 0, bmax = 0;  // INV
+  int combo = 0, tiles = 0;             // GEMM
+  int rows_pad = 0, kpad = 0;           // PACK / TC
+  __nv_bfloat16* dst = nullptr;         // PACK destination, TC A operand
+  __nv_bfloat16* bsrc = nullptr;        // TC B operand
+  int nA = 0, mode = 0, b = 0, nB = 0;  // TC
+  __nv_bfloat16* zout = nullptr;        // TC mode 1 output (Z^T slices)
+};
+
+#define CUE(x)                      \
+  do {                              \
+    cudaError_t e_ = (x);           \
+    if (e_ != cudaSuccess) {        \
+      E.last_error = e_;            \
+      return MBINV_ECUDA;           \
+    }                               \
+  } while (0)
+
+}  // namespace
+
+size_t inv_scratch_bytes(int bmax, int precision, int count) {
+  const Strides st = inv_strides(bmax, precision);
+  return (size_t)count * (st.work + st.wrow + st.perm + 256);
+}
+
+size_t pack_bytes(int bmax, int slices, size_t ops) {
+  const int T = tc::tile_rows(), KT = tc::tile_k();
+  const size_t rpad = (size_t)(bmax + T - 1) / T * T, kpad = (size_t)(bmax + KT - 1) / KT * KT;
+  return 3 * ops * slices * rpad * kpad * 2;
+}
+
+mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
+  E.launches = E.gemm_launches = 0;
+  E.gemm_dev_s = E.inv_dev_s = E.pack_dev_s = 0;
+  E.job_singular.assign(jobs.size(), 0);
+  if (jobs.empty()) return MBINV_OK;
+  const bool mixed = E.precision == MBINV_MIXED_BF16;
+  const int wt = env_work_type(E.precision);
+  size_t nsteps = 0;
+  int bmax = 0;
+  for (const Job& J : jobs) {
+    nsteps = std::max(nsteps, J.S->steps.size());
+    bmax = std::max(bmax, J.b);
+  }
+  const Strides st = inv_strides(bmax, E.precision);
+  const int T = tc::tile_rows(), KT = tc::tile_k();
+  const int NS = E.slices;
+
+  // ---- pass 1: sizes of the descriptor arena and of the packed slabs
+  size_t need = 512, maxA = 1, maxB = 1, maxZ = 1;  // maxA/B/Z in bytes
+  for (size_t t = 0; t < nsteps; ++t) {
+    size_t ninv = 0, ngemm = 0;
+    std::map<int, std::pair<size_t, size_t>> per_b;  // b -> (distinct A, products)
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      const Schedule& S = *jobs[q].S;
+      if (t >= S.steps.size()) continue;
+      const Step& s = S.steps[t];
+      if (s.kind == Step::INV) {
+        ninv += s.inv.size();
+      } else {
+        ngemm += s.gemm.size();
+        per_b[jobs[q].b].second += s.gemm.size();
+        per_b[jobs[q].b].first += s.gemm.size();
+      }
+    }
+    need += ninv * sizeof(InvDesc) + 256 * ((ninv + E.inv_chunk - 1) / E.inv_chunk + 1);
+    need += ngemm * sizeof(GemmDesc) + 256;
+    if (mixed) {
+      size_t zsum = 0;
+      for (auto& kv : per_b) {
+        need += kv.second.first * sizeof(tc::PackDesc) * 2 + kv.second.second * sizeof(tc::TcProblem) + 1024;
+        const size_t slab = (size_t)NS * ((kv.first + T - 1) / T * T) * ((kv.first + KT - 1) / KT * KT) * 2;
+        maxA = std::max(maxA, kv.second.first * slab);
+        maxB = std::max(maxB, kv.second.second * slab);
+        zsum += al(kv.second.second * slab);
+      }
+      maxZ = std::max(maxZ, zsum);
+    }
+  }
+  CUE(E.desc.ensure(need));
+  CUE(E.hdesc.ensure(need));
+  CUE(E.status.ensure(256));
+  CUE(E.flags.ensure(al(jobs.size() * sizeof(int))));
+  CUE(E.inv_work.ensure((size_t)E.inv_chunk * st.work));
+  CUE(E.inv_wrow.ensure((size_t)E.inv_chunk * st.wrow));
+  CUE(E.inv_perm.ensure((size_t)E.inv_chunk * st.perm));
+  CUE(E.inv_amax.ensure((size_t)E.inv_chunk * 256));
+  if (mixed) {
+    CUE(E.apk.ensure(maxA));
+    CUE(E.bpk.ensure(maxB));
+    CUE(E.b2pk.ensure(maxZ));
+    CUE(E.tcerr.ensure(256));
+  }
+  char* hbase = (char*)E.hdesc.p;
+  char* dbase = (char*)E.desc.p;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += al(bytes);
+    return o;
+  };
+  std::vector<Launch> L;
+  int* dflags = (int*)E.flags.p;
+
+  // ---- pass 2: descriptors
+  std::map<std::pair<int, int>, int> zslab;  // (request, slot of a Z value) -> slab in its group
+  std::map<int, size_t> zbase;                // order b -> byte offset of its group in b2pk
+  std::map<int, int> zcount;                  // order b -> Z slabs of its group
+  for (size_t t = 0; t < nsteps; ++t) {
+    int kind = -1;
+    for (const Job& J : jobs)
+      if (t < J.S->steps.size()) {
+        const int k2 = J.S->steps[t].kind;
+        if (kind >= 0 && k2 != kind) return MBINV_ENOTSUP;  // schedules must align
+        kind = k2;
+      }
+    if (kind == Step::INV) {
+      std::vector<std::pair<int, const InvOp*>> ops;
+      for (size_t q = 0; q < jobs.size(); ++q)
+        if (t < jobs[q].S->steps.size())
+          for (const InvOp& io : jobs[q].S->steps[t].inv) ops.emplace_back((int)q, &io);
+      for (size_t c0 = 0; c0 < ops.size(); c0 += E.inv_chunk) {
+        const size_t c1 = std::min(ops.size(), c0 + (size_t)E.inv_chunk);
+        const size_t o = take((c1 - c0) * sizeof(InvDesc));
+        InvDesc* hd = (InvDesc*)(hbase + o);
+        int in_dt = -1, out_dt = -1, bm = 0;
+        for (size_t u = c0; u < c1; ++u) {
+          const Job& J = jobs[ops[u].first];
+          InvDesc d{};
+          int64_t ld;
+          int idt, odt;
+          d.src = resolve(J, ops[u].second->src, &ld, &idt);
+          d.lds = ld;
+          d.dst = (void*)resolve(J, ops[u].second->dst, &ld, &odt);
+          d.ldd = ld;
+          if ((in_dt >= 0 && idt != in_dt) || (out_dt >= 0 && odt != out_dt)) return MBINV_ENOTSUP;
+          in_dt = idt;
+          out_dt = odt;
+          d.work = (char*)E.inv_work.p + (u - c0) * st.work;
+          d.wrow = (char*)E.inv_wrow.p + (u - c0) * st.wrow;
+          d.perm = (int*)((char*)E.inv_perm.p + (u - c0) * st.perm);
+          d.amax = (unsigned long long*)((char*)E.inv_amax.p + (u - c0) * 256);
+          d.b = J.b;
+          d.tag = ops[u].first;
+          d.flag = dflags + ops[u].first;
+          bm = std::max(bm, J.b);
+          hd[u - c0] = d;
+        }
+        Launch l{Launch::INV, o, (int)(c1 - c0)};
+        l.in_dt = in_dt;
+        l.out_dt = out_dt;
+        l.bmax = bm;
+        L.push_back(l);
+      }
+      continue;
+    }
+    // ---- GEMM step
+    std::vector<std::pair<int, const GemmOp*>> ops;
+    for (size_t q = 0; q < jobs.size(); ++q)
+      if (t < jobs[q].S->steps.size())
+        for (const GemmOp& g : jobs[q].S->steps[t].gemm) ops.emplace_back((int)q, &g);
+    if (ops.empty()) continue;
+    if (!mixed) {
+      const size_t o = take(ops.size() * sizeof(GemmDesc));
+      GemmDesc* hd = (GemmDesc*)(hbase + o);
+      int combo = -1, tiles = 0;
+      for (size_t u = 0; u < ops.size(); ++u) {
+        const Job& J = jobs[ops[u].first];
+        const GemmOp& g = *ops[u].second;
+        GemmDesc d{};
+        int adt, bdt, cdt, idt = -1;
+        int64_t ld;
+        d.A = resolve(J, g.A, &ld, &adt);
+        d.lda = ld;
+        d.B = resolve(J, g.B, &ld, &bdt);
+        d.ldb = ld;
+        d.C = (void*)resolve(J, g.C, &ld, &cdt);
+        d.ldc = ld;
+        if (g.Cin.kind != Ref::NONE) {
+          d.Cin = resolve(J, g.Cin, &ld, &idt);
+          d.ldcin = ld;
+        }
+        d.m = d.n = d.k = J.b;
+        d.alpha = g.alpha;
+        d.beta = g.beta;
+        const int cb = combo_for(adt, bdt, cdt);
+        if (cb < 0 || (combo >= 0 && cb != combo) || (idt >= 0 && idt != cdt)) return MBINV_ENOTSUP;
+        combo = cb;
+        int bm, bn;
+        gemm_tile_shape(combo, &bm, &bn);
+        d.tiles_n = (d.n + bn - 1) / bn;
+        d.tile_start = tiles;
+        tiles += ((d.m + bm - 1) / bm) * d.tiles_n;
+        hd[u] = d;
+      }
+      Launch l{Launch::GEMM, o, (int)ops.size()};
+      l.combo = combo;
+      l.tiles = tiles;
+      L.push_back(l);
+      continue;
+    }
+    // mixed: one pack/product sequence per distinct order b
+    const bool second = ops[0].second->Cin.kind != Ref::NONE;  // X = K - L Z
+    std::map<int, std::vector<size_t>> by_b;
+    for (size_t u = 0; u < ops.size(); ++u) by_b[jobs[ops[u].first].b].push_back(u);
+    if (!second) {
+      zbase.clear();
+      zcount.clear();
+      size_t zo = 0;
+      for (auto& kv : by_b) {
+        zbase[kv.first] = zo;
+        zcount[kv.first] = (int)kv.second.size();
+        const int b = kv.first;
+        zo += al(kv.second.size() * (size_t)NS * ((b + T - 1) / T * T) * ((b + KT - 1) / KT * KT) * 2);
+      }
+    }
+    for (auto& kv : by_b) {
+      const int b = kv.first;
+      const int rpad = (b + T - 1) / T * T, kpad = (b + KT - 1) / KT * KT;
+      const std::vector<size_t>& us = kv.second;
+      __nv_bfloat16* zb = (__nv_bfloat16*)((char*)E.b2pk.p + zbase[b]);
+      // distinct A operands
+      std::map<std::tuple<int, int, int, int>, int> aslab;
+      std::vector<size_t> afirst;
+      auto akey = [&](size_t u) {
+        const GemmOp& g = *ops[u].second;
+        return std::make_tuple(ops[u].first, (int)g.A.kind, g.A.kind == Ref::SLOT ? g.A.slot : g.A.r, g.A.c);
+      };
+      for (size_t u : us)
+        if (aslab.emplace(akey(u), (int)afirst.size()).second) afirst.push_back(u);
+      {
+        const size_t o = take(afirst.size() * sizeof(tc::PackDesc));
+        tc::PackDesc* pd = (tc::PackDesc*)(hbase + o);
+        for (size_t a = 0; a < afirst.size(); ++a) {
+          int64_t ld;
+          int dt;
+          const void* p = resolve(jobs[ops[afirst[a]].first], ops[afirst[a]].second->A, &ld, &dt);
+          pd[a] = tc::PackDesc{p, ld, b, b, dt == F64 ? 1 : 0, 0, (int)a};
+        }
+        Launch l{Launch::PACK, o, (int)afirst.size()};
+        l.rows_pad = rpad;
+        l.kpad = kpad;
+        l.dst = (__nv_bfloat16*)E.apk.p;
+        L.push_back(l);
+      }
+      if (!second) {
+        const size_t o = take(us.size() * sizeof(tc::PackDesc));
+        tc::PackDesc* pd = (tc::PackDesc*)(hbase + o);
+        for (size_t v = 0; v < us.size(); ++v) {
+          int64_t ld;
+          int dt;
+          const void* p = resolve(jobs[ops[us[v]].first], ops[us[v]].second->B, &ld, &dt);
+          pd[v] = tc::PackDesc{p, ld, b, b, dt == F64 ? 1 : 0, 1, (int)v};
+        }
+        Launch l{Launch::PACK, o, (int)us.size()};
+        l.rows_pad = rpad;
+        l.kpad = kpad;
+        l.dst = (__nv_bfloat16*)E.bpk.p;
+        L.push_back(l);
+      }
+      const size_t o = take(us.size() * sizeof(tc::TcProblem));
+      tc::TcProblem* pr = (tc::TcProblem*)(hbase + o);
+      for (size_t v = 0; v < us.size(); ++v) {
+        const Job& J = jobs[ops[us[v]].first];
+        const GemmOp& g = *ops[us[v]].second;
+        tc::TcProblem qd{};
+        qd.a_slab = aslab[akey(us[v])];
+        if (!second) {
+          qd.b_slab = (int)v;
+          qd.out_slab = (int)v;
+          zslab[{ops[us[v]].first, g.C.slot}] = (int)v;
+        } else {
+          auto it = zslab.find({ops[us[v]].first, g.B.slot});
+          if (g.B.kind != Ref::SLOT || it == zslab.end()) return MBINV_ENOTSUP;
+          qd.b_slab = it->second;
+          int64_t ld;
+          int dt;
+          qd.cin = resolve(J, g.Cin, &ld, &dt);
+          qd.ldcin = ld;
+          qd.cin_f64 = dt == F64 ? 1 : 0;
+          qd.out = (void*)resolve(J, g.C, &ld, &dt);
+          qd.ldo = ld;
+          if (dt != F32) return MBINV_ENOTSUP;
+        }
+        pr[v] = qd;
+      }
+      Launch l{Launch::TC, o, (int)us.size()};
+      l.rows_pad = rpad;
+      l.kpad = kpad;
+      l.nA = (int)afirst.size();
+      l.mode = second ? 0 : 1;
+      l.b = b;
+      l.dst = (__nv_bfloat16*)E.apk.p;
+      l.bsrc = second ? zb : (__nv_bfloat16*)E.bpk.p;
+      l.zout = zb;
+      l.nB = second ? zcount[b] : (int)us.size();
+      L.push_back(l);
+    }
+    if (!second) {
+      // a second-product step reads zslab; the next first-product step starts afresh
+    } else {
+      zslab.clear();
+    }
+  }
+  if (off + 64 > need) return MBINV_ENOTSUP;
+
+  // ---- launches
+  CUE(cudaMemcpyAsync(dbase, hbase, off, cudaMemcpyHostToDevice, E.stream));
+  DevStatus* hst = (DevStatus*)(hbase + need - 64);
+  hst[0] = DevStatus{0, INT_MAX};
+  CUE(cudaMemcpyAsync(E.status.p, &hst[0], sizeof(DevStatus), cudaMemcpyHostToDevice, E.stream));
+  CUE(cudaMemsetAsync(E.flags.p, 0, jobs.size() * sizeof(int), E.stream));
+  if (mixed) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
+  if (E.profile) CUE(ensure_events(E, 2 * L.size()));
+  tc::TcParams P{};
+  if (mixed) {
+    P.S = NS;
+    tc::pair_table(NS, &P.npairs, P.pa, P.pb);
+    P.err = (int*)E.tcerr.p;
+  }
+  for (size_t q = 0; q < L.size(); ++q) {
+    const Launch& l = L[q];
+    if (E.profile) CUE(cudaEventRecord(E.events[2 * q], E.stream));
+    switch (l.kind) {
+      case Launch::INV:
+        CUE(run_inverse_batch(l.in_dt, l.out_dt, wt, (const InvDesc*)(dbase + l.off), l.count, l.bmax,
+                              (DevStatus*)E.status.p, E.stream, &E.launches));
+        break;
+      case Launch::GEMM:
+        CUE(launch_gemm_grouped(l.combo, (const GemmDesc*)(dbase + l.off), l.count, l.tiles, E.stream));
+        ++E.launches;
+        ++E.gemm_launches;
+        break;
+      case Launch::PACK:
+        CUE(tc::launch_pack((const tc::PackDesc*)(dbase + l.off), l.count, NS, l.rows_pad, l.kpad, l.dst, E.stream));
+        ++E.launches;
+        break;
+      case Launch::TC:
+        P.m = P.n = l.b;
+        P.kpad = l.kpad;
+        P.tiles_m = P.tiles_n = l.rows_pad / T;
+        P.orows = l.rows_pad;
+        P.okpad = l.kpad;
+        P.mode = l.mode;
+        P.alpha = l.mode == 0 ? -1.f : 1.f;
+        P.beta = 1.f;
+        P.opk = l.zout;
+        CUE(tc::launch_gemm(l.dst, l.nA, l.rows_pad, l.bsrc, l.nB, l.rows_pad, P,
+                            (const tc::TcProblem*)(dbase + l.off), l.count, E.stream));
+        ++E.launches;
+        ++E.gemm_launches;
+        break;
+    }
+    if (E.profile) CUE(cudaEventRecord(E.events[2 * q + 1], E.stream));
+  }
+  CUE(cudaMemcpyAsync(&hst[1], E.status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, E.stream));
+  int herr = 0;
+  CUE(cudaStreamSynchronize(E.stream));
+  std::vector<int> fl(jobs.size(), 0);
+  CUE(cudaMemcpy(fl.data(), E.flags.p, jobs.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  if (mixed) CUE(cudaMemcpy(&herr, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t q = 0; q < jobs.size(); ++q) E.job_singular[q] = fl[q];
+  if (E.profile) {
+    for (size_t q = 0; q < L.size(); ++q) {
+      float ms = 0;
+      CUE(cudaEventElapsedTime(&ms, E.events[2 * q], E.events[2 * q + 1]));
+      if (L[q].kind == Launch::INV) E.inv_dev_s += ms * 1e-3;
+      else if (L[q].kind == Launch::PACK) E.pack_dev_s += ms * 1e-3;
+      else E.gemm_dev_s += ms * 1e-3;
+    }
+  }
+  if (herr) return MBINV_ETIMEOUT;
+  if (hst[1].singular) return MBINV_ESINGULAR;
+  return MBINV_OK;
+}
+
+}  // namespace mbinv

@@ -1,0 +1,100 @@
+// Executor of recursion schedules: one or many independent requests run
+// together, level by level, in grouped launches on one stream.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/mbinv.h"
+#include "mbinv_internal.h"
+
+namespace mbinv {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+struct HostBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMallocHost(&p, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+// One request: the matrix it reads, its value slots, its output, its schedule.
+struct Job {
+  const void* dM = nullptr;  // (bordered) matrix, row-major
+  int64_t ldm = 0;
+  int mdt = F64;
+  int b = 0;
+  char* slots = nullptr;     // this request's slots, slot_bytes apart
+  size_t slot_bytes = 0;
+  int slot_dt = F64;
+  void* out = nullptr;       // device destination of N_ij (b x b)
+  int64_t ldo = 0;
+  int out_dt = F64;
+  const Schedule* S = nullptr;
+};
+
+// Buffers and settings shared by the requests of one run.
+struct Env {
+  cudaStream_t stream = nullptr;
+  int precision = MBINV_FP64;
+  int slices = 3;
+  bool profile = false;
+  int inv_chunk = 1;  // matrices per inverse launch
+  DevBuf inv_work, inv_wrow, inv_perm, inv_amax, desc, status, flags, apk, bpk, b2pk, tcerr;
+  HostBuf hdesc;
+  std::vector<cudaEvent_t> events;
+  // results of the last run
+  int launches = 0, gemm_launches = 0;
+  double gemm_dev_s = 0, inv_dev_s = 0, pack_dev_s = 0;
+  std::vector<int> job_singular;  // per request
+  cudaError_t last_error = cudaSuccess;
+
+  void release();
+};
+
+inline int env_work_type(int precision) { return precision == MBINV_FP32 ? F32 : F64; }
+inline int env_slot_type(int precision) { return precision == MBINV_FP64 ? F64 : F32; }
+size_t slot_bytes_for(int b, int precision);
+// Device bytes of inverse scratch for count matrices of order at most bmax.
+size_t inv_scratch_bytes(int bmax, int precision, int count);
+// Device bytes of the packed operand slabs of the mixed path for a run whose
+// widest GEMM step has `ops` products of order bmax.
+size_t pack_bytes(int bmax, int slices, size_t ops);
+
+// Runs the schedules of `jobs` together: step t of every schedule goes out in
+// the same grouped launches.  Returns MBINV_ESINGULAR if any request met a
+// singular pivot (E.job_singular says which).
+mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs);
+
+}  // namespace mbinv

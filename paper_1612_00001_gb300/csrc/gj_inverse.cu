@@ -95,9 +95,13 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   const int q = (int)cluster.block_rank();
   const InvDesc d = descs[blockIdx.x / CL];
   const int b = d.b;
+  // matrices of a batch may differ in order: this one's panel may be narrower
+  // or already past its end (the whole cluster leaves together)
+  const int ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
+  nb = min(nb, b - p);
+  if (nb <= 0) return;
   const int R = (b + CL - 1) / CL;
   const int r0 = min(b, q * R), r1 = min(b, r0 + R);
-  const int ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
   TW* P = (TW*)smem_raw;   // P[(i - r0) * ldp + t] is X[i][p + t]
   TW* prow = P + (size_t)R * ldp;       // pivot row before scaling (nb)
   TW* srow = prow + ldp;                // scaled pivot row (nb)
@@ -163,6 +167,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
           if (!(v > tol) || !isfinite((double)v)) {
             atomicExch(&status->singular, 1);
             atomicMin(&status->tag, d.tag);
+            if (d.flag) atomicExch(d.flag, 1);
           }
           d.perm[j] = ix;
         }
@@ -254,6 +259,8 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const InvDesc* __restric
   const int b = d.b;
   const int m0 = blockIdx.y * Cfg::BM, n0 = blockIdx.x * Cfg::BN;
   if (m0 >= b || n0 >= b) return;
+  nb = min(nb, b - p);
+  if (nb <= 0 || nb >= b) return;  // past this matrix's end, or its panel is the whole matrix
   if (n0 >= p && n0 + Cfg::BN <= p + nb) return;  // tile inside the panel
   TW* X = (TW*)d.work;
   TW acc[Cfg::TM][Cfg::TN];
@@ -334,7 +341,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     attr_set = true;
   }
   for (int p = 0; p < b; p += nb) {
-    const int w = std::min(nb, b - p);
+    const int w = std::min(nb, b - p);  // widest panel of this step (b is the largest order)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * CL, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
@@ -350,7 +357,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status);
     if (e != cudaSuccess) return e;
     ++nl;
-    if (w < b) {
+    if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
       using Cfg = TileCfg<TW>;
       dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);
       gj_update_kernel<TW><<<g, 256, 0, s>>>(d_desc, p, w);

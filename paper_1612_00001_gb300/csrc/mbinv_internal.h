@@ -64,6 +64,7 @@ struct Schedule {
   double gemm_flops_units = 0;  // in units of b^3 (2 per product)
   double inv_units = 0;         // in units of b^3 (2 per inverse)
   size_t frames = 0, inversions = 0;
+  int inv_chunk = 0;            // matrices per inverse launch chosen to fit the cap
 };
 
 // Builds the level-by-level schedule of one request.  zchunk bounds the
@@ -108,6 +109,7 @@ struct InvDesc {
   unsigned long long* amax;  // max |entry| (bit pattern of a non-negative double)
   int b;
   int tag;          // reported through the status word when singular
+  int* flag;        // set to 1 when singular (may be null): per-problem status
 };
 // Status word written by the inverse kernels: flag != 0 when a pivot was
 // singular; tag holds the smallest failing InvDesc::tag.
@@ -117,9 +119,10 @@ struct DevStatus {
 };
 // Panel width of the blocked elimination for order b in working type wtype.
 int inv_panel_width(int b, int wtype);
-// Inverts count matrices of order b (all the same order) described by
-// d_desc.  in_dtype / out_dtype / wtype are DType values; wtype is F64 or F32.
-// d_amax must hold count zeroed words (the call zeroes them).
+// Inverts count matrices described by d_desc; b is the largest order among
+// them (each descriptor carries its own).  in_dtype / out_dtype / wtype are
+// DType values; wtype is F64 or F32.  The max|entry| words are zeroed by the
+// call.
 cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
                               DevStatus* d_status, cudaStream_t s, int* launches);
 

@@ -216,3 +216,41 @@ def test_cap_respected_by_chunked_schedule(mb):
     c = to_np(small.block(3, 4))
     assert small.last_report["peak_device_bytes"] <= int(need * 0.85)
     assert oracle.rel_fro(c, a) < 1e-13
+
+
+def test_requests_run_together_match_one_at_a_time(mb):
+    """mbinv_blocks runs several independent requests level by level in the
+    same grouped launches; each block is bit for bit the one-at-a-time block."""
+    m = bi.uniform_shift(512, 6)
+    ctx = mb.Context(dev(m), 8)
+    ij = [(0, 0), (3, 5), (7, 1), (2, 2), (6, 7)]
+    together = [to_np(x) for x in ctx.blocks(ij)]
+    for (i, j), t in zip(ij, together):
+        one = to_np(mb.Context(dev(m), 8).block(i, j))
+        assert np.array_equal(t, one), (i, j)
+        assert oracle.rel_fro(t, oracle_block(m, 8, i, j)) <= parity_tol(m, 8, i, j, TOL_FP64)[0]
+
+
+def test_requests_together_with_padding_and_host_outputs(mb):
+    n, k = 250, 4
+    m = bi.uniform_shift(n, 8)
+    ctx = mb.Context(dev(m), k, pad_seed=3)
+    ij = [(0, 1), (1, 3), (3, 0), (3, 3), (2, 2)]
+    outs = [torch.empty((ctx.extent(i), ctx.extent(j)), dtype=torch.float64) for i, j in ij]  # host
+    ctx.blocks(ij, outs=outs)
+    inv = np.linalg.inv(m)
+    b = ctx.b
+    for (i, j), o in zip(ij, outs):
+        ref = inv[i * b:i * b + ctx.extent(i), j * b:j * b + ctx.extent(j)]
+        assert oracle.rel_fro(o.numpy(), ref) < 1e-11, (i, j)
+
+
+def test_mixed_requests_together(mb):
+    m = bi.uniform_shift(256, 0)
+    M = torch.tensor(m, dtype=torch.float32, device="cuda")
+    ctx = mb.Context(M, 4, precision="mixed")
+    ij = [(0, 0), (1, 3), (3, 2)]
+    together = [to_np(x) for x in ctx.blocks(ij)]
+    for (i, j), t in zip(ij, together):
+        one = to_np(mb.Context(M, 4, precision="mixed").block(i, j))
+        assert np.array_equal(t, one), (i, j)
