@@ -45,6 +45,14 @@ def parse():
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
     p.add_argument("--slices", type=int, default=3)
     p.add_argument("--refine", type=int, default=0)
+    p.add_argument("--together", type=int, default=0,
+                   help="run each step's blocks as that many independent runs executed together (0: one at a time)")
+    p.add_argument("--matrix", default="uniform", choices=["uniform", "haar", "spd"])
+    p.add_argument("--kappa", type=float, default=1e4)
+    p.add_argument("--batched", type=int, default=0,
+                   help="batched workload: this many independent matrices of uneven n and k, one block each")
+    p.add_argument("--backward", action="store_true",
+                   help="differentiation workload: one block forward and the adjoint backward per step")
     return p.parse_args()
 
 
@@ -54,6 +62,20 @@ def peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_matrix(args, n):
+    import bri_inputs as bi
+    if args.matrix == "haar":
+        return bi.haar_svd(n, args.kappa, 0)
+    if args.matrix == "spd":
+        return bi.spd(n, args.kappa, 0)
+    return bi.uniform_shift(n, 0)
+
+
+def matrix_name(args):
+    return {"uniform": "uniform[-1,1)+nI", "haar": f"U diag(sigma) V^T, Haar U V, cond {args.kappa:g}",
+            "spd": f"SPD Q diag(mu) Q^T, cond {args.kappa:g}"}[args.matrix]
 
 
 def block_list(k, start, count):
@@ -146,6 +168,123 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def _clock_region(local):
+    c = Clocks(local)
+    c.start()
+    return c
+
+
+def run_batched(args, rank, world, dist):
+    """Independent matrices of uneven n in [256, 4096] (multiples of 64) and k in
+    {2..8}, uniform[-1,1)+nI, one block (i, j) each; a step is the whole batch
+    through mbinv_batched_blocks."""
+    import numpy as np
+    import torch
+
+    import bri_inputs as bi
+    import paper_1612_00001_gb300 as mb
+    probs = bi.ragged_batch(args.batched, 0)
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    mats = [torch.tensor(bi.uniform_shift(p["n"], p["seed"]), dtype=dt, device="cuda") for p in probs]
+    work = [(M, p["k"], p["i"], p["j"]) for M, p in zip(mats, probs)]
+    flops = 0.0
+    for s in range(args.warmup):
+        outs, st, rep, rc = mb.batched_blocks(work, precision=args.precision)
+        assert rc == mb.OK, st
+    stream = torch.cuda.current_stream()
+    clocks = _clock_region(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    agg = {"gemm_flops": 0.0, "inv_flops": 0.0, "launches": 0}
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        outs, st, rep, rc = mb.batched_blocks(work, precision=args.precision)
+        ev[s][1].record(stream)
+        for key in agg:
+            agg[key] += rep[key]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
+    # accuracy on a sample of the batch against dense inverses
+    errs = []
+    for q in range(0, len(probs), max(1, len(probs) // 8)):
+        p = probs[q]
+        m = bi.uniform_shift(p["n"], p["seed"])
+        inv = np.linalg.inv(m.astype(np.float32 if dt == torch.float32 else np.float64).astype(np.float64))
+        bb = -(-p["n"] // p["k"])
+        r = inv[p["i"] * bb:p["i"] * bb + outs[q].shape[0], p["j"] * bb:p["j"] * bb + outs[q].shape[1]]
+        errs.append(float(np.linalg.norm(outs[q].double().cpu().numpy() - r) / np.linalg.norm(r)))
+    line = {"metric": METRIC, "value": args.batched * args.steps / secs, "unit": "blocks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"{args.batched} matrices, n ~ U[256,4096] step 64, k ~ U{{2..8}}, "
+                                   f"uniform[-1,1)+nI, one block each, runs executed together ({args.precision})",
+                       "max_rel_err_vs_dense_inverse_sample": max(errs)},
+            "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12, "gpu_launches": agg["launches"],
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_backward(args, rank, world, dist):
+    """Differentiation: L = sum(W * N_ij), W ~ N(0,1); a step is the forward
+    block and dL/dM = -(X_i)^T W (Y_j)^T, the block row and column recomputed
+    block by block."""
+    import numpy as np
+    import torch
+
+    import bri_inputs as bi
+    import paper_1612_00001_gb300 as mb
+    n, k = args.n, args.k
+    b = -(-n // k)
+    m = bi.spd(n, args.kappa, 0) if args.matrix == "spd" else make_matrix(args, n)
+    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    M = torch.tensor(m, dtype=dt, device="cuda")
+    W = torch.tensor(bi.gaussian_matrix(b, b, 0), dtype=dt, device="cuda")
+    i, j = 1, k - 2
+    ctx = mb.Context(M, k, precision=args.precision, slices=args.slices)
+    dM = torch.zeros((n, n), dtype=dt, device="cuda")
+
+    def step():
+        nb = ctx.block(i, j)
+        dM.zero_()
+        ctx.backward(i, j, W, dM)
+        return nb
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    clocks = _clock_region(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        nb = step()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
+    # FP64 reference gradient from a dense inverse on the host
+    inv = np.linalg.inv(m)
+    ref = -(inv[i * b:(i + 1) * b, :].T @ W.double().cpu().numpy() @ inv[:, j * b:(j + 1) * b].T)
+    gerr = float(np.linalg.norm(dM.double().cpu().numpy() - ref) / np.linalg.norm(ref))
+    ferr = float(np.linalg.norm(nb.double().cpu().numpy() - inv[i * b:(i + 1) * b, j * b:(j + 1) * b])
+                 / np.linalg.norm(inv[i * b:(i + 1) * b, j * b:(j + 1) * b]))
+    line = {"metric": METRIC, "value": args.steps / secs, "unit": "forward+backward/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, L = sum(W * N_{i}{j}), "
+                                   f"forward + adjoint ({args.precision})",
+                       "rel_err_forward_vs_dense": ferr, "rel_err_grad_vs_fp64_reference": gerr},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -167,10 +306,14 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     mb.build()
+    if args.batched:
+        return run_batched(args, rank, world, dist)
+    if args.backward:
+        return run_backward(args, rank, world, dist)
     n, k = args.n, args.k
     b = -(-n // k)
     bps = args.blocks_per_step
-    m_host = bi.uniform_shift(n, 0)
+    m_host = make_matrix(args, n)
     dt = torch.float64 if (args.precision == "fp64" or args.refine) else torch.float32
     M = torch.tensor(m_host, dtype=dt, device="cuda")
     stream = torch.cuda.current_stream()
@@ -182,7 +325,11 @@ def main():
 
     def step(s, c=ctx, dst=outs):
         reps = []
-        for q, (i, j) in enumerate(block_list(k, base + s * bps * world, bps)):
+        ij = block_list(k, base + s * bps * world, bps)
+        if args.together:
+            c.blocks(ij, outs=dst, width=args.together)
+            return [c.last_report]
+        for q, (i, j) in enumerate(ij):
             c.block(i, j, out=dst[q])
             reps.append(c.last_report)
         return reps
@@ -258,7 +405,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[
                 args.precision], "data": "synthetic",
-            "config": {"workload": f"n={n} k={k} b={b} uniform[-1,1)+nI, blocks one at a time ({args.precision})",
+            "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, "
+                                   + (f"{args.together} runs executed together" if args.together
+                                      else "blocks one at a time") + f" ({args.precision})",
                        "blocks_per_step": bps, "precision": args.precision, "slices": args.slices,
                        "refine": args.refine,
                        "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",

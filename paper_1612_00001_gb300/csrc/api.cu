@@ -166,6 +166,28 @@ size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int G, int inv_chunk) {
 mbinv_status get_plan(mbinv_ctx* c, int64_t i, int64_t j, int G, const Schedule** out) {
   auto key = std::make_pair((int)i, (int)j);
   auto it = c->plans.find(key);
+  if (c->k == 1) {
+    // the recursion degenerates to one inversion of M
+    if (it == c->plans.end()) {
+      Schedule S;
+      Step st;
+      st.kind = Step::INV;
+      InvOp io;
+      io.src.kind = Ref::MBLK;
+      io.dst.kind = Ref::OUT;
+      st.inv.push_back(io);
+      S.steps.push_back(st);
+      S.inv_units = 2;
+      S.inversions = 1;
+      S.max_inv_batch = 1;
+      S.inv_chunk = 1;
+      if (c->opt.device_cap_bytes && c->own_M.bytes + run_bytes(c, S, 1, 1) > c->opt.device_cap_bytes)
+        return MBINV_ENOMEM_CAP;
+      it = c->plans.emplace(key, std::make_pair(Plan{}, std::move(S))).first;
+    }
+    *out = &it->second.second;
+    return MBINV_OK;
+  }
   if (it == c->plans.end() || it->second.second.inv_chunk == 0 || G > 1) {
     Plan P = (it == c->plans.end()) ? build_plan((int)c->k, (int)i, (int)j, c->l > 0) : it->second.first;
     const size_t cap = c->opt.device_cap_bytes;
@@ -455,6 +477,19 @@ mbinv_status refined_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_
 
 }  // namespace
 
+// Nothing may be thrown across the C ABI: a failed host allocation or any
+// other exception inside a call becomes a status.
+template <typename F>
+mbinv_status guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return MBINV_ENOMEM_CAP;
+  } catch (...) {
+    return MBINV_EINVAL;
+  }
+}
+
 // ====================================================================== ABI
 
 extern "C" {
@@ -489,7 +524,7 @@ const char* mbinv_version(void) { return "mbinv 0.2 (sm_103a)"; }
 
 const char* mbinv_last_cuda_error(void) { return cudaGetErrorString(last_cuda_error()); }
 
-mbinv_status mbinv_create(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,
+static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,
                           const mbinv_options* opt) {
   if (!out || !M || n <= 0 || k <= 0 || k > 63 || k > n || ld < n || (dtype != F64 && dtype != F32))
     return MBINV_EINVAL;
@@ -578,7 +613,7 @@ void mbinv_destroy(mbinv_ctx* c) {
   delete c;
 }
 
-mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
+static mbinv_status mbinv_block_impl(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
   if (!c || !out || i < 0 || j < 0 || i >= c->k || j >= c->k) return MBINV_EINVAL;
   if (ldo < block_extent(c, j)) return MBINV_EINVAL;
   start_report(rep);
@@ -595,7 +630,7 @@ mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t 
   return s;
 }
 
-mbinv_status mbinv_blocks(mbinv_ctx* c, int64_t count, const int64_t* ij, void* const* outs, const int64_t* ldos,
+static mbinv_status mbinv_blocks_impl(mbinv_ctx* c, int64_t count, const int64_t* ij, void* const* outs, const int64_t* ldos,
                           int width, mbinv_report* rep) {
   if (!c || count < 0 || (count > 0 && (!ij || !outs || !ldos))) return MBINV_EINVAL;
   std::vector<std::pair<int64_t, int64_t>> v;
@@ -638,7 +673,7 @@ mbinv_status mbinv_blocks(mbinv_ctx* c, int64_t count, const int64_t* ij, void* 
   return s;
 }
 
-mbinv_status mbinv_all_blocks(mbinv_ctx* c, void* out, int64_t ldo, const uint8_t* done, mbinv_block_done_cb cb,
+static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, const uint8_t* done, mbinv_block_done_cb cb,
                               void* user, mbinv_report* rep) {
   if (!c || !out || ldo < c->n) return MBINV_EINVAL;
   start_report(rep);
@@ -677,19 +712,19 @@ mbinv_status mbinv_all_blocks(mbinv_ctx* c, void* out, int64_t ldo, const uint8_
   return MBINV_OK;
 }
 
-mbinv_status mbinv_block_row(mbinv_ctx* c, int64_t i, void* out, int64_t ldo, mbinv_report* rep) {
+static mbinv_status mbinv_block_row_impl(mbinv_ctx* c, int64_t i, void* out, int64_t ldo, mbinv_report* rep) {
   if (!c || !out || i < 0 || i >= c->k || ldo < c->n) return MBINV_EINVAL;
   start_report(rep);
   return row_or_col(c, i, true, out, ldo, rep);
 }
 
-mbinv_status mbinv_block_col(mbinv_ctx* c, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
+static mbinv_status mbinv_block_col_impl(mbinv_ctx* c, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
   if (!c || !out || j < 0 || j >= c->k || ldo < block_extent(c, j)) return MBINV_EINVAL;
   start_report(rep);
   return row_or_col(c, j, false, out, ldo, rep);
 }
 
-mbinv_status mbinv_backward(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM, int64_t ldd,
+static mbinv_status mbinv_backward_impl(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM, int64_t ldd,
                             mbinv_report* rep) {
   if (!c || !G || !dM || i < 0 || j < 0 || i >= c->k || j >= c->k || ldd < c->n) return MBINV_EINVAL;
   const int64_t bi = block_extent(c, i), bj = block_extent(c, j), n = c->n;
@@ -741,7 +776,7 @@ mbinv_status mbinv_backward(mbinv_ctx* c, int64_t i, int64_t j, const void* G, i
   return MBINV_OK;
 }
 
-mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem* probs, int dtype, const mbinv_options* opt,
+static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* probs, int dtype, const mbinv_options* opt,
                                   mbinv_report* rep) {
   if (count < 0 || (count > 0 && !probs)) return MBINV_EINVAL;
   if (dtype != F64 && dtype != F32) return MBINV_EINVAL;
@@ -869,6 +904,36 @@ mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem* probs, int dtype
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return first;
+}
+
+mbinv_status mbinv_create(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,
+                          const mbinv_options* opt) {
+  return guarded([&] { return mbinv_create_impl(out, n, k, dtype, M, ld, opt); });
+}
+mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
+  return guarded([&] { return mbinv_block_impl(c, i, j, out, ldo, rep); });
+}
+mbinv_status mbinv_blocks(mbinv_ctx* c, int64_t count, const int64_t* ij, void* const* outs, const int64_t* ldos,
+                          int width, mbinv_report* rep) {
+  return guarded([&] { return mbinv_blocks_impl(c, count, ij, outs, ldos, width, rep); });
+}
+mbinv_status mbinv_all_blocks(mbinv_ctx* c, void* out, int64_t ldo, const uint8_t* done, mbinv_block_done_cb cb,
+                              void* user, mbinv_report* rep) {
+  return guarded([&] { return mbinv_all_blocks_impl(c, out, ldo, done, cb, user, rep); });
+}
+mbinv_status mbinv_block_row(mbinv_ctx* c, int64_t i, void* out, int64_t ldo, mbinv_report* rep) {
+  return guarded([&] { return mbinv_block_row_impl(c, i, out, ldo, rep); });
+}
+mbinv_status mbinv_block_col(mbinv_ctx* c, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
+  return guarded([&] { return mbinv_block_col_impl(c, j, out, ldo, rep); });
+}
+mbinv_status mbinv_backward(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM, int64_t ldd,
+                            mbinv_report* rep) {
+  return guarded([&] { return mbinv_backward_impl(c, i, j, G, ldg, dM, ldd, rep); });
+}
+mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem* probs, int dtype, const mbinv_options* opt,
+                                  mbinv_report* rep) {
+  return guarded([&] { return mbinv_batched_blocks_impl(count, probs, dtype, opt, rep); });
 }
 
 }  // extern "C"
