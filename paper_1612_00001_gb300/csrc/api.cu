@@ -157,7 +157,9 @@ size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int G, int inv_chunk) {
     for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
     bytes += pack_bytes((int)c->b, c->opt.bf16_slices, ops * G);
   }
-  bytes += (size_t)c->b * c->b * 8 + (4u << 20);  // output staging, descriptors
+  size_t ops = 0;
+  for (const Step& st : S.steps) ops += st.inv.size() + st.gemm.size();
+  bytes += (size_t)G * ops * 2 * sizeof(GemmDesc) + S.steps.size() * 1024 + (64u << 10);  // descriptors
   return bytes;
 }
 
