@@ -2,9 +2,10 @@
 """Throughput of the block recursive inverse (blocks of M^-1 per second).
 
 Workload (default): n = 4096, k = 8 (b = 512), M = uniform[-1, 1) + n I
-(seed 0), every block N_ij computed one at a time; a step is
-``--blocks-per-step`` consecutive blocks in row-major order (cycling through
-all k^2 blocks over the steps).  M (134 MB FP64) is larger than L2 (129 MB)
+(seed 0), every block N_ij computed by its own run of the recursion; a step
+is ``--blocks-per-step`` consecutive blocks in row-major order (cycling
+through all k^2 blocks over the steps), whose runs are executed together
+level by level (``--together``, 0 = one run after the other).  M (134 MB FP64) is larger than L2 (129 MB)
 and L2 is also flushed between timed steps.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
@@ -45,8 +46,9 @@ def parse():
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
     p.add_argument("--slices", type=int, default=3)
     p.add_argument("--refine", type=int, default=0)
-    p.add_argument("--together", type=int, default=0,
-                   help="run each step's blocks as that many independent runs executed together (0: one at a time)")
+    p.add_argument("--together", type=int, default=8,
+                   help="run each step's blocks as independent runs, this many executed together level by level "
+                        "in grouped launches (0: one run after the other)")
     p.add_argument("--matrix", default="uniform", choices=["uniform", "haar", "spd"])
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--batched", type=int, default=0,
