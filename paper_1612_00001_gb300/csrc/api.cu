@@ -415,65 +415,163 @@ mbinv_status row_or_col(mbinv_ctx* c, int64_t t, bool row, void* out, int64_t ld
   return blocks_to(c, ij, outs, ldos, (int)c->k, rep);
 }
 
-// Mixed path with one two-sided refinement step:
+// Mixed path with one two-sided refinement step (refined_blocks below):
 //   X_i = block row i, Y_j = block column j of M^-1 from the mixed sweep,
 //   R   = E_i^T - X_i M                      (FP64 accumulation)
 //   N_ij <- X_i E_j + R Y_j                  (FP64)
 // With dX, dY the errors of X_i, Y_j the result differs from N_ij by
 // -dX M dY: the error is squared when it is small.
-mbinv_status refined_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
-  const int64_t n = c->n, b = c->b;
-  const int64_t bi = block_extent(c, i), bj = block_extent(c, j);
-  CU(c->rowbuf.ensure((size_t)b * n * 4 + 256));
-  CU(c->colbuf.ensure((size_t)n * b * 4 + 256));
-  CU(c->resid.ensure((size_t)b * n * 8 + (size_t)b * b * 8 + 512));
+
+// Uploads and runs a list of GEMM descriptors of one element-type combination.
+mbinv_status gemm_list(mbinv_ctx* c, int combo, std::vector<GemmDesc>& ds) {
+  if (ds.empty()) return MBINV_OK;
+  int bm, bn, tiles = 0;
+  gemm_tile_shape(combo, &bm, &bn);
+  for (GemmDesc& d : ds) {
+    d.tiles_n = (d.n + bn - 1) / bn;
+    d.tile_start = tiles;
+    tiles += ((d.m + bm - 1) / bm) * d.tiles_n;
+  }
+  CU(c->gemmdesc.ensure(ds.size() * sizeof(GemmDesc) + 256));
+  CU(cudaMemcpyAsync(c->gemmdesc.p, ds.data(), ds.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, c->stream));
+  CU(launch_gemm_grouped(combo, (const GemmDesc*)c->gemmdesc.p, (int)ds.size(), tiles, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return MBINV_OK;
+}
+
+GemmDesc gdesc(const void* A, int64_t lda, const void* B, int64_t ldb, const void* Cin, int64_t ldcin, void* C,
+               int64_t ldc, int m, int n, int k, double alpha, double beta) {
+  GemmDesc d{};
+  d.A = A;
+  d.lda = lda;
+  d.B = B;
+  d.ldb = ldb;
+  d.Cin = Cin;
+  d.ldcin = ldcin;
+  d.C = C;
+  d.ldc = ldc;
+  d.m = m;
+  d.n = n;
+  d.k = k;
+  d.alpha = alpha;
+  d.beta = beta;
+  return d;
+}
+
+// Refinement of many blocks at once: the block rows X_i and block columns Y_j
+// they need are computed once (every block of them by its own run, all runs
+// executed together), then one residual E_i^T - X_i M per distinct row and
+// one correction X_i E_j + R_i Y_j per block, each set in one grouped launch.
+mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, int64_t>>& v,
+                            const std::vector<void*>& outs, const std::vector<int64_t>& ldos, mbinv_report* rep) {
+  const int64_t n = c->n, b = c->b, k = c->k;
+  std::map<int64_t, int> rows, cols;
+  for (auto& p : v) {
+    rows.emplace(p.first, (int)rows.size());
+    cols.emplace(p.second, (int)cols.size());
+  }
+  const size_t rsz = (size_t)b * n, csz = (size_t)n * b;
+  CU(c->rowbuf.ensure(rows.size() * rsz * 4 + 256));
+  CU(c->colbuf.ensure(cols.size() * csz * 4 + 256));
+  CU(c->resid.ensure(rows.size() * rsz * 8 + v.size() * (size_t)b * b * 8 + 512));
+  float* X = (float*)c->rowbuf.p;  // X_i at X + rows[i] * rsz, leading dimension n
+  float* Y = (float*)c->colbuf.p;  // Y_j at Y + cols[j] * csz, leading dimension b
+  // every block of the needed rows and columns, each computed once
+  std::vector<std::pair<int64_t, int64_t>> ij;
+  std::vector<void*> dst;
+  std::vector<int64_t> ld;
+  std::vector<std::pair<int64_t, int64_t>> copies;  // blocks also needed in a column
+  for (auto& r : rows)
+    for (int64_t q = 0; q < k; ++q) {
+      ij.emplace_back(r.first, q);
+      dst.push_back(X + r.second * rsz + q * b);
+      ld.push_back(n);
+      if (cols.count(q)) copies.emplace_back(r.first, q);
+    }
+  for (auto& cc : cols)
+    for (int64_t q = 0; q < k; ++q) {
+      if (rows.count(q)) continue;
+      ij.emplace_back(q, cc.first);
+      dst.push_back(Y + cc.second * csz + q * b * b);
+      ld.push_back(b);
+    }
   const int saved_dtype = c->dtype;
   c->dtype = F32;  // the sweeps write FP32 blocks
-  mbinv_status s = row_or_col(c, i, true, c->rowbuf.p, n, rep);
-  if (s == MBINV_OK) s = row_or_col(c, j, false, c->colbuf.p, b, rep);
+  mbinv_status s = blocks_to(c, ij, dst, ld, kDefaultWidth, rep);
   c->dtype = saved_dtype;
   if (s != MBINV_OK) return s;
-  double* R = (double*)c->resid.p;  // bi x n
-  double* Nij = R + (size_t)b * n;   // bi x bj
-  double* acc = Nij + (size_t)b * b;
-  const int cm = c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64;
-  s = gemm1(c, cm, c->rowbuf.p, n, 0, c->dM, c->ldm, 0, nullptr, 0, R, n, (int)bi, (int)n, (int)n, -1.0, 0.0);
+  for (auto& p : copies) {
+    const int64_t bi = block_extent(c, p.first), bj = block_extent(c, p.second);
+    CU(cudaMemcpy2DAsync(Y + cols[p.second] * csz + p.first * b * b, (size_t)b * 4,
+                         X + rows[p.first] * rsz + p.second * b, (size_t)n * 4, (size_t)bj * 4, (size_t)bi,
+                         cudaMemcpyDeviceToDevice, c->stream));
+  }
+  // R_i = -X_i M + E_i^T
+  double* R = (double*)c->resid.p;
+  double* Nb = R + rows.size() * rsz;
+  std::vector<GemmDesc> ds;
+  for (auto& r : rows)
+    ds.push_back(gdesc(X + r.second * rsz, n, c->dM, c->ldm, nullptr, 0, R + r.second * rsz, n,
+                       (int)block_extent(c, r.first), (int)n, (int)n, -1.0, 0.0));
+  s = gemm_list(c, c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64, ds);
   if (s != MBINV_OK) return s;
-  add_eye_kernel<<<(unsigned)((bi + 255) / 256), 256, 0, c->stream>>>(R, n, i * b, bi);
-  CU(cudaGetLastError());
-  CU(cudaMemsetAsync(acc, 0, sizeof(double), c->stream));
-  sumsq_kernel<<<64, 256, 0, c->stream>>>(R, n, bi, n, acc);
-  CU(cudaGetLastError());
-  convert_kernel<float, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
-      (const float*)c->rowbuf.p + j * b, n, Nij, bj, bi, bj);
-  CU(cudaGetLastError());
-  s = gemm1(c, G_F64F32_F64, R, n, 0, c->colbuf.p, b, 0, Nij, bj, Nij, bj, (int)bi, (int)bj, (int)n, 1.0, 1.0);
-  if (s != MBINV_OK) return s;
-  double hacc = 0;
-  CU(cudaMemcpyAsync(&hacc, acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  const bool out_dev = is_device_ptr(out);
-  const size_t es = dtype_size(c->dtype);
-  if (c->dtype == F64) {
-    CU(cudaMemcpy2DAsync(out, (size_t)ldo * es, Nij, (size_t)bj * 8, (size_t)bj * 8, (size_t)bi,
-                         out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-  } else {
-    CU(c->outtmp.ensure((size_t)b * b * 8 + 256));
-    convert_kernel<double, float><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
-        Nij, bj, (float*)c->outtmp.p, bj, bi, bj);
+  double rmax = 0;
+  for (auto& r : rows) {
+    const int64_t bi = block_extent(c, r.first);
+    double* Ri = R + r.second * rsz;
+    add_eye_kernel<<<(unsigned)((bi + 255) / 256), 256, 0, c->stream>>>(Ri, n, r.first * b, bi);
     CU(cudaGetLastError());
-    CU(cudaMemcpy2DAsync(out, (size_t)ldo * es, c->outtmp.p, (size_t)bj * 4, (size_t)bj * 4, (size_t)bi,
-                         out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    double* acc = Nb + v.size() * (size_t)b * b;
+    CU(cudaMemsetAsync(acc, 0, sizeof(double), c->stream));
+    sumsq_kernel<<<64, 256, 0, c->stream>>>(Ri, n, bi, n, acc);
+    CU(cudaGetLastError());
+    double h = 0;
+    CU(cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    rmax = std::max(rmax, std::sqrt(h / (double)bi));
+  }
+  // N_ij = X_i E_j + R_i Y_j
+  ds.clear();
+  for (size_t t = 0; t < v.size(); ++t) {
+    const int64_t i = v[t].first, j = v[t].second;
+    const int64_t bi = block_extent(c, i), bj = block_extent(c, j);
+    double* Nt = Nb + t * (size_t)b * b;
+    convert_kernel<float, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+        X + rows[i] * rsz + j * b, n, Nt, bj, bi, bj);
+    CU(cudaGetLastError());
+    ds.push_back(gdesc(R + rows[i] * rsz, n, Y + cols[j] * csz, b, Nt, bj, Nt, bj, (int)bi, (int)bj, (int)n, 1.0,
+                       1.0));
+  }
+  s = gemm_list(c, G_F64F32_F64, ds);
+  if (s != MBINV_OK) return s;
+  const size_t es = dtype_size(c->dtype);
+  for (size_t t = 0; t < v.size(); ++t) {
+    const int64_t bi = block_extent(c, v[t].first), bj = block_extent(c, v[t].second);
+    double* Nt = Nb + t * (size_t)b * b;
+    const bool dev = is_device_ptr(outs[t]);
+    if (c->dtype == F64) {
+      CU(cudaMemcpy2DAsync(outs[t], (size_t)ldos[t] * es, Nt, (size_t)bj * 8, (size_t)bj * 8, (size_t)bi,
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      CU(c->outtmp.ensure((size_t)b * b * 8 + 256));
+      convert_kernel<double, float><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+          Nt, bj, (float*)c->outtmp.p, bj, bi, bj);
+      CU(cudaGetLastError());
+      CU(cudaMemcpy2DAsync(outs[t], (size_t)ldos[t] * es, c->outtmp.p, (size_t)bj * 4, (size_t)bj * 4, (size_t)bi,
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    }
   }
   CU(cudaStreamSynchronize(c->stream));
   if (rep) {
-    rep->gemm_flops += 2.0 * bi * n * n + 2.0 * bi * bj * n;
-    rep->launches += 5;
-    rep->rel_residual = std::sqrt(hacc / (double)bi);
+    for (auto& r : rows) rep->gemm_flops += 2.0 * block_extent(c, r.first) * n * n;
+    for (auto& p : v) rep->gemm_flops += 2.0 * block_extent(c, p.first) * block_extent(c, p.second) * n;
+    rep->launches += 2 + 2 * rows.size() + v.size();
+    rep->rel_residual = std::max(rep->rel_residual, rmax);
     rep->peak_device_bytes =
         std::max(rep->peak_device_bytes, c->peak + c->rowbuf.bytes + c->colbuf.bytes + c->resid.bytes);
   }
-  if (!(std::sqrt(hacc / (double)bi) < 1.0)) return MBINV_ENOTCONV;
+  if (!(rmax < 1.0)) return MBINV_ENOTCONV;
   return MBINV_OK;
 }
 
@@ -623,7 +721,7 @@ static mbinv_status mbinv_block_impl(mbinv_ctx* c, int64_t i, int64_t j, void* o
   mbinv_status s;
   if (c->opt.precision == MBINV_MIXED_BF16 && c->opt.refine_steps > 0 && !c->in_sweep) {
     c->in_sweep = true;
-    s = refined_block(c, i, j, out, ldo, rep);
+    s = refined_blocks(c, {{i, j}}, {out}, {ldo}, rep);
     c->in_sweep = false;
   } else {
     s = blocks_to(c, {{i, j}}, {out}, {ldo}, 1, rep);
@@ -649,25 +747,9 @@ static mbinv_status mbinv_blocks_impl(mbinv_ctx* c, int64_t count, const int64_t
   auto t0 = std::chrono::steady_clock::now();
   mbinv_status s = MBINV_OK;
   if (c->opt.precision == MBINV_MIXED_BF16 && c->opt.refine_steps > 0) {
-    for (int64_t t = 0; t < count && s == MBINV_OK; ++t) {
-      mbinv_report r;
-      start_report(&r);
-      c->in_sweep = true;
-      s = refined_block(c, v[t].first, v[t].second, o[t], l[t], &r);
-      c->in_sweep = false;
-      if (rep) {
-        rep->gemm_flops += r.gemm_flops;
-        rep->inv_flops += r.inv_flops;
-        rep->frames += r.frames;
-        rep->inversions += r.inversions;
-        rep->launches += r.launches;
-        rep->gemm_launches += r.gemm_launches;
-        rep->gemm_device_seconds += r.gemm_device_seconds;
-        rep->inv_device_seconds += r.inv_device_seconds;
-        rep->rel_residual = std::max(rep->rel_residual, r.rel_residual);
-        rep->peak_device_bytes = std::max(rep->peak_device_bytes, r.peak_device_bytes);
-      }
-    }
+    c->in_sweep = true;
+    s = refined_blocks(c, v, o, l, rep);
+    c->in_sweep = false;
   } else {
     s = blocks_to(c, v, o, l, width > 0 ? width : kDefaultWidth, rep);
   }
@@ -837,7 +919,9 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
         continue;
       }
       used += need;
-      ic = std::min(ic, S->inv_chunk);
+      // without a cap every member's inverses of a step share one launch
+      // sequence; under a cap each member keeps the chunk that fits it
+      ic = o.device_cap_bytes ? std::min(ic, S->inv_chunk) : (ic == INT_MAX ? 0 : ic) + S->inv_chunk;
       Job J;
       J.dM = c->dM;
       J.ldm = c->ldm;

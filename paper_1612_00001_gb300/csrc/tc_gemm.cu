@@ -34,7 +34,7 @@ namespace tc {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 6;
+constexpr int STAGES = 3;  // 97 KB of shared memory: two CTAs per SM overlap epilogue and main loop
 constexpr int THREADS = 128;
 constexpr uint32_t TILE_A_BYTES = BM * BK * 2;  // 16 KB
 constexpr uint32_t TILE_B_BYTES = BN * BK * 2;  // 16 KB
@@ -139,7 +139,7 @@ __device__ __forceinline__ void split_bf16(float x, int S, __nv_bfloat16 (&s)[3]
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams P, const TcProblem* __restrict__ probs) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];

@@ -86,3 +86,20 @@ def test_mixed_all_blocks_batched_levels(mb):
         # FP32 frame values: the k = 8 recursion amplifies rounding ~1e4-1e6x
         tol = max(1e-3, 1e9 * oracle.sensitivity_floor(ref32, 8, i, j))
         assert oracle.rel_fro(got, ref) < tol
+
+
+def test_mixed_refined_many_blocks_share_rows_and_columns(mb):
+    """Refining all 16 blocks at once computes each needed block row and
+    column once; every block still reaches the refined accuracy and equals
+    the block refined alone."""
+    m = bi.uniform_shift(256, 3)
+    M = torch.tensor(m, device="cuda")
+    ctx = mb.Context(M, 4, precision="mixed", refine=1)
+    ij = [(i, j) for i in range(4) for j in range(4)]
+    outs = ctx.blocks(ij)
+    inv = np.linalg.inv(m)
+    for (i, j), o in zip(ij, outs):
+        got = to_np(o)
+        assert oracle.rel_fro(got, inv[i * 64:(i + 1) * 64, j * 64:(j + 1) * 64]) < 1e-10, (i, j)
+    alone = to_np(mb.Context(M, 4, precision="mixed", refine=1).block(2, 1))
+    assert oracle.rel_fro(alone, to_np(outs[9])) < 1e-13
