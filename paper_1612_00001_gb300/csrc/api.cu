@@ -147,6 +147,14 @@ mbinv_status set_border(mbinv_ctx* c, int mode) {
   return MBINV_OK;
 }
 
+// Inverse scratch is bounded even without a cap: at most this many matrices
+// of order b go into one batched inverse launch sequence.
+constexpr size_t kInvScratchBudget = 8ull << 30;
+int max_inv_chunk(int b, int prec) {
+  const size_t per = inv_scratch_bytes(b, prec, 1);
+  return (int)std::max<size_t>(1, std::min<size_t>(1 << 20, kInvScratchBudget / per));
+}
+
 // Memory of running G requests together (beyond M).
 size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int G, int inv_chunk) {
   const int prec = c->opt.precision;
@@ -198,7 +206,7 @@ mbinv_status get_plan(mbinv_ctx* c, int64_t i, int64_t j, int G, const Schedule*
     bool ok = false;
     for (int z : {0, 64, 16, 4, 1}) {
       Schedule T = build_schedule(P, z);
-      const int full = std::max(1, T.max_inv_batch) * G;
+      const int full = std::min(std::max(1, T.max_inv_batch) * G, max_inv_chunk((int)c->b, c->opt.precision));
       for (int ic : {full, 256, 64, 16, 4, 1}) {
         if (ic > full) continue;
         if (cap == 0 || base + run_bytes(c, T, G, ic) <= cap) {
@@ -901,6 +909,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     std::vector<int64_t> members;
     size_t used = 0;
     int ic = INT_MAX;
+    int64_t bmax_wave = 1;
     size_t q = q0;
     for (; q < order.size(); ++q) {
       mbinv_ctx* c = ctxs[order[q]];
@@ -922,6 +931,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
       // without a cap every member's inverses of a step share one launch
       // sequence; under a cap each member keeps the chunk that fits it
       ic = o.device_cap_bytes ? std::min(ic, S->inv_chunk) : (ic == INT_MAX ? 0 : ic) + S->inv_chunk;
+      bmax_wave = std::max<int64_t>(bmax_wave, c->b);
       Job J;
       J.dM = c->dM;
       J.ldm = c->ldm;
@@ -940,7 +950,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     }
     q0 = q;
     if (members.empty()) continue;
-    env.inv_chunk = std::max(1, ic);
+    env.inv_chunk = std::max(1, std::min(ic, max_inv_chunk((int)bmax_wave, o.precision)));
     mbinv_status s = run_jobs(env, jobs);
     if (s == MBINV_ECUDA) {
       last_cuda_error() = env.last_error;
