@@ -234,22 +234,31 @@ __global__ void __launch_bounds__(THREADS, 2)
       float v[16];
       tmem_ld16(trow + c0, v);
       if (P.mode == 0) {
-        if (row < P.m) {
-          float* out = (float*)pr.out + (int64_t)row * pr.ldo;
+        // stage the warp's 32 x 16 piece through shared memory (the ring is
+        // free once every MMA has completed) so that each row is read and
+        // written as one contiguous segment by consecutive lanes
+        float* T = (float*)base + warp * (32 * 17);
 #pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            const int col = tn * BN + c0 + t;
-            if (col < P.n) {
-              float y = P.alpha * v[t];
-              if (pr.cin) {
-                const double ci = pr.cin_f64 ? ((const double*)pr.cin)[(int64_t)row * pr.ldcin + col]
-                                             : (double)((const float*)pr.cin)[(int64_t)row * pr.ldcin + col];
-                y = (float)((double)P.beta * ci + (double)y);
-              }
-              out[col] = y;
+        for (int t = 0; t < 16; ++t) T[lane * 17 + t] = v[t];
+        __syncwarp();
+        const int rr = lane >> 4, cc = lane & 15;  // two rows of 16 columns per pass
+        const int col = tn * BN + c0 + cc;
+#pragma unroll 4
+        for (int r2 = 0; r2 < 32; r2 += 2) {
+          const int lr = r2 + rr;
+          const int grow = tm * BM + warp * 32 + lr;
+          if (grow < P.m && col < P.n) {
+            // FP32 epilogue: the output is FP32, and FP64 arithmetic is scarce here
+            float y = P.alpha * T[lr * 17 + cc];
+            if (pr.cin) {
+              const float ci = pr.cin_f64 ? (float)((const double*)pr.cin)[(int64_t)grow * pr.ldcin + col]
+                                          : ((const float*)pr.cin)[(int64_t)grow * pr.ldcin + col];
+              y = fmaf(P.beta, ci, y);
             }
+            ((float*)pr.out)[(int64_t)grow * pr.ldo + col] = y;
           }
         }
+        __syncwarp();
       } else {
         // D^T slices into the packed K-major slab of the next product:
         // element (n, k) of slab [out_slab][q] is D[k][n]
