@@ -36,6 +36,7 @@ namespace mbinv {
 namespace {
 
 constexpr int kPanelThreads = 256;
+constexpr int kMaxPanelLanes = 8;  // panel width up to 256 columns: 8 per lane
 constexpr int kSmemLimit = 200 * 1024;
 
 template <typename T>
@@ -84,13 +85,16 @@ __global__ void gj_init_kernel(const InvDesc* __restrict__ descs, int in_dtype) 
 // its shared memory (R = ceil(b / CL)); the CTAs exchange pivot candidates
 // and the pivot row through distributed shared memory, so that the
 // per-column work (the elimination of nb columns from every row) is spread
-// over CL SMs instead of one.  Every CTA takes the same pivot decision.
+// over CL SMs instead of one.  Every warp of every CTA takes the same pivot
+// decision from the same candidates, so one column costs one CTA barrier and
+// two cluster barriers.
 template <typename TW>
 __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* __restrict__ descs, int p, int nb,
                                                                  DevStatus* status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NW = kPanelThreads / 32;
   const int CL = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
   const InvDesc d = descs[blockIdx.x / CL];
@@ -102,79 +106,71 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   if (nb <= 0) return;
   const int R = (b + CL - 1) / CL;
   const int r0 = min(b, q * R), r1 = min(b, r0 + R);
-  TW* P = (TW*)smem_raw;   // P[(i - r0) * ldp + t] is X[i][p + t]
+  TW* P = (TW*)smem_raw;                // P[(i - r0) * ldp + t] is X[i][p + t]
   TW* prow = P + (size_t)R * ldp;       // pivot row before scaling (nb)
-  TW* srow = prow + ldp;                // scaled pivot row (nb)
-  TW* jrow = srow + ldp;                // old row j, for the owner of row r (nb)
-  __shared__ TW cand_v[2];
-  __shared__ int cand_i[2];
-  __shared__ TW red_v[kPanelThreads / 32];
-  __shared__ int red_i[kPanelThreads / 32];
+  TW* jrow = prow + ldp;                // old row j, for the owner of row r (nb)
   int* piv_hist = (int*)(jrow + ldp);   // pivot row of every column of the panel (nb)
+  __shared__ TW cand_v[2][NW];
+  __shared__ int cand_i[2][NW];
   TW* X = (TW*)d.work;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kPanelThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < (r1 - r0) * nb; e += kPanelThreads) {
     const int i = e / nb, t = e % nb;
     P[i * ldp + t] = X[(int64_t)(r0 + i) * b + p + t];
   }
   const double amax = __longlong_as_double((long long)*d.amax);
   const TW tol = (TW)((double)b * (double)eps_of<TW>() * amax);
-  cluster.sync();
+  __syncthreads();
 
   for (int t = 0; t < nb; ++t) {
     const int j = p + t;
     const int buf = t & 1;
-    // ---- local pivot candidate: first row of largest magnitude, rows >= j
-    TW best = (TW)-1;
-    int bi = b;
-    for (int i = max(j, r0) + tid; i < r1; i += kPanelThreads) {
-      const TW v = fabs(P[(i - r0) * ldp + t]);
-      if (v > best) { best = v; bi = i; }  // NaN never wins
+    // ---- this warp's pivot candidate: first row of largest magnitude, rows >= j
+    {
+      TW best = (TW)-1;
+      int bi = b;
+      for (int i = max(j, r0) + tid; i < r1; i += kPanelThreads) {
+        const TW v = fabs(P[(i - r0) * ldp + t]);
+        if (v > best) { best = v; bi = i; }  // NaN never wins
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const TW ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { cand_v[buf][warp] = best; cand_i[buf][warp] = bi; }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const TW ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      TW bv = red_v[0];
-      int bix = red_i[0];
-      for (int w = 1; w < nwarps; ++w)
-        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bix)) { bv = red_v[w]; bix = red_i[w]; }
-      cand_v[buf] = bv;
-      cand_i[buf] = bix;
-    }
-    cluster.sync();  // candidates of every CTA visible
-    // ---- global pivot: the same decision in every CTA (one remote load per rank)
-    if (warp == 0) {
+    cluster.sync();  // #1: the candidates of every warp of every CTA are visible
+    // ---- global pivot, computed by every warp from the same CL x NW candidates
+    int r;
+    TW gv;
+    {
       TW v = (TW)-1;
       int ix = b;
-      if (lane < CL) {
-        v = *cluster.map_shared_rank(&cand_v[buf], lane);
-        ix = *cluster.map_shared_rank(&cand_i[buf], lane);
+      for (int u = lane; u < CL * NW; u += 32) {
+        const TW cv = *cluster.map_shared_rank(&cand_v[buf][u % NW], u / NW);
+        const int ci = *cluster.map_shared_rank(&cand_i[buf][u % NW], u / NW);
+        if (cv > v || (cv == v && ci < ix)) { v = cv; ix = ci; }
       }
       for (int o = 16; o > 0; o >>= 1) {
         const TW ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
         if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
       }
-      if (lane == 0) {
-        if (ix >= b) ix = j;  // every candidate NaN
-        piv_hist[t] = ix;
-        if (q == 0) {
-          if (!(v > tol) || !isfinite((double)v)) {
-            atomicExch(&status->singular, 1);
-            atomicMin(&status->tag, d.tag);
-            if (d.flag) atomicExch(d.flag, 1);
-          }
-          d.perm[j] = ix;
+      r = ix >= b ? j : ix;  // every candidate NaN: keep the row
+      gv = v;
+    }
+    if (tid == 0) {
+      piv_hist[t] = r;
+      if (q == 0) {
+        if (!(gv > tol) || !isfinite((double)gv)) {
+          atomicExch(&status->singular, 1);
+          atomicMin(&status->tag, d.tag);
+          if (d.flag) atomicExch(d.flag, 1);
         }
+        d.perm[j] = r;
       }
     }
-    __syncthreads();
-    const int r = piv_hist[t];
     const int oj = j / R, orr = r / R;  // owners of rows j and r
     // ---- read the pivot row (old row r) and, for the owner of r, old row j
     {
@@ -185,31 +181,40 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
         for (int c = tid; c < nb; c += kPanelThreads) jrow[c] = sj[c];
       }
     }
-    cluster.sync();  // every CTA has read rows j and r
-    // ---- scaled pivot row; the owners write the exchanged rows
+    cluster.sync();  // #2: every CTA has read rows j and r; prow and jrow are complete
+    // ---- scale the pivot row and eliminate column j (warp per row, lane per
+    // column).  Row j receives the scaled pivot row; row r, when it moved,
+    // starts from the old row j (jrow).
+    // the scaled pivot row, once per warp: lane holds columns lane + 32 u
     const TW piv = prow[t];
-    for (int c = tid; c < nb; c += kPanelThreads) srow[c] = ((c == t) ? (TW)1 : prow[c]) / piv;
-    __syncthreads();
-    if (q == oj)
-      for (int c = tid; c < nb; c += kPanelThreads) P[(size_t)(j - r0) * ldp + c] = srow[c];
-    if (q == orr && r != j)
-      for (int c = tid; c < nb; c += kPanelThreads) P[(size_t)(r - r0) * ldp + c] = jrow[c];
-    __syncthreads();
-    // ---- eliminate column j from the CTA's rows (warp per row, lane per column)
-    for (int i = r0 + warp; i < r1; i += nwarps) {
-      if (i == j) continue;
+    TW sc[kMaxPanelLanes];
+#pragma unroll
+    for (int u = 0; u < kMaxPanelLanes; ++u) {
+      const int c = lane + 32 * u;
+      sc[u] = (c < nb) ? ((c == t) ? (TW)1 : prow[c]) / piv : (TW)0;
+    }
+    for (int i = r0 + warp; i < r1; i += NW) {
       TW* xi = P + (size_t)(i - r0) * ldp;
-      const TW f = xi[t];
-      __syncwarp();
-      if (f != (TW)0) {
-        for (int c = lane; c < nb; c += 32) {
-          const TW base = (c == t) ? (TW)0 : xi[c];
-          xi[c] = base - f * srow[c];
+      if (i == j) {
+#pragma unroll
+        for (int u = 0; u < kMaxPanelLanes; ++u) {
+          const int c = lane + 32 * u;
+          if (c < nb) xi[c] = sc[u];
+        }
+        continue;
+      }
+      const TW* src = (i == r && r != j) ? jrow : xi;
+      const TW f = src[t];
+#pragma unroll
+      for (int u = 0; u < kMaxPanelLanes; ++u) {
+        const int c = lane + 32 * u;
+        if (c < nb) {
+          const TW base = (c == t) ? (TW)0 : src[c];
+          xi[c] = (f != (TW)0) ? base - f * sc[u] : base;
         }
       }
-      __syncwarp();
     }
-    __syncthreads();
+    __syncthreads();  // the next column's candidates read the eliminated rows
   }
   // panel back to global memory
   for (int e = tid; e < (r1 - r0) * nb; e += kPanelThreads) {
@@ -331,8 +336,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   // cluster size: spread the panel over more SMs when few matrices are batched
   int CL = 8;
   while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
-  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
-  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW);
+  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
+  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW);
   if (psmem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
@@ -345,7 +350,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * CL, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
-    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
+    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 3) * (w + 1) * sizeof(TW);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -382,7 +387,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
 
 int inv_panel_width(int b, int wtype) {
   const size_t es = wtype == F64 ? 8 : 4;
-  if ((size_t)b * (b + 1) * es <= 132 * 1024) return b;  // whole matrix in one panel
+  if (b <= 32 * kMaxPanelLanes && (size_t)b * (b + 1) * es <= 132 * 1024) return b;  // whole matrix in one panel
   return 32;
 }
 
