@@ -36,7 +36,7 @@ namespace mbinv {
 namespace {
 
 constexpr int kPanelThreads = 256;
-constexpr int kMaxPanelLanes = 8;  // panel width up to 256 columns: 8 per lane
+constexpr int kMaxPanelWidth = 256;
 constexpr int kSmemLimit = 200 * 1024;
 
 template <typename T>
@@ -86,7 +86,7 @@ __global__ void gj_init_kernel(const InvDesc* __restrict__ descs, int in_dtype) 
 // and the pivot row through distributed shared memory, so that the
 // per-column work (the elimination of nb columns from every row) is spread
 // over CL SMs instead of one.  Every warp of every CTA takes the same pivot
-// decision from the same candidates, so one column costs one CTA barrier and
+// decision from the same candidates, so one column costs two CTA barriers and
 // two cluster barriers.
 template <typename TW>
 __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* __restrict__ descs, int p, int nb,
@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   TW* P = (TW*)smem_raw;                // P[(i - r0) * ldp + t] is X[i][p + t]
   TW* prow = P + (size_t)R * ldp;       // pivot row before scaling (nb)
   TW* jrow = prow + ldp;                // old row j, for the owner of row r (nb)
-  int* piv_hist = (int*)(jrow + ldp);   // pivot row of every column of the panel (nb)
+  TW* srow = jrow + ldp;                // scaled pivot row (nb)
+  int* piv_hist = (int*)(srow + ldp);   // pivot row of every column of the panel (nb)
   __shared__ TW cand_v[2][NW];
   __shared__ int cand_i[2][NW];
   TW* X = (TW*)d.work;
@@ -185,33 +186,21 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
     // ---- scale the pivot row and eliminate column j (warp per row, lane per
     // column).  Row j receives the scaled pivot row; row r, when it moved,
     // starts from the old row j (jrow).
-    // the scaled pivot row, once per warp: lane holds columns lane + 32 u
+    // the scaled pivot row, once per CTA (FP64 divisions are dear: one per column)
     const TW piv = prow[t];
-    TW sc[kMaxPanelLanes];
-#pragma unroll
-    for (int u = 0; u < kMaxPanelLanes; ++u) {
-      const int c = lane + 32 * u;
-      sc[u] = (c < nb) ? ((c == t) ? (TW)1 : prow[c]) / piv : (TW)0;
-    }
+    for (int c = tid; c < nb; c += kPanelThreads) srow[c] = ((c == t) ? (TW)1 : prow[c]) / piv;
+    __syncthreads();
     for (int i = r0 + warp; i < r1; i += NW) {
       TW* xi = P + (size_t)(i - r0) * ldp;
       if (i == j) {
-#pragma unroll
-        for (int u = 0; u < kMaxPanelLanes; ++u) {
-          const int c = lane + 32 * u;
-          if (c < nb) xi[c] = sc[u];
-        }
+        for (int c = lane; c < nb; c += 32) xi[c] = srow[c];
         continue;
       }
       const TW* src = (i == r && r != j) ? jrow : xi;
       const TW f = src[t];
-#pragma unroll
-      for (int u = 0; u < kMaxPanelLanes; ++u) {
-        const int c = lane + 32 * u;
-        if (c < nb) {
-          const TW base = (c == t) ? (TW)0 : src[c];
-          xi[c] = (f != (TW)0) ? base - f * sc[u] : base;
-        }
+      for (int c = lane; c < nb; c += 32) {
+        const TW base = (c == t) ? (TW)0 : src[c];
+        xi[c] = (f != (TW)0) ? base - f * srow[c] : base;
       }
     }
     __syncthreads();  // the next column's candidates read the eliminated rows
@@ -336,8 +325,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   // cluster size: spread the panel over more SMs when few matrices are batched
   int CL = 8;
   while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
-  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
-  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 3) * (nb + 1) * sizeof(TW);
+  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
+  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW);
   if (psmem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
@@ -350,7 +339,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * CL, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
-    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 3) * (w + 1) * sizeof(TW);
+    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -387,7 +376,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
 
 int inv_panel_width(int b, int wtype) {
   const size_t es = wtype == F64 ? 8 : 4;
-  if (b <= 32 * kMaxPanelLanes && (size_t)b * (b + 1) * es <= 132 * 1024) return b;  // whole matrix in one panel
+  if (b <= kMaxPanelWidth && (size_t)b * (b + 1) * es <= 132 * 1024) return b;  // whole matrix in one panel
   return 32;
 }
 
