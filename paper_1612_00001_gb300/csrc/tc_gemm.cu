@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -286,6 +287,191 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
 }
 
+// Persistent variant: one CTA per SM walks the tiles blockIdx.x, +gridDim.x,
+// ... with two TMEM accumulators, so that the epilogue of one tile (warps 2-5)
+// runs under the main loop of the next (warps 0 and 1).
+//   warp 0, one lane:  TMA producer over all the CTA's tiles and K steps;
+//   warp 1:            TMEM allocation (2 x 128 columns); one lane issues the
+//                      MMAs of tile t into accumulator t % 2 once the epilogue
+//                      has drained it, and commits "full" for it;
+//   warps 2-5:         epilogue; warp w reads TMEM lanes 32 (w % 4) ... + 31,
+//                      then arrives "empty" for the accumulator.
+constexpr int PSTAGES = 5;
+constexpr int PTHREADS = 192;
+constexpr uint32_t PTMEM_COLS = 2 * BN;
+
+size_t psmem_bytes() { return PSTAGES * (TILE_A_BYTES + TILE_B_BYTES) + 4 * 32 * 17 * 4 + 1024 + 512; }
+
+__global__ void __launch_bounds__(PTHREADS, 1)
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                              const TcParams P, const TcProblem* __restrict__ probs, int total_tiles) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + PSTAGES * TILE_A_BYTES;
+  float* stage_out = (float*)(sB + PSTAGES * TILE_B_BYTES);  // 4 warps x 32 x 17
+  uint64_t* full = (uint64_t*)(stage_out + 4 * 32 * 17);
+  uint64_t* empty = full + PSTAGES;
+  uint64_t* tfull = empty + PSTAGES;  // [2]
+  uint64_t* tempty = tfull + 2;       // [2]
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  int* failed = (int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_per = P.tiles_m * P.tiles_n;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+    }
+    *failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(PTMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nkb = P.kpad / BK;
+  const int nk = P.npairs * nkb;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      uint32_t it = 0;  // running K-step counter over all tiles
+      for (int tile = blockIdx.x; tile < total_tiles && !*(volatile int*)failed; tile += gridDim.x) {
+        const int g = tile / tiles_per, rem = tile - g * tiles_per;
+        const int tm = rem / P.tiles_n, tn = rem - tm * P.tiles_n;
+        const TcProblem pr = probs[g];
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = (int)(it % PSTAGES);
+          const uint32_t ph = (it / PSTAGES) & 1u;
+          if (it >= PSTAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+            atomicExch(failed, 1);
+            break;
+          }
+          mbar_expect_tx(&full[s], TILE_A_BYTES + TILE_B_BYTES);
+          const int pq = kt / nkb, kb = kt - pq * nkb;
+          tma_load_3d(sA + s * TILE_A_BYTES, &tmA, &full[s], kb * BK, tm * BM, pr.a_slab * P.S + P.pa[pq]);
+          tma_load_3d(sB + s * TILE_B_BYTES, &tmB, &full[s], kb * BK, tn * BN, pr.b_slab * P.S + P.pb[pq]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      uint32_t it = 0;
+      int lt = 0;  // local tile counter
+      for (int tile = blockIdx.x; tile < total_tiles && !*(volatile int*)failed; tile += gridDim.x, ++lt) {
+        const int acc = lt & 1;
+        const uint32_t aph = ((uint32_t)(lt >> 1) & 1u) ^ 1u;  // first use of each buffer passes at once
+        if (!mbar_wait(&tempty[acc], aph)) {
+          atomicExch(failed, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tacc = tmem + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = (int)(it % PSTAGES);
+          const uint32_t ph = (it / PSTAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            atomicExch(failed, 1);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * TILE_A_BYTES), b0 = smem_u32(sB + s * TILE_B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma(tacc, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (kt > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        umma_commit(&tfull[acc]);  // arrives when this tile's MMAs have completed
+        if (!ok) break;
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5
+    const int ew = warp - 2;                 // 0..3
+    const int quarter = warp & 3;            // the TMEM lanes this warp may read
+    float* T = stage_out + ew * (32 * 17);
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++lt) {
+      const int acc = lt & 1;
+      const bool ok = mbar_wait(&tfull[acc], (uint32_t)(lt >> 1) & 1u);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok || *(volatile int*)failed) {
+        if (lane == 0 && P.err) atomicExch(P.err, 1);
+        atomicExch(failed, 1);
+        break;
+      }
+      const int g = tile / tiles_per, rem = tile - g * tiles_per;
+      const int tm = rem / P.tiles_n, tn = rem - tm * P.tiles_n;
+      const TcProblem pr = probs[g];
+      const int row = tm * BM + quarter * 32 + lane;
+      const uint32_t trow = tmem + (uint32_t)(acc * BN) + ((uint32_t)(quarter * 32) << 16);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+        if (P.mode == 0) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) T[lane * 17 + t] = v[t];
+          __syncwarp();
+          const int rr = lane >> 4, cc = lane & 15;
+          const int col = tn * BN + c0 + cc;
+#pragma unroll 4
+          for (int r2 = 0; r2 < 32; r2 += 2) {
+            const int lr = r2 + rr;
+            const int grow = tm * BM + quarter * 32 + lr;
+            if (grow < P.m && col < P.n) {
+              float y = P.alpha * T[lr * 17 + cc];
+              if (pr.cin) {
+                const float ci = pr.cin_f64 ? (float)((const double*)pr.cin)[(int64_t)grow * pr.ldcin + col]
+                                            : ((const float*)pr.cin)[(int64_t)grow * pr.ldcin + col];
+                y = fmaf(P.beta, ci, y);
+              }
+              ((float*)pr.out)[(int64_t)grow * pr.ldo + col] = y;
+            }
+          }
+          __syncwarp();
+        } else if (row < P.okpad) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int col = tn * BN + c0 + t;
+            if (col < P.orows) {
+              __nv_bfloat16 sl[3];
+              split_bf16(P.alpha * v[t], P.S, sl);
+              for (int q = 0; q < P.S; ++q)
+                P.opk[(((int64_t)pr.out_slab * P.S + q) * P.orows + col) * P.okpad + row] = sl[q];
+            }
+          }
+        }
+      }
+      // this warp is done reading the accumulator
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PTMEM_COLS) : "memory");
+  }
+}
+
 // packed slab [slab][q][rows_pad][kpad] <- slices of src (rows x cols, ld), or
 // of its transpose (output row r = source column r).
 __global__ void pack_kernel(const PackDesc* __restrict__ descs, int S, int rows_pad, int kpad, __nv_bfloat16* dst) {
@@ -368,14 +554,19 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
   if (!make_map(&ta, apk, P.kpad, a_rows_pad, a_slabs * P.S, BM)) return cudaErrorInvalidValue;
   if (!make_map(&tb, bpk, P.kpad, b_rows_pad, b_slabs * P.S, BN)) return cudaErrorInvalidValue;
   static bool attr = false;
-  const size_t sm = smem_bytes();
+  static int nsm = 0;
+  const size_t sm = psmem_bytes();
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
     attr = true;
   }
-  const int grid = count * P.tiles_m * P.tiles_n;
-  tc_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, P, d_probs);
+  const int total = count * P.tiles_m * P.tiles_n;
+  const int grid = std::min(total, nsm);
+  tc_gemm_persistent_kernel<<<grid, PTHREADS, sm, s>>>(ta, tb, P, d_probs, total);
   return cudaGetLastError();
 }
 
