@@ -84,6 +84,12 @@ def block_list(k, start, count):
     return [((start + t) % (k * k) // k, (start + t) % (k * k) % k) for t in range(count)]
 
 
+def rank_blocks(k, rank, world, step, bps):
+    """The blocks a replica computes in one step: the step's world*bps
+    consecutive blocks of the row-major sequence, split into contiguous shares."""
+    return block_list(k, (step * world + rank) * bps, bps)
+
+
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -322,12 +328,11 @@ def main():
     ctx = mb.Context(M, k, precision=args.precision, profile=True, slices=args.slices, refine=args.refine)
     outs = [torch.empty((b, b), dtype=dt, device="cuda") for _ in range(bps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    # each rank takes its own slice of the block sequence (replicas, no collective)
-    base = rank * bps
+    # each rank takes its own share of the block sequence (replicas, no collective)
 
     def step(s, c=ctx, dst=outs):
         reps = []
-        ij = block_list(k, base + s * bps * world, bps)
+        ij = rank_blocks(k, rank, world, s, bps)
         if args.together:
             c.blocks(ij, outs=dst, width=args.together)
             return [c.last_report]
@@ -370,7 +375,7 @@ def main():
     # accuracy of the last step's blocks against a dense LAPACK inverse on the host
     inv_ref = np.linalg.inv(m_host)
     errs = []
-    for q, (i, j) in enumerate(block_list(k, base + (args.warmup + args.steps - 1) * bps * world, bps)):
+    for q, (i, j) in enumerate(rank_blocks(k, rank, world, args.warmup + args.steps - 1, bps)):
         r = inv_ref[i * b:(i + 1) * b, j * b:(j + 1) * b]
         errs.append(float(np.linalg.norm(outs[q].double().cpu().numpy() - r) / np.linalg.norm(r)))
     del inv_ref

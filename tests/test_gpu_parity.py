@@ -257,3 +257,21 @@ def test_mixed_requests_together(mb):
     for (i, j), t in zip(ij, together):
         one = to_np(mb.Context(M, 4, precision="mixed").block(i, j))
         assert np.array_equal(t, one), (i, j)
+
+
+def test_k16_blocks_and_cap(mb):
+    """k = 16 (3502 distinct frames per block), b = 32, against the oracle; then
+    under a cap well below the unconstrained workspace."""
+    n, k = 512, 16
+    m = bi.uniform_shift(n, 12)
+    ctx = mb.Context(dev(m), k)
+    for i, j in [(0, 0), (15, 3), (7, 9)]:
+        got = to_np(ctx.block(i, j))
+        assert ctx.last_report["frames"] == 3502
+        tol, floor = parity_tol(m, k, i, j, TOL_FP64)
+        assert oracle.rel_fro(got, oracle_block(m, k, i, j)) <= tol, (i, j)
+    need = ctx.last_report["peak_device_bytes"]
+    small = mb.Context(dev(m), k, cap=int(need * 0.6))
+    got = to_np(small.block(15, 3))
+    assert small.last_report["peak_device_bytes"] <= int(need * 0.6)
+    assert oracle.rel_fro(got, to_np(ctx.block(15, 3))) < 1e-12
