@@ -44,6 +44,7 @@ struct PackDesc {
 
 int tile_rows();  // 128: the M and N tile
 int tile_k();     // 64: inner-dimension tile and padding unit
+size_t smem_bytes();
 void pair_table(int S, int* npairs, int* pa, int* pb);
 
 cudaError_t launch_pack(const PackDesc* d_descs, int count, int S, int rows_pad, int kpad, __nv_bfloat16* dst,
