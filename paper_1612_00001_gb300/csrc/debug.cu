@@ -1,11 +1,12 @@
-// Test hook of the tensor-core product (not part of the public header): runs
-// the grouped tcgen05 GEMM on plain row-major FP32 inputs so that the tests
-// can check it against a plain product without going through the recursion.
+// Test hooks of the tensor-core products (not part of the public header): run
+// the grouped tcgen05 GEMMs on plain row-major inputs so that the tests can
+// check them against a plain product without going through the recursion.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
 
+#include "ozaki.h"
 #include "tc_gemm.h"
 
 using namespace mbinv;
@@ -82,6 +83,75 @@ extern "C" int mbinv_debug_tc_gemm(const float* A, const float* B, float* C, int
   cudaFree(apk);
   cudaFree(bpk);
   cudaFree(opk);
+  cudaFree(dd);
+  cudaFree(dp);
+  cudaFree(derr);
+  return rc;
+}
+
+// C[g] = beta * Cin[g] + alpha * A[g] B[g] for count row-major FP64 problems
+// (A m x k, B k x n, Cin and C m x n; Cin may be null) through the digit-split
+// FP64 product, in K chunks of at most 512 as the executor runs it.
+extern "C" int mbinv_debug_oz_gemm(const double* A, const double* B, const double* Cin, double* C, int m, int n,
+                                   int k, int count, double alpha, double beta, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int TM = oz::tile_m(), TN = oz::tile_n(), KT = oz::tile_k(), ND = oz::kDigits;
+  const int mpad = (m + TM - 1) / TM * TM, npad = (n + TN - 1) / TN * TN, kpad = (k + KT - 1) / KT * KT;
+  __nv_bfloat16 *apk = nullptr, *bpk = nullptr;
+  int *ea = nullptr, *eb = nullptr, *derr = nullptr;
+  oz::PackDesc* dd = nullptr;
+  oz::Problem* dp = nullptr;
+  int rc = 0;
+  if (cudaMalloc(&apk, (size_t)count * ND * mpad * kpad * 2) || cudaMalloc(&bpk, (size_t)count * ND * npad * kpad * 2) ||
+      cudaMalloc(&ea, sizeof(int) * count * mpad) || cudaMalloc(&eb, sizeof(int) * count * npad) ||
+      cudaMalloc(&dd, sizeof(oz::PackDesc) * 2 * count) || cudaMalloc(&dp, sizeof(oz::Problem) * 2 * count) ||
+      cudaMalloc(&derr, sizeof(int)))
+    rc = 1;
+  if (!rc) {
+    std::vector<oz::PackDesc> pd(2 * count);
+    std::vector<oz::Problem> pr(2 * count);
+    for (int g = 0; g < count; ++g) {
+      pd[g] = oz::PackDesc{A + (size_t)g * m * k, k, m, k, 0, g};
+      pd[count + g] = oz::PackDesc{B + (size_t)g * k * n, n, k, n, 1, g};  // slab row = column of B
+      double* out = C + (size_t)g * m * n;
+      pr[g] = oz::Problem{g, g, Cin ? Cin + (size_t)g * m * n : nullptr, n, out, n};
+      pr[count + g] = oz::Problem{g, g, out, n, out, n};  // later K chunks accumulate into C
+    }
+    cudaMemcpyAsync(dd, pd.data(), sizeof(oz::PackDesc) * 2 * count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dp, pr.data(), sizeof(oz::Problem) * 2 * count, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(derr, 0, sizeof(int), s);
+    if (oz::launch_pack(dd, count, mpad, kpad, apk, ea, s) != cudaSuccess) rc = 2;
+    if (!rc && oz::launch_pack(dd + count, count, npad, kpad, bpk, eb, s) != cudaSuccess) rc = 3;
+    oz::Params P{};
+    P.m = m;
+    P.n = n;
+    P.kpad = kpad;
+    P.tiles_m = mpad / TM;
+    P.tiles_n = npad / TN;
+    P.alpha = alpha;
+    P.ea = ea;
+    P.eb = eb;
+    P.ea_rows = mpad;
+    P.eb_rows = npad;
+    P.err = derr;
+    const int nkb = kpad / KT;
+    for (int kb0 = 0; !rc && kb0 < nkb; kb0 += oz::kMaxKBlocks) {
+      P.kb0 = kb0;
+      P.nkb = nkb - kb0 < oz::kMaxKBlocks ? nkb - kb0 : oz::kMaxKBlocks;
+      P.beta = kb0 == 0 ? beta : 1.0;
+      if (oz::launch_gemm(apk, count, mpad, bpk, count, npad, P, dp + (kb0 == 0 ? 0 : count), count, s) !=
+          cudaSuccess)
+        rc = 4;
+    }
+    int herr = 0;
+    if (!rc && cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = 5;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = 6;
+    if (!rc && herr) rc = 7;
+  }
+  cudaFree(apk);
+  cudaFree(bpk);
+  cudaFree(ea);
+  cudaFree(eb);
   cudaFree(dd);
   cudaFree(dp);
   cudaFree(derr);

@@ -1,0 +1,448 @@
+// FP64-accurate grouped GEMM on the BF16 tensor cores (tcgen05, sm_103a), by
+// exact digit splitting - the error-free splitting idea of Ozaki, Ogita,
+// Oishi and Rump, here with integer digits.
+//
+// Packing.  Every entry x of row r of an operand is written, relative to the
+// power of two 2^E_r just above the row's largest magnitude, as a 56-bit
+// fixed-point integer and its balanced base-128 digits:
+//     X = round(x * 2^(55 - E_r)) = sum_{p=0..7} d_p * 128^(7 - p),  |d_p| <= 64,
+// all exact in BF16.  The rounding error is at most 2^(E_r - 56).
+//
+// Product.  For C = A * B^T (B packed by rows of B^T, i.e. transposed)
+//     sum_k X_ik Y_jk = sum_{p,q} 128^(14 - p - q) * G_{p+q},
+//     G_g = sum_k sum_{p+q=g} d_p(i,k) e_q(j,k).
+// Each digit product is an integer of at most 2^12, so G_g (at most 8 pairs,
+// K <= 512 terms) stays within 2^24 and the FP32 accumulators of
+// tcgen05.mma hold it exactly.  The 36 pairs with g <= 7 are kept; the
+// dropped ones weigh at most 2^-53 K max|a_i.| max|b_j.| - the size of an
+// FP64 product's own rounding error.  Then
+//     C_ij = 2^(E_i + F_j - 61) * S,  S = sum_{g=0..7} G_g 128^(7 - g),
+// where S (below 2^75) is formed in integer arithmetic and rounded once to
+// FP64; the Schur update out = beta * Cin + alpha * C takes one more FP64
+// rounding.  GB300's FP64 pipe is narrow, so the epilogue does everything but
+// that last add with integer instructions.
+//
+// Kernel.  One CTA per 128 x 64 output tile, 256 threads, one CTA per SM (the
+// eight 64-column group accumulators take all 512 TMEM columns):
+//   warp 0, one lane:  TMA producer.  Per K block of 64 it loads all eight
+//                      digits of the B tile in one 3-D copy (64 KB, double
+//                      buffered) and each digit of the A tile (16 KB) into a
+//                      four-deep ring.
+//   warp 1, one lane:  MMA issuer.  For A digit p one tcgen05.mma (two when
+//                      more than four B digits remain) multiplies it by the
+//                      B digits q = 0..7-p stacked along N, writing TMEM
+//                      columns 64 (p + q) - so every pair lands in its group
+//                      G_{p+q} without any data movement.
+//   all warps:         epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..,
+//                      columns half w / 4, combines the groups, and writes
+//                      beta * Cin + alpha * C through a shared-memory stage
+//                      so that rows are read and written contiguously.
+// Every mbarrier wait is bounded (about two seconds of %globaltimer); a wait
+// that runs out raises the error word and the CTA drains, frees its TMEM and
+// returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "ozaki.h"
+#include "tcgen05_ptx.cuh"
+
+namespace mbinv {
+namespace oz {
+
+namespace {
+
+using namespace mbinv::ptx;
+
+constexpr int ND = kDigits;
+constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int ASTAGES = 4;
+constexpr int THREADS = 256;
+constexpr int PR = 32;                                  // slab rows per pack CTA
+constexpr uint32_t A_BYTES = BM * BK * 2;               // one digit of the A tile: 16 KB
+constexpr uint32_t BQ_BYTES = BN * BK * 2;              // one digit of the B tile: 8 KB
+constexpr uint32_t B_BYTES = ND * BQ_BYTES;             // all digits of the B tile: 64 KB
+constexpr uint32_t TMEM_COLS = 512;
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+
+// Balanced base-128 digits of round(x * 2^(55 - E)), with 2^E > |x|; zero
+// and subnormal x give zero digits.  Integer instructions only.
+__device__ __forceinline__ void digits8(double x, int E, int (&d)[ND]) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  int64_t X = 0;
+  if (ex != 0 && E < kNonFinite) {
+    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // x = m 2^(ex - 1075)
+    const int sh = ex - 1020 - E;                                   // X = m 2^sh, sh <= 2
+    uint64_t u = 0;
+    if (sh >= 0) {
+      u = m << sh;
+    } else if (sh >= -54) {
+      const int r = -sh;
+      u = (m + (1ull << (r - 1))) >> r;  // nearest, ties away from zero
+    }
+    X = (bits >> 63) ? -(int64_t)u : (int64_t)u;
+  }
+#pragma unroll
+  for (int p = ND - 1; p >= 1; --p) {
+    int r = (int)(X & 127);
+    if (r >= 64) r -= 128;
+    d[p] = r;
+    X = (X - r) / 128;  // exact
+  }
+  d[0] = (int)X;
+}
+
+// alpha * 2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64
+// (ties to even); the exponent field is assembled directly unless the
+// result is subnormal or overflows.
+__device__ __forceinline__ double combine(const int (&a)[ND], int e, double alpha) {
+  const long long hi = ((a[0] * 128LL + a[1]) * 128LL + a[2]) * 128LL + a[3];
+  const long long lo = ((a[4] * 128LL + a[5]) * 128LL + a[6]) * 128LL + a[7];
+  const __int128 S = (__int128)hi * (__int128)(1LL << 28) + (__int128)lo;
+  if (S == 0) return 0.0;
+  bool neg = S < 0;
+  const unsigned __int128 U = neg ? (unsigned __int128)(-S) : (unsigned __int128)S;
+  const uint64_t uh = (uint64_t)(U >> 64), ul = (uint64_t)U;
+  int top = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);  // leading bit, <= 74
+  uint64_t mant;
+  if (top <= 52) {
+    mant = ul << (52 - top);
+  } else {
+    const int sh = top - 52;  // 1 .. 22
+    mant = (uint64_t)(U >> sh);
+    const uint64_t rem = ul & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1))) ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++top;
+    }
+  }
+  if (alpha == -1.0) neg = !neg;
+  const int e2 = top + e;  // value = mant 2^(e2 - 52)
+  double v;
+  if (e2 >= -1022 && e2 <= 1023) {
+    v = __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)(e2 + 1023) << 52) |
+                                         (mant & 0xFFFFFFFFFFFFFull)));
+  } else {
+    v = scalbn((double)mant, e2 - 52);
+    if (neg) v = -v;
+  }
+  if (alpha != 1.0 && alpha != -1.0) v = alpha * v;
+  return v;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params P,
+                   const Problem* __restrict__ probs) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sB = base;                 // 2 x 64 KB
+  uint8_t* sA = base + 2 * B_BYTES;   // ASTAGES x 16 KB
+  uint64_t* fullB = (uint64_t*)(sA + ASTAGES * A_BYTES);
+  uint64_t* emptyB = fullB + 2;
+  uint64_t* fullA = emptyB + 2;
+  uint64_t* emptyA = fullA + ASTAGES;
+  uint64_t* done = emptyA + ASTAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* failed = (int*)(tmem_slot + 1);
+  int* fexp = failed + 1;  // exponents of this tile's 64 output columns
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_per = P.tiles_m * P.tiles_n;
+  const int g = blockIdx.x / tiles_per;
+  const int rem = blockIdx.x - g * tiles_per;
+  const int tm = rem / P.tiles_n, tn = rem - (rem / P.tiles_n) * P.tiles_n;
+  const Problem pr = probs[g];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&fullB[s], 1);
+      mbar_init(&emptyB[s], 1);
+    }
+    for (int s = 0; s < ASTAGES; ++s) {
+      mbar_init(&fullA[s], 1);
+      mbar_init(&emptyA[s], 1);
+    }
+    mbar_init(done, 1);
+    *failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (threadIdx.x < BN) fexp[threadIdx.x] = P.eb[(int64_t)pr.b_slab * P.eb_rows + tn * BN + threadIdx.x];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    auto load_b = [&](int u) -> bool {
+      const int s = u & 1;
+      if (u >= 2 && !mbar_wait(&emptyB[s], ((uint32_t)(u >> 1) & 1u) ^ 1u)) return false;
+      mbar_expect_tx(&fullB[s], B_BYTES);
+      tma_load_3d(sB + s * B_BYTES, &tmB, &fullB[s], (P.kb0 + u) * BK, tn * BN, pr.b_slab * ND);
+      return true;
+    };
+    bool ok = load_b(0);
+    for (int u = 0; ok && u < P.nkb; ++u) {
+      for (int p = 0; p < ND; ++p) {
+        const int n = u * ND + p, s = n % ASTAGES;
+        if (n >= ASTAGES && !mbar_wait(&emptyA[s], ((uint32_t)(n / ASTAGES) & 1u) ^ 1u)) {
+          ok = false;
+          break;
+        }
+        if (*(volatile int*)failed) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&fullA[s], A_BYTES);
+        tma_load_3d(sA + s * A_BYTES, &tmA, &fullA[s], (P.kb0 + u) * BK, tm * BM, pr.a_slab * ND + p);
+        // the next B tile goes out early: its buffer was freed with K block u - 1
+        if (p == 1 && u + 1 < P.nkb && !load_b(u + 1)) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    if (!ok) atomicExch(failed, 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int u = 0; ok && u < P.nkb; ++u) {
+      const int sb = u & 1;
+      if (!mbar_wait(&fullB[sb], (uint32_t)(u >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      const uint32_t b0 = smem_u32(sB + sb * B_BYTES);
+      for (int p = 0; p < ND; ++p) {
+        const int n = u * ND + p, s = n % ASTAGES;
+        if (!mbar_wait(&fullA[s], (uint32_t)(n / ASTAGES) & 1u)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + s * A_BYTES);
+        const int nq0 = ND - p < 4 ? ND - p : 4, nq1 = ND - p - nq0;
+        const uint32_t id0 = idesc(64 * nq0), id1 = idesc(64 * (nq1 > 0 ? nq1 : 1));
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          // the first MMAs (digit 0 of the first K block) start all eight groups
+          const uint32_t acc = (u > 0 || p > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ad = sdesc(a0 + kk * 32);
+          umma(tmem + 64 * p, ad, sdesc(b0 + kk * 32), id0, acc);
+          if (nq1 > 0) umma(tmem + 64 * (p + 4), ad, sdesc(b0 + 4 * BQ_BYTES + kk * 32), id1, acc);
+        }
+        umma_commit(&emptyA[s]);
+      }
+      umma_commit(&emptyB[sb]);
+    }
+    if (!ok) atomicExch(failed, 1);
+    umma_commit(done);  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue
+  const bool ok = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok || *(volatile int*)failed) {
+    if (lane == 0 && P.err) atomicExch(P.err, 1);
+  } else {
+    const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, column half
+    const int row = tm * BM + q * 32 + lane;
+    const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + row];
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    double* T = (double*)sA + warp * (32 * 17);  // the A ring is idle once every MMA has completed
+    for (int c0 = h * 32; c0 < h * 32 + 32; c0 += 16) {
+      uint32_t acc[ND][16];
+#pragma unroll
+      for (int gg = 0; gg < ND; ++gg) tmem_ld16_async(trow + 64 * gg + c0, acc[gg]);
+      tmem_wait();
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int fj = fexp[c0 + t];
+        double v;
+        if (ei >= kNonFinite || fj >= kNonFinite) {
+          v = __longlong_as_double(0x7FF8000000000000LL);
+        } else {
+          int a[ND];
+#pragma unroll
+          for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][t]));
+          v = combine(a, ei + fj - 61, P.alpha);
+        }
+        T[lane * 17 + t] = v;
+      }
+      __syncwarp();
+      const int rr = lane >> 4, cc = lane & 15;  // two rows of 16 columns per pass
+      const int col = tn * BN + c0 + cc;
+#pragma unroll 4
+      for (int r2 = 0; r2 < 32; r2 += 2) {
+        const int lr = r2 + rr;
+        const int grow = tm * BM + q * 32 + lr;
+        if (grow < P.m && col < P.n) {
+          double y = T[lr * 17 + cc];
+          if (pr.cin) {
+            const double ci = pr.cin[(int64_t)grow * pr.ldcin + col];
+            y = (P.beta == 1.0) ? ci + y : fma(P.beta, ci, y);
+          }
+          pr.out[(int64_t)grow * pr.ldo + col] = y;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// One CTA per 32 slab rows: pass 1 finds each row's largest magnitude (the
+// bit patterns of |x| order like the values; Inf and NaN sort above every
+// finite value), pass 2 writes the digits.  The source is staged through a
+// 32 x 64 shared tile so that both orientations read it contiguously.
+__global__ void __launch_bounds__(256) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
+                                                       __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
+  __shared__ double S[PR][65];
+  __shared__ int sE[PR];
+  const PackDesc d = descs[blockIdx.y];
+  const int r0 = blockIdx.x * PR;
+  const int R = d.transpose ? d.cols : d.rows, KD = d.transpose ? d.rows : d.cols;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto load_tile = [&](int k0) {
+    if (!d.transpose) {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int rr = (tid >> 6) + 4 * it, kk = tid & 63;
+        const int r = r0 + rr, k = k0 + kk;
+        S[rr][kk] = (r < R && k < KD) ? d.src[(int64_t)r * d.ld + k] : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int rr = tid & 31, kk = (tid >> 5) + 8 * it;
+        const int r = r0 + rr, k = k0 + kk;
+        S[rr][kk] = (r < R && k < KD) ? d.src[(int64_t)k * d.ld + r] : 0.0;
+      }
+    }
+  };
+  unsigned long long mx[4] = {0, 0, 0, 0};
+  if (r0 < R) {
+    for (int k0 = 0; k0 < KD; k0 += 64) {
+      __syncthreads();
+      load_tile(k0);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int rr = warp + 8 * j;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const unsigned long long bits =
+              (unsigned long long)__double_as_longlong(S[rr][2 * lane + hh]) & 0x7FFFFFFFFFFFFFFFull;
+          mx[j] = bits > mx[j] ? bits : mx[j];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx[j], o);
+      mx[j] = y > mx[j] ? y : mx[j];
+    }
+    if (lane == 0) {
+      const int rr = warp + 8 * j;
+      const int ex = (int)(mx[j] >> 52);
+      // 2^E > max|x|: E = ex - 1022 for a normal maximum
+      const int E = mx[j] == 0 ? 0 : (ex == 0x7ff ? kNonFinite : (ex == 0 ? -1022 : ex - 1022));
+      sE[rr] = E;
+      exps[(int64_t)d.slab * rows_pad + r0 + rr] = E;
+    }
+  }
+  for (int k0 = 0; k0 < kpad; k0 += 64) {
+    __syncthreads();
+    load_tile(k0);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int rr = warp + 8 * j;
+      const int E = sE[rr];
+      int d0[ND], d1[ND];
+      digits8(S[rr][2 * lane], E, d0);
+      digits8(S[rr][2 * lane + 1], E, d1);
+#pragma unroll
+      for (int p = 0; p < ND; ++p) {
+        __nv_bfloat162 v;
+        v.x = __float2bfloat16_rn((float)d0[p]);
+        v.y = __float2bfloat16_rn((float)d1[p]);
+        *(__nv_bfloat162*)&dst[(((int64_t)d.slab * ND + p) * rows_pad + r0 + rr) * kpad + k0 + 2 * lane] = v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int tile_m() { return BM; }
+int tile_n() { return BN; }
+int tile_k() { return BK; }
+int pack_rows() { return PR; }
+size_t smem_bytes() { return 2 * B_BYTES + ASTAGES * A_BYTES + 1024 + 512; }
+
+cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kpad, __nv_bfloat16* dst, int* exps,
+                        cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (rows_pad % PR || kpad % BK || ((uintptr_t)dst & 3)) return cudaErrorInvalidValue;
+  dim3 grid(rows_pad / PR, count);
+  oz_pack_kernel<<<grid, 256, 0, s>>>(d_descs, rows_pad, kpad, dst, exps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, const __nv_bfloat16* bpk, int b_slabs,
+                        int b_rows_pad, const Params& P, const Problem* d_probs, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (P.kpad % BK || a_rows_pad % BM || b_rows_pad % BN || P.tiles_m * BM > a_rows_pad ||
+      P.tiles_n * BN > b_rows_pad || P.nkb < 1 || P.nkb > kMaxKBlocks || P.kb0 < 0 ||
+      (P.kb0 + P.nkb) * BK > P.kpad || P.ea_rows != a_rows_pad || P.eb_rows != b_rows_pad)
+    return cudaErrorInvalidValue;
+  if (((uintptr_t)apk | (uintptr_t)bpk) & 15) return cudaErrorInvalidValue;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, apk, P.kpad, a_rows_pad, a_slabs * ND, BM, BK, 1)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, bpk, P.kpad, b_rows_pad, b_slabs * ND, BN, BK, ND)) return cudaErrorInvalidValue;
+  static bool attr = false;
+  const size_t sm = smem_bytes();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = count * P.tiles_m * P.tiles_n;
+  oz_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, P, d_probs);
+  return cudaGetLastError();
+}
+
+}  // namespace oz
+}  // namespace mbinv
