@@ -29,6 +29,12 @@ if ROOT not in sys.path:
 METRIC = "inverse blocks/sec & GEMM % of tensor peak, mixed vs FP64 at ≤1e-10 rel err"
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
+DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
+
+
+def dtype_name(args):
+    return {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32",
+            "fp64_tc": "f64 (Schur products: exact bf16 digit products, f32 accumulate)"}[args.precision]
 
 
 def parse():
@@ -37,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed", "fp64_tc"])
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--k", type=int, default=8)
     p.add_argument("--blocks-per-step", type=int, default=8)
@@ -192,7 +198,7 @@ def run_batched(args, rank, world, dist):
     import bri_inputs as bi
     import paper_1612_00001_gb300 as mb
     probs = bi.ragged_batch(args.batched, 0)
-    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    dt = torch.float64 if args.precision in ("fp64", "fp64_tc") else torch.float32
     mats = [torch.tensor(bi.uniform_shift(p["n"], p["seed"]), dtype=dt, device="cuda") for p in probs]
     work = [(M, p["k"], p["i"], p["j"]) for M, p in zip(mats, probs)]
     flops = 0.0
@@ -225,7 +231,7 @@ def run_batched(args, rank, world, dist):
     line = {"metric": METRIC, "value": args.batched * args.steps / secs, "unit": "blocks/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[args.precision],
+            "dtype": dtype_name(args),
             "data": "synthetic",
             "config": {"workload": f"{args.batched} matrices, n ~ U[256,4096] step 64, k ~ U{{2..8}}, "
                                    f"uniform[-1,1)+nI, one block each, runs executed together ({args.precision})",
@@ -248,7 +254,7 @@ def run_backward(args, rank, world, dist):
     n, k = args.n, args.k
     b = -(-n // k)
     m = bi.spd(n, args.kappa, 0) if args.matrix == "spd" else make_matrix(args, n)
-    dt = torch.float64 if args.precision == "fp64" else torch.float32
+    dt = torch.float64 if args.precision in ("fp64", "fp64_tc") else torch.float32
     M = torch.tensor(m, dtype=dt, device="cuda")
     W = torch.tensor(bi.gaussian_matrix(b, b, 0), dtype=dt, device="cuda")
     i, j = 1, k - 2
@@ -283,7 +289,7 @@ def run_backward(args, rank, world, dist):
     line = {"metric": METRIC, "value": args.steps / secs, "unit": "forward+backward/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[args.precision],
+            "dtype": dtype_name(args),
             "data": "synthetic",
             "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, L = sum(W * N_{i}{j}), "
                                    f"forward + adjoint ({args.precision})",
@@ -322,7 +328,7 @@ def main():
     b = -(-n // k)
     bps = args.blocks_per_step
     m_host = make_matrix(args, n)
-    dt = torch.float64 if (args.precision == "fp64" or args.refine) else torch.float32
+    dt = torch.float64 if (args.precision in ("fp64", "fp64_tc") or args.refine) else torch.float32
     M = torch.tensor(m_host, dtype=dt, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = mb.Context(M, k, precision=args.precision, profile=True, slices=args.slices, refine=args.refine)
@@ -385,13 +391,20 @@ def main():
     npairs = {1: 1, 2: 3, 3: 6}[args.slices] if args.precision == "mixed" else 1
     alu = {"fp64": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
            "fp32": (FP32_NOMINAL_GFLOPS / 1e3, "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
-           "mixed": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)")}[args.precision]
+           "mixed": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
+           "fp64_tc": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)")}[args.precision]
     fams = {}
     if args.precision == "mixed":
         fams["tc_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * npairs,
                                   "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
                                   "peak": pk["bf16_tflops_sustained"],
                                   "peak_source": f"bf16_tflops_sustained ({pk_src}), executed BF16 slice products"}
+    elif args.precision == "fp64_tc":
+        fams["oz_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * DIGIT_PAIRS,
+                                  "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
+                                  "peak": pk["bf16_tflops_sustained"],
+                                  "peak_source": f"bf16_tflops_sustained ({pk_src}), executed BF16 digit-pair "
+                                                 f"products ({DIGIT_PAIRS} per FP64 product)"}
     else:
         fams["gemm_grouped_kernel"] = {"bound": "alu", "work": agg["gemm_flops"], "dsec": agg["gemm_device_seconds"],
                                        "launches": agg["gemm_launches"], "peak": alu[0], "peak_source": alu[1]}
@@ -403,6 +416,8 @@ def main():
         ach = f["work"] / f["dsec"] / 1e12 if f["dsec"] > 0 else 0.0
         kernels[name] = {"bound": f["bound"], "achieved": ach, "peak": f["peak"], "unit": "TFLOP/s",
                          "frac": ach / f["peak"], "device_seconds": f["dsec"], "peak_source": f["peak_source"]}
+        if name == "oz_gemm_kernel":
+            kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
     dom = max(kernels, key=lambda k: kernels[k]["device_seconds"])
     roofline = dict(kernels[dom])
     roofline.update({"kernel": dom, "traffic": None, "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
@@ -410,8 +425,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": f"bf16x{args.slices}/f32"}[
-                args.precision], "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(args), "data": "synthetic",
             "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, "
                                    + (f"{args.together} runs executed together" if args.together
                                       else "blocks one at a time") + f" ({args.precision})",

@@ -57,8 +57,19 @@ typedef enum { MBINV_DTYPE_F64 = 0, MBINV_DTYPE_F32 = 1 } mbinv_dtype;
  *                     operand slices and FP32 accumulation, frame values kept
  *                     in FP32, every b x b pivot inverted in FP64; with
  *                     refine_steps = 1 the block is corrected by an FP64
- *                     block-row residual (see mbinv_block). */
-typedef enum { MBINV_FP64 = 0, MBINV_FP32 = 1, MBINV_MIXED_BF16 = 2 } mbinv_precision;
+ *                     block-row residual (see mbinv_block).
+ *   MBINV_FP64_TC     frame values and b x b inverses in FP64 as MBINV_FP64;
+ *                     the Schur products run on the BF16 tensor cores as
+ *                     exact digit products: every row of the left operand
+ *                     and every column of the right one is scaled by a power
+ *                     of two, rounded to a 56-bit integer and split into 8
+ *                     balanced base-128 digits; the 36 digit pairs whose
+ *                     weights reach 2^-56 are summed exactly in FP32 and
+ *                     recombined in integer arithmetic.  Each product then
+ *                     carries an error below K 2^-53 max|row| max|column|
+ *                     (the paper computes in plain FP64; this is a way to
+ *                     run its FP64 products on the tensor pipe). */
+typedef enum { MBINV_FP64 = 0, MBINV_FP32 = 1, MBINV_MIXED_BF16 = 2, MBINV_FP64_TC = 3 } mbinv_precision;
 
 typedef struct {
     size_t struct_size;         /* sizeof(mbinv_options) */

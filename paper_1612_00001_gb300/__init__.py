@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmbinv.so")
 
 OK, EINVAL, ENOMEM_CAP, ESINGULAR, ENOTCONV, ETIMEOUT, ECUDA, ENOTSUP = range(8)
-PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_bf16": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_bf16": 2, "fp64_tc": 3}
 DTYPE_F64, DTYPE_F32 = 0, 1
 
 _lock = threading.Lock()

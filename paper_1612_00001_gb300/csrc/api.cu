@@ -165,6 +165,11 @@ size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int G, int inv_chunk) {
     for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
     bytes += pack_bytes((int)c->b, c->opt.bf16_slices, ops * G);
   }
+  if (prec == MBINV_FP64_TC) {
+    size_t ops = 0;
+    for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
+    bytes += digit_bytes((int)c->b, ops * G);
+  }
   size_t ops = 0;
   for (const Step& st : S.steps) ops += st.inv.size() + st.gemm.size();
   bytes += (size_t)G * ops * 2 * sizeof(GemmDesc) + S.steps.size() * 1024 + (64u << 10);  // descriptors
@@ -294,7 +299,7 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
   if (s == MBINV_ECUDA) last_cuda_error() = c->env.last_error;
   size_t held = c->slots.bytes + c->own_M.bytes + c->outtmp.bytes;
   for (DevBuf* d : {&c->env.inv_work, &c->env.inv_wrow, &c->env.inv_perm, &c->env.inv_amax, &c->env.desc,
-                    &c->env.apk, &c->env.bpk, &c->env.b2pk})
+                    &c->env.apk, &c->env.bpk, &c->env.b2pk, &c->env.oexp})
     held += d->bytes;
   c->peak = std::max(c->peak, held);
   if (rep) {
@@ -643,7 +648,7 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
     if (opt->struct_size != sizeof(mbinv_options)) return MBINV_EINVAL;
     o = *opt;
   }
-  if (o.precision < MBINV_FP64 || o.precision > MBINV_MIXED_BF16) return MBINV_EINVAL;
+  if (o.precision < MBINV_FP64 || o.precision > MBINV_FP64_TC) return MBINV_EINVAL;
   if (o.precision == MBINV_MIXED_BF16 && (o.bf16_slices < 1 || o.bf16_slices > 3)) return MBINV_EINVAL;
   if (o.refine_steps < 0 || o.refine_steps > 1) return MBINV_EINVAL;
   std::unique_ptr<mbinv_ctx> c(new (std::nothrow) mbinv_ctx);
@@ -658,7 +663,8 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   c->stream = (cudaStream_t)o.cuda_stream;
   // the plain paths read M in their own precision; the mixed path reads the
   // caller's M as given (its residual is taken against it)
-  c->mdt = (o.precision == MBINV_FP64) ? F64 : (o.precision == MBINV_FP32 ? F32 : dtype);
+  c->mdt = (o.precision == MBINV_FP64 || o.precision == MBINV_FP64_TC) ? F64
+                                                                          : (o.precision == MBINV_FP32 ? F32 : dtype);
   const size_t es = dtype_size(dtype), mes = dtype_size(c->mdt);
   const bool dev = is_device_ptr(M);
   if (c->l == 0 && dev && c->mdt == dtype) {

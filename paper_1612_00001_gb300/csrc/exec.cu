@@ -15,12 +15,14 @@
 #include <tuple>
 
 #include "exec.h"
+#include "ozaki.h"
 #include "tc_gemm.h"
 
 namespace mbinv {
 
 void Env::release() {
-  for (DevBuf* d : {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr})
+  for (DevBuf* d :
+       {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr, &oexp})
     d->release();
   hdesc.release();
   for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -35,6 +37,7 @@ size_t slot_bytes_for(int b, int precision) {
 namespace {
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+size_t up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 struct Strides {
   size_t work, wrow, perm;
@@ -89,7 +92,7 @@ cudaError_t ensure_events(Env& E, size_t n) {
 
 // One launch (or launch sequence) of a run, in order.
 struct Launch {
-  enum Kind : int { INV = 0, GEMM = 1, PACK = 2, TC = 3 } kind;
+  enum Kind : int { INV = 0, GEMM = 1, PACK = 2, TC = 3, OZPACK = 4, OZ = 5 } kind;
   size_t off;  // descriptors in the arena
   int count;
   int in_dt = 0, out_dt = 0, bmax = 0;  // INV
@@ -99,6 +102,10 @@ struct Launch {
   __nv_bfloat16* bsrc = nullptr;        // TC B operand
   int nA = 0, mode = 0, b = 0, nB = 0;  // TC
   __nv_bfloat16* zout = nullptr;        // TC mode 1 output (Z^T slices)
+  int* exps = nullptr;                  // OZPACK destination / OZ exponents of A
+  int* exps_b = nullptr;                // OZ exponents of B
+  int b_rows_pad = 0, kb0 = 0, nkb = 0; // OZ
+  double alpha = 1, beta = 0;           // OZ
 };
 
 #define CUE(x)                      \
@@ -123,12 +130,18 @@ size_t pack_bytes(int bmax, int slices, size_t ops) {
   return 3 * ops * slices * rpad * kpad * 2;
 }
 
+size_t digit_bytes(int bmax, size_t ops) {
+  const size_t rpa = up(bmax, oz::tile_m()), rpb = up(bmax, oz::tile_n()), kpad = up(bmax, oz::tile_k());
+  return ops * (oz::kDigits * (rpa + rpb) * kpad * 2 + (rpa + rpb) * 4) + 3 * 256;
+}
+
 mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   E.launches = E.gemm_launches = 0;
   E.gemm_dev_s = E.inv_dev_s = E.pack_dev_s = 0;
   E.job_singular.assign(jobs.size(), 0);
   if (jobs.empty()) return MBINV_OK;
   const bool mixed = E.precision == MBINV_MIXED_BF16;
+  const bool ozk = E.precision == MBINV_FP64_TC;
   const int wt = env_work_type(E.precision);
   size_t nsteps = 0;
   int bmax = 0;
@@ -141,7 +154,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   const int NS = E.slices;
 
   // ---- pass 1: sizes of the descriptor arena and of the packed slabs
-  size_t need = 512, maxA = 1, maxB = 1, maxZ = 1;  // maxA/B/Z in bytes
+  size_t need = 512, maxA = 1, maxB = 1, maxZ = 1, maxE = 1;  // maxA/B/Z/E in bytes
   for (size_t t = 0; t < nsteps; ++t) {
     size_t ninv = 0, ngemm = 0;
     std::map<int, std::pair<size_t, size_t>> per_b;  // b -> (distinct A, products)
@@ -170,6 +183,17 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
       }
       maxZ = std::max(maxZ, zsum);
     }
+    if (ozk) {
+      for (auto& kv : per_b) {
+        const size_t b = kv.first, nops = kv.second.second;
+        const size_t rpa = up(b, oz::tile_m()), rpb = up(b, oz::tile_n()), kpad = up(b, oz::tile_k());
+        const size_t chunks = up(kpad / oz::tile_k(), oz::kMaxKBlocks) / oz::kMaxKBlocks;
+        need += nops * (2 * sizeof(oz::PackDesc) + chunks * sizeof(oz::Problem)) + 256 * (3 + chunks);
+        maxA = std::max(maxA, nops * oz::kDigits * rpa * kpad * 2);
+        maxB = std::max(maxB, nops * oz::kDigits * rpb * kpad * 2);
+        maxE = std::max(maxE, nops * (rpa + rpb) * 4);
+      }
+    }
   }
   CUE(E.desc.ensure(need));
   CUE(E.hdesc.ensure(need));
@@ -183,6 +207,12 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
     CUE(E.apk.ensure(maxA));
     CUE(E.bpk.ensure(maxB));
     CUE(E.b2pk.ensure(maxZ));
+    CUE(E.tcerr.ensure(256));
+  }
+  if (ozk) {
+    CUE(E.apk.ensure(maxA));
+    CUE(E.bpk.ensure(maxB));
+    CUE(E.oexp.ensure(maxE));
     CUE(E.tcerr.ensure(256));
   }
   char* hbase = (char*)E.hdesc.p;
@@ -254,6 +284,95 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
       if (t < jobs[q].S->steps.size())
         for (const GemmOp& g : jobs[q].S->steps[t].gemm) ops.emplace_back((int)q, &g);
     if (ops.empty()) continue;
+    if (ozk) {
+      // FP64 products on the tensor cores: per distinct order b, the digits
+      // of the distinct left operands and of the right operands (transposed),
+      // then one grouped launch per K chunk of at most 512
+      const double alpha = ops[0].second->alpha, beta = ops[0].second->beta;
+      std::map<int, std::vector<size_t>> by_b;
+      for (size_t u = 0; u < ops.size(); ++u) {
+        if (ops[u].second->alpha != alpha || ops[u].second->beta != beta) return MBINV_ENOTSUP;
+        by_b[jobs[ops[u].first].b].push_back(u);
+      }
+      for (auto& kv : by_b) {
+        const int b = kv.first;
+        const int rpa = (int)up(b, oz::tile_m()), rpb = (int)up(b, oz::tile_n()), kpad = (int)up(b, oz::tile_k());
+        const std::vector<size_t>& us = kv.second;
+        auto key = [&](size_t u, const Ref& r) {
+          return std::make_tuple(ops[u].first, (int)r.kind, r.kind == Ref::SLOT ? r.slot : r.r, r.c);
+        };
+        std::map<std::tuple<int, int, int, int>, int> aslab, bslab;
+        std::vector<size_t> afirst, bfirst;
+        for (size_t u : us) {
+          if (aslab.emplace(key(u, ops[u].second->A), (int)afirst.size()).second) afirst.push_back(u);
+          if (bslab.emplace(key(u, ops[u].second->B), (int)bfirst.size()).second) bfirst.push_back(u);
+        }
+        int* ea = (int*)E.oexp.p;
+        int* eb = ea + afirst.size() * rpa;
+        for (int side = 0; side < 2; ++side) {
+          const std::vector<size_t>& first = side == 0 ? afirst : bfirst;
+          const size_t o = take(first.size() * sizeof(oz::PackDesc));
+          oz::PackDesc* pd = (oz::PackDesc*)(hbase + o);
+          for (size_t a = 0; a < first.size(); ++a) {
+            int64_t ld;
+            int dt;
+            const GemmOp& g = *ops[first[a]].second;
+            const void* p = resolve(jobs[ops[first[a]].first], side == 0 ? g.A : g.B, &ld, &dt);
+            if (dt != F64) return MBINV_ENOTSUP;
+            pd[a] = oz::PackDesc{(const double*)p, ld, b, b, side, (int)a};
+          }
+          Launch l{Launch::OZPACK, o, (int)first.size()};
+          l.rows_pad = side == 0 ? rpa : rpb;
+          l.kpad = kpad;
+          l.dst = (__nv_bfloat16*)(side == 0 ? E.apk.p : E.bpk.p);
+          l.exps = side == 0 ? ea : eb;
+          L.push_back(l);
+        }
+        const int nkb = kpad / oz::tile_k();
+        for (int kb0 = 0; kb0 < nkb; kb0 += oz::kMaxKBlocks) {
+          const size_t o = take(us.size() * sizeof(oz::Problem));
+          oz::Problem* pr = (oz::Problem*)(hbase + o);
+          for (size_t v = 0; v < us.size(); ++v) {
+            const Job& J = jobs[ops[us[v]].first];
+            const GemmOp& g = *ops[us[v]].second;
+            oz::Problem q{};
+            q.a_slab = aslab[key(us[v], g.A)];
+            q.b_slab = bslab[key(us[v], g.B)];
+            int64_t ld;
+            int dt;
+            q.out = (double*)resolve(J, g.C, &ld, &dt);
+            q.ldo = ld;
+            if (dt != F64) return MBINV_ENOTSUP;
+            if (kb0 > 0) {  // later K chunks add to what the first wrote
+              q.cin = q.out;
+              q.ldcin = q.ldo;
+            } else if (g.Cin.kind != Ref::NONE) {
+              q.cin = (const double*)resolve(J, g.Cin, &ld, &dt);
+              q.ldcin = ld;
+              if (dt != F64) return MBINV_ENOTSUP;
+            }
+            pr[v] = q;
+          }
+          Launch l{Launch::OZ, o, (int)us.size()};
+          l.b = b;
+          l.rows_pad = rpa;
+          l.b_rows_pad = rpb;
+          l.kpad = kpad;
+          l.kb0 = kb0;
+          l.nkb = std::min(oz::kMaxKBlocks, nkb - kb0);
+          l.alpha = alpha;
+          l.beta = kb0 > 0 ? 1.0 : beta;
+          l.dst = (__nv_bfloat16*)E.apk.p;
+          l.nA = (int)afirst.size();
+          l.bsrc = (__nv_bfloat16*)E.bpk.p;
+          l.nB = (int)bfirst.size();
+          l.exps = ea;
+          l.exps_b = eb;
+          L.push_back(l);
+        }
+      }
+      continue;
+    }
     if (!mixed) {
       const size_t o = take(ops.size() * sizeof(GemmDesc));
       GemmDesc* hd = (GemmDesc*)(hbase + o);
@@ -404,7 +523,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   hst[0] = DevStatus{0, INT_MAX};
   CUE(cudaMemcpyAsync(E.status.p, &hst[0], sizeof(DevStatus), cudaMemcpyHostToDevice, E.stream));
   CUE(cudaMemsetAsync(E.flags.p, 0, jobs.size() * sizeof(int), E.stream));
-  if (mixed) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
+  if (mixed || ozk) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
   if (E.profile) CUE(ensure_events(E, 2 * L.size()));
   tc::TcParams P{};
   if (mixed) {
@@ -444,6 +563,32 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
         ++E.launches;
         ++E.gemm_launches;
         break;
+      case Launch::OZPACK:
+        CUE(oz::launch_pack((const oz::PackDesc*)(dbase + l.off), l.count, l.rows_pad, l.kpad, l.dst, l.exps,
+                            E.stream));
+        ++E.launches;
+        break;
+      case Launch::OZ: {
+        oz::Params Q{};
+        Q.m = Q.n = l.b;
+        Q.kpad = l.kpad;
+        Q.kb0 = l.kb0;
+        Q.nkb = l.nkb;
+        Q.tiles_m = l.rows_pad / oz::tile_m();
+        Q.tiles_n = l.b_rows_pad / oz::tile_n();
+        Q.alpha = l.alpha;
+        Q.beta = l.beta;
+        Q.ea = l.exps;
+        Q.eb = l.exps_b;
+        Q.ea_rows = l.rows_pad;
+        Q.eb_rows = l.b_rows_pad;
+        Q.err = (int*)E.tcerr.p;
+        CUE(oz::launch_gemm(l.dst, l.nA, l.rows_pad, l.bsrc, l.nB, l.b_rows_pad, Q,
+                            (const oz::Problem*)(dbase + l.off), l.count, E.stream));
+        ++E.launches;
+        ++E.gemm_launches;
+        break;
+      }
     }
     if (E.profile) CUE(cudaEventRecord(E.events[2 * q + 1], E.stream));
   }
@@ -452,14 +597,14 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   CUE(cudaStreamSynchronize(E.stream));
   std::vector<int> fl(jobs.size(), 0);
   CUE(cudaMemcpy(fl.data(), E.flags.p, jobs.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  if (mixed) CUE(cudaMemcpy(&herr, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (mixed || ozk) CUE(cudaMemcpy(&herr, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
   for (size_t q = 0; q < jobs.size(); ++q) E.job_singular[q] = fl[q];
   if (E.profile) {
     for (size_t q = 0; q < L.size(); ++q) {
       float ms = 0;
       CUE(cudaEventElapsedTime(&ms, E.events[2 * q], E.events[2 * q + 1]));
       if (L[q].kind == Launch::INV) E.inv_dev_s += ms * 1e-3;
-      else if (L[q].kind == Launch::PACK) E.pack_dev_s += ms * 1e-3;
+      else if (L[q].kind == Launch::PACK || L[q].kind == Launch::OZPACK) E.pack_dev_s += ms * 1e-3;
       else E.gemm_dev_s += ms * 1e-3;
     }
   }

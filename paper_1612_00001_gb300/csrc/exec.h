@@ -71,7 +71,7 @@ struct Env {
   int slices = 3;
   bool profile = false;
   int inv_chunk = 1;  // matrices per inverse launch
-  DevBuf inv_work, inv_wrow, inv_perm, inv_amax, desc, status, flags, apk, bpk, b2pk, tcerr;
+  DevBuf inv_work, inv_wrow, inv_perm, inv_amax, desc, status, flags, apk, bpk, b2pk, tcerr, oexp;
   HostBuf hdesc;
   std::vector<cudaEvent_t> events;
   // results of the last run
@@ -84,13 +84,18 @@ struct Env {
 };
 
 inline int env_work_type(int precision) { return precision == MBINV_FP32 ? F32 : F64; }
-inline int env_slot_type(int precision) { return precision == MBINV_FP64 ? F64 : F32; }
+inline int env_slot_type(int precision) {
+  return (precision == MBINV_FP64 || precision == MBINV_FP64_TC) ? F64 : F32;
+}
 size_t slot_bytes_for(int b, int precision);
 // Device bytes of inverse scratch for count matrices of order at most bmax.
 size_t inv_scratch_bytes(int bmax, int precision, int count);
 // Device bytes of the packed operand slabs of the mixed path for a run whose
 // widest GEMM step has `ops` products of order bmax.
 size_t pack_bytes(int bmax, int slices, size_t ops);
+// Device bytes of the digit slabs and row exponents of the FP64_TC path for a
+// run whose widest GEMM step has `ops` products of order bmax.
+size_t digit_bytes(int bmax, size_t ops);
 
 // Runs the schedules of `jobs` together: step t of every schedule goes out in
 // the same grouped launches.  Returns MBINV_ESINGULAR if any request met a

@@ -1,0 +1,162 @@
+"""The FP64_TC path (FP64 frame values and inverses, Schur products as exact
+BF16 digit products on the tensor cores) against the CPU oracle, through the
+C ABI.  Same bar as the FP64 path: max(1e-11, 10 x the oracle's own
+sensitivity floor), element by element on the same seeded inputs."""
+import itertools
+
+import numpy as np
+import pytest
+
+import bri_inputs as bi
+import oracle
+from helpers import oracle_block, parity_tol, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-11
+P = "fp64_tc"
+
+
+@pytest.fixture(scope="module")
+def mb():
+    import paper_1612_00001_gb300 as mb
+    mb.build()
+    return mb
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(a, dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("i,j", [(0, 0), (1, 3), (3, 0), (2, 2)])
+def test_small_config_blocks(mb, i, j):
+    """n=256, k=4 (b=64), uniform[-1,1] + n I."""
+    m = bi.uniform_shift(256, 0)
+    ctx = mb.Context(dev(m), 4, precision=P)
+    got = to_np(ctx.block(i, j))
+    tol, floor = parity_tol(m, 4, i, j, TOL_FP64)
+    err = oracle.rel_fro(got, oracle_block(m, 4, i, j))
+    assert err <= tol, (err, tol, floor)
+    assert ctx.last_report["frames"] == 14
+
+
+@pytest.mark.parametrize("n,k", [(300, 3), (600, 3), (400, 2), (520, 5), (1200, 2), (1024, 8)])
+def test_ragged_tiles_and_k_chunks(mb, n, k):
+    """b = 100, 200, 200, 104 (ragged tiles), 600 (two K chunks of the exact
+    accumulation), 128 with k = 8 (270 frames)."""
+    m = bi.uniform_shift(n, 3, shift=n / 8)
+    ctx = mb.Context(dev(m), k, precision=P)
+    for i, j in [(0, 0), (k - 1, 0), (1, k - 1)]:
+        got = to_np(ctx.block(i, j))
+        tol, floor = parity_tol(m, k, i, j, TOL_FP64)
+        err = oracle.rel_fro(got, oracle_block(m, k, i, j))
+        assert err <= tol, (i, j, err, tol)
+
+
+def test_haar_matrix_kappa_1e4(mb):
+    """Haar-random orthogonal factors, log-spaced singular values, kappa = 1e4."""
+    n, k = 512, 4
+    m = bi.haar_svd(n, 1e4, 2)
+    ctx = mb.Context(dev(m), k, precision=P)
+    for i, j in [(0, 0), (2, 1), (3, 3)]:
+        got = to_np(ctx.block(i, j))
+        tol, floor = parity_tol(m, k, i, j, TOL_FP64)
+        err = oracle.rel_fro(got, oracle_block(m, k, i, j))
+        assert err <= tol, (i, j, err, tol)
+
+
+def test_close_to_plain_fp64_path(mb):
+    m = bi.uniform_shift(2048, 5)
+    a = to_np(mb.Context(dev(m), 8).block(3, 6))
+    c = to_np(mb.Context(dev(m), 8, precision=P).block(3, 6))
+    floor = oracle.sensitivity_floor(m, 8, 3, 6)
+    assert oracle.rel_fro(c, a) <= max(TOL_FP64, 10 * floor)
+
+
+def test_padding_border(mb):
+    n, k, seed = 250, 4, 17
+    m = bi.uniform_shift(n, 8)
+    ctx = mb.Context(dev(m), k, pad_seed=seed, precision=P)
+    inv = np.linalg.inv(m)
+    b = -(-n // k)
+    cpl = bi.pad_columns(n, k * b - n, seed)
+    for i, j in itertools.product(range(k), range(k)):
+        got = to_np(ctx.block(i, j))
+        g, _, _ = oracle.augment(m, k, i, j, coupling=cpl)
+        ref = oracle_block(g, k, i, j, pad_last=True)
+        r1, c1 = min(b, n - i * b), min(b, n - j * b)
+        tol, _ = parity_tol(g, k, i, j, TOL_FP64, pad_last=True)
+        assert oracle.rel_fro(got, ref[:r1, :c1]) <= tol, (i, j)
+        assert oracle.rel_fro(got, inv[i * b:i * b + r1, j * b:j * b + c1]) < 1e-11
+
+
+def test_requests_together_bitwise_equal_one_at_a_time(mb):
+    m = bi.uniform_shift(512, 6)
+    ctx = mb.Context(dev(m), 8, precision=P)
+    ij = [(0, 0), (3, 5), (7, 1), (2, 2), (6, 7)]
+    together = [to_np(x) for x in ctx.blocks(ij)]
+    for (i, j), t in zip(ij, together):
+        one = to_np(mb.Context(dev(m), 8, precision=P).block(i, j))
+        assert np.array_equal(t, one), (i, j)
+
+
+def test_power_of_two_scaling_bitwise(mb):
+    """Row and column exponents absorb a power-of-two scale exactly."""
+    m = bi.uniform_shift(384, 4)
+    a = to_np(mb.Context(dev(m), 4, precision=P).block(1, 2))
+    c = to_np(mb.Context(dev(m * 8.0), 4, precision=P).block(1, 2))
+    assert np.array_equal(c * 8.0, a)
+
+
+def test_singular_and_nan(mb):
+    m = bi.block_diagonal(4, 16, 3)
+    ctx = mb.Context(dev(m), 4, precision=P)
+    with pytest.raises(mb.MbinvError) as e:
+        ctx.block(0, 1)
+    assert e.value.status == mb.ESINGULAR
+    got = to_np(ctx.block(2, 2))
+    assert oracle.rel_fro(got, np.linalg.inv(m[32:48, 32:48])) < 1e-14
+    m = bi.uniform_shift(64, 2)
+    m[5, 7] = np.nan
+    with pytest.raises(mb.MbinvError) as e:
+        mb.Context(dev(m), 4, precision=P).block(0, 0)
+    assert e.value.status == mb.ESINGULAR
+
+
+def test_batched_problems(mb):
+    probs = bi.ragged_batch(6, 3, nmin=64, nmax=700, kmin=2, kmax=5)
+    tensors, refs = [], []
+    for p in probs:
+        m = bi.uniform_shift(p["n"], p["seed"])
+        tensors.append((dev(m), p["k"], p["i"], p["j"]))
+        g, b, l = oracle.augment(m, p["k"], p["i"], p["j"], coupling=bi.pad_columns(p["n"], (-p["n"]) % p["k"], 0))
+        refs.append(oracle_block(g, p["k"], p["i"], p["j"], pad_last=l > 0))
+    outs, statuses, rep, st = mb.batched_blocks(tensors, precision=P)
+    assert st == mb.OK and all(s == mb.OK for s in statuses)
+    for o, r in zip(outs, refs):
+        o = to_np(o)
+        assert oracle.rel_fro(o, r[:o.shape[0], :o.shape[1]]) < 1e-10
+
+
+def test_backward_matches_fp64_reference(mb):
+    n, k, b, i, j = 256, 4, 64, 2, 1
+    m = bi.spd(n, 1e2, 3)
+    g = bi.gaussian_matrix(b, b, 5)
+    ref = oracle.adjoint(np.linalg.inv(m), g, i, j, b)
+    M = dev(m).requires_grad_(True)
+    out = mb.block(M, k, i, j, precision=P)
+    (out * dev(g)).sum().backward()
+    assert oracle.rel_fro(to_np(M.grad), ref) < 1e-11
+
+
+def test_cap_respected(mb):
+    m = bi.uniform_shift(2048, 1)
+    full = mb.Context(dev(m), 8, precision=P)
+    a = to_np(full.block(3, 4))
+    need = full.last_report["peak_device_bytes"]
+    cap = int(need * 0.85)
+    small = mb.Context(dev(m), 8, cap=cap, precision=P)
+    c = to_np(small.block(3, 4))
+    assert small.last_report["peak_device_bytes"] <= cap
+    assert np.array_equal(c, a)
