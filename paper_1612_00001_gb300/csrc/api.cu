@@ -298,7 +298,7 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
   s = run_jobs(c->env, jobs);
   if (s == MBINV_ECUDA) last_cuda_error() = c->env.last_error;
   size_t held = c->slots.bytes + c->own_M.bytes + c->outtmp.bytes;
-  for (DevBuf* d : {&c->env.inv_work, &c->env.inv_wrow, &c->env.inv_perm, &c->env.inv_amax, &c->env.desc,
+  for (DevBuf* d : {&c->env.inv_work, &c->env.inv_wrow, &c->env.inv_perm, &c->env.inv_amax, &c->env.inv_tc, &c->env.desc,
                     &c->env.apk, &c->env.bpk, &c->env.b2pk, &c->env.oexp})
     held += d->bytes;
   c->peak = std::max(c->peak, held);

@@ -114,8 +114,8 @@ extern "C" int mbinv_debug_oz_gemm(const double* A, const double* B, const doubl
       pd[g] = oz::PackDesc{A + (size_t)g * m * k, k, m, k, 0, g};
       pd[count + g] = oz::PackDesc{B + (size_t)g * k * n, n, k, n, 1, g};  // slab row = column of B
       double* out = C + (size_t)g * m * n;
-      pr[g] = oz::Problem{g, g, Cin ? Cin + (size_t)g * m * n : nullptr, n, out, n};
-      pr[count + g] = oz::Problem{g, g, out, n, out, n};  // later K chunks accumulate into C
+      pr[g] = oz::Problem{g, g, Cin ? Cin + (size_t)g * m * n : nullptr, n, out, n, m, n, 0, 0, 0, 0};
+      pr[count + g] = oz::Problem{g, g, out, n, out, n, m, n, 0, 0, 0, 0};  // later K chunks accumulate into C
     }
     cudaMemcpyAsync(dd, pd.data(), sizeof(oz::PackDesc) * 2 * count, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dp, pr.data(), sizeof(oz::Problem) * 2 * count, cudaMemcpyHostToDevice, s);
@@ -123,8 +123,6 @@ extern "C" int mbinv_debug_oz_gemm(const double* A, const double* B, const doubl
     if (oz::launch_pack(dd, count, mpad, kpad, apk, ea, s) != cudaSuccess) rc = 2;
     if (!rc && oz::launch_pack(dd + count, count, npad, kpad, bpk, eb, s) != cudaSuccess) rc = 3;
     oz::Params P{};
-    P.m = m;
-    P.n = n;
     P.kpad = kpad;
     P.tiles_m = mpad / TM;
     P.tiles_n = npad / TN;

@@ -22,7 +22,7 @@ namespace mbinv {
 
 void Env::release() {
   for (DevBuf* d :
-       {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr, &oexp})
+       {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &inv_tc, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr, &oexp})
     d->release();
   hdesc.release();
   for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -46,7 +46,7 @@ struct Strides {
 Strides inv_strides(int bmax, int precision) {
   const int wt = env_work_type(precision);
   const size_t ws = dtype_size(wt);
-  const size_t nb = (size_t)inv_panel_width(bmax, wt);
+  const size_t nb = (size_t)inv_panel_width(bmax, wt, precision == MBINV_FP64_TC);
   return Strides{al((size_t)bmax * bmax * ws), al(nb * bmax * ws), al((size_t)bmax * 4)};
 }
 
@@ -121,7 +121,9 @@ struct Launch {
 
 size_t inv_scratch_bytes(int bmax, int precision, int count) {
   const Strides st = inv_strides(bmax, precision);
-  return (size_t)count * (st.work + st.wrow + st.perm + 256);
+  size_t bytes = (size_t)count * (st.work + st.wrow + st.perm + 256);
+  if (precision == MBINV_FP64_TC) bytes += inv_tc_bytes(bmax, count);
+  return bytes;
 }
 
 size_t pack_bytes(int bmax, int slices, size_t ops) {
@@ -203,6 +205,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   CUE(E.inv_wrow.ensure((size_t)E.inv_chunk * st.wrow));
   CUE(E.inv_perm.ensure((size_t)E.inv_chunk * st.perm));
   CUE(E.inv_amax.ensure((size_t)E.inv_chunk * 256));
+  if (ozk) CUE(E.inv_tc.ensure(inv_tc_bytes(bmax, E.inv_chunk)));
   if (mixed) {
     CUE(E.apk.ensure(maxA));
     CUE(E.bpk.ensure(maxB));
@@ -336,6 +339,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
             const Job& J = jobs[ops[us[v]].first];
             const GemmOp& g = *ops[us[v]].second;
             oz::Problem q{};
+            q.m = q.n = b;
             q.a_slab = aslab[key(us[v], g.A)];
             q.b_slab = bslab[key(us[v], g.B)];
             int64_t ld;
@@ -525,6 +529,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   CUE(cudaMemsetAsync(E.flags.p, 0, jobs.size() * sizeof(int), E.stream));
   if (mixed || ozk) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
   if (E.profile) CUE(ensure_events(E, 2 * L.size()));
+  const InvTc itc{E.inv_tc.p, (int*)E.tcerr.p};
   tc::TcParams P{};
   if (mixed) {
     P.S = NS;
@@ -537,7 +542,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
     switch (l.kind) {
       case Launch::INV:
         CUE(run_inverse_batch(l.in_dt, l.out_dt, wt, (const InvDesc*)(dbase + l.off), l.count, l.bmax,
-                              (DevStatus*)E.status.p, E.stream, &E.launches));
+                              (DevStatus*)E.status.p, E.stream, &E.launches, ozk ? &itc : nullptr));
         break;
       case Launch::GEMM:
         CUE(launch_gemm_grouped(l.combo, (const GemmDesc*)(dbase + l.off), l.count, l.tiles, E.stream));
@@ -570,7 +575,6 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
         break;
       case Launch::OZ: {
         oz::Params Q{};
-        Q.m = Q.n = l.b;
         Q.kpad = l.kpad;
         Q.kb0 = l.kb0;
         Q.nkb = l.nkb;

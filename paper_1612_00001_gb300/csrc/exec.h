@@ -71,7 +71,7 @@ struct Env {
   int slices = 3;
   bool profile = false;
   int inv_chunk = 1;  // matrices per inverse launch
-  DevBuf inv_work, inv_wrow, inv_perm, inv_amax, desc, status, flags, apk, bpk, b2pk, tcerr, oexp;
+  DevBuf inv_work, inv_wrow, inv_perm, inv_amax, inv_tc, desc, status, flags, apk, bpk, b2pk, tcerr, oexp;
   HostBuf hdesc;
   std::vector<cudaEvent_t> events;
   // results of the last run

@@ -15,7 +15,10 @@
 //      product of the nb elementary transforms; the pivot rows of the other
 //      columns are copied to a scratch W = X[J, rest].
 //   2. update kernel (many CTAs per matrix): X[:, rest] = T[:, J] W + X[:, rest]
-//      with the rows of J zeroed first - a rank-nb GEMM on the CUDA cores.
+//      with the rows of J zeroed first - a rank-nb GEMM on the CUDA cores,
+//      or (FP64_TC) an exact digit product on the tensor cores (ozaki.cu):
+//      T[:, J] by rows and W by columns are digit-packed and one grouped
+//      product per panel forms the update in FP64.
 // After the last panel the recorded row interchanges are undone as column
 // interchanges in reverse order while the result is written out.  For b at
 // most 128 the panel is the whole matrix and step 2 never runs.
@@ -27,6 +30,7 @@
 #include <cfloat>
 
 #include "mbinv_internal.h"
+#include "ozaki.h"
 #include "tile_gemm.cuh"
 
 #include <cooperative_groups.h>
@@ -279,6 +283,65 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const InvDesc* __restric
   }
 }
 
+// Descriptors of the tensor-core trailing update of panel [p, p + nb): the
+// panel columns T = X[:, J] as the left operand (by rows), the pivot rows
+// W = X[J, :] as the right one (by columns), out = X with the rows of J taking
+// no addend and the columns of J left alone.  A matrix past its last panel,
+// or whose panel is the whole matrix, gets an empty problem.
+__global__ void gj_tc_setup_kernel(const InvDesc* __restrict__ descs, int count, int p, int nb,
+                                   oz::PackDesc* __restrict__ pa, oz::PackDesc* __restrict__ pb,
+                                   oz::Problem* __restrict__ pr) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= count) return;
+  const InvDesc d = descs[u];
+  const int b = d.b;
+  const int w = min(nb, b - p);
+  const bool live = w > 0 && w < b;
+  double* X = (double*)d.work;
+  pa[u] = oz::PackDesc{X + (live ? p : 0), b, live ? b : 0, live ? w : 0, 0, u};
+  pb[u] = oz::PackDesc{(const double*)d.wrow, b, live ? w : 0, live ? b : 0, 1, u};
+  oz::Problem q{};
+  q.a_slab = q.b_slab = u;
+  q.cin = X;
+  q.ldcin = b;
+  q.out = X;
+  q.ldo = b;
+  q.m = q.n = live ? b : 0;
+  q.nocin_r0 = q.skip_c0 = p;
+  q.nocin_r1 = q.skip_c1 = p + (live ? w : 0);
+  pr[u] = q;
+}
+
+struct TcLayout {
+  int rpa, rpb;
+  size_t da, db, ea, eb, pa, pb, pr, total;
+};
+
+TcLayout tc_layout(int bmax, int count) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  TcLayout L;
+  L.rpa = (bmax + oz::tile_m() - 1) / oz::tile_m() * oz::tile_m();
+  L.rpb = (bmax + oz::tile_n() - 1) / oz::tile_n() * oz::tile_n();
+  const size_t K = oz::tile_k();
+  size_t o = 0;
+  L.da = o;
+  o += al((size_t)count * oz::kDigits * L.rpa * K * 2);
+  L.db = o;
+  o += al((size_t)count * oz::kDigits * L.rpb * K * 2);
+  L.ea = o;
+  o += al((size_t)count * L.rpa * 4);
+  L.eb = o;
+  o += al((size_t)count * L.rpb * 4);
+  L.pa = o;
+  o += al((size_t)count * sizeof(oz::PackDesc));
+  L.pb = o;
+  o += al((size_t)count * sizeof(oz::PackDesc));
+  L.pr = o;
+  o += al((size_t)count * sizeof(oz::Problem));
+  L.total = o;
+  return L;
+}
+
 // out[r][c] = X[r][col_of[c]], where col_of undoes the row interchanges as
 // column interchanges taken in reverse order.
 template <typename TW, typename TO>
@@ -310,7 +373,7 @@ __global__ void gj_finalize_kernel(const InvDesc* __restrict__ descs, int rows_p
 
 template <typename TW>
 cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int count, int b, DevStatus* d_status,
-                        cudaStream_t s, int* launches) {
+                        cudaStream_t s, int* launches, const InvTc* tc) {
   int nl = 0;
   zero_amax_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count);
   ++nl;
@@ -321,7 +384,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     gj_init_kernel<TW><<<g, 256, 0, s>>>(d_desc, in_dtype);
     ++nl;
   }
-  const int nb = inv_panel_width(b, sizeof(TW) == 8 ? F64 : F32);
+  const int nb = inv_panel_width(b, sizeof(TW) == 8 ? F64 : F32, tc != nullptr);
   // cluster size: spread the panel over more SMs when few matrices are batched
   int CL = 8;
   while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
@@ -351,7 +414,38 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status);
     if (e != cudaSuccess) return e;
     ++nl;
-    if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
+    if (w < b && tc) {  // the trailing update on the tensor cores
+      const TcLayout T = tc_layout(b, count);
+      char* base = (char*)tc->scratch;
+      auto* pa = (oz::PackDesc*)(base + T.pa);
+      auto* pb = (oz::PackDesc*)(base + T.pb);
+      auto* pr = (oz::Problem*)(base + T.pr);
+      auto* da = (__nv_bfloat16*)(base + T.da);
+      auto* db = (__nv_bfloat16*)(base + T.db);
+      int* ea = (int*)(base + T.ea);
+      int* eb = (int*)(base + T.eb);
+      gj_tc_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
+      e = oz::launch_pack(pa, count, T.rpa, oz::tile_k(), da, ea, s);
+      if (e != cudaSuccess) return e;
+      e = oz::launch_pack(pb, count, T.rpb, oz::tile_k(), db, eb, s);
+      if (e != cudaSuccess) return e;
+      oz::Params Q{};
+      Q.kpad = oz::tile_k();
+      Q.kb0 = 0;
+      Q.nkb = 1;
+      Q.tiles_m = T.rpa / oz::tile_m();
+      Q.tiles_n = T.rpb / oz::tile_n();
+      Q.alpha = 1.0;
+      Q.beta = 1.0;
+      Q.ea = ea;
+      Q.eb = eb;
+      Q.ea_rows = T.rpa;
+      Q.eb_rows = T.rpb;
+      Q.err = tc->err;
+      e = oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
+      if (e != cudaSuccess) return e;
+      nl += 4;
+    } else if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
       using Cfg = TileCfg<TW>;
       dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);
       gj_update_kernel<TW><<<g, 256, 0, s>>>(d_desc, p, w);
@@ -374,17 +468,23 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
 
 }  // namespace
 
-int inv_panel_width(int b, int wtype) {
+int inv_panel_width(int b, int wtype, bool tc) {
   const size_t es = wtype == F64 ? 8 : 4;
   if (b <= kMaxPanelWidth && (size_t)b * (b + 1) * es <= 132 * 1024) return b;  // whole matrix in one panel
+  // the tensor-core update takes K in blocks of 64; wider panels must still
+  // fit a cluster of 8 CTAs
+  if (tc && wtype == F64 && ((size_t)(b + 7) / 8 + 4) * 65 * es <= (size_t)kSmemLimit) return 64;
   return 32;
 }
 
+size_t inv_tc_bytes(int bmax, int count) { return tc_layout(bmax, count).total; }
+
 cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
-                              DevStatus* d_status, cudaStream_t s, int* launches) {
+                              DevStatus* d_status, cudaStream_t s, int* launches, const InvTc* tc) {
   if (count <= 0) return cudaSuccess;
-  if (wtype == F64) return run_batch_t<double>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches);
-  return run_batch_t<float>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches);
+  if (wtype == F64) return run_batch_t<double>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, tc);
+  if (tc) return cudaErrorInvalidValue;
+  return run_batch_t<float>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, nullptr);
 }
 
 }  // namespace mbinv

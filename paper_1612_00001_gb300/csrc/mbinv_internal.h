@@ -117,13 +117,23 @@ struct DevStatus {
   int singular;
   int tag;
 };
-// Panel width of the blocked elimination for order b in working type wtype.
-int inv_panel_width(int b, int wtype);
+// Panel width of the blocked elimination for order b in working type wtype
+// (tc: the trailing update runs on the tensor cores, which favour 64).
+int inv_panel_width(int b, int wtype, bool tc = false);
+// Device scratch of the tensor-core trailing update for count FP64 matrices
+// of order at most bmax: digit slabs of the panel columns and of the pivot
+// rows, their exponents, and the per-matrix descriptors.
+struct InvTc {
+  void* scratch;  // inv_tc_bytes(bmax, count) bytes, 256-byte aligned
+  int* err;       // raised when a wait of the product kernel ran out
+};
+size_t inv_tc_bytes(int bmax, int count);
 // Inverts count matrices described by d_desc; b is the largest order among
 // them (each descriptor carries its own).  in_dtype / out_dtype / wtype are
 // DType values; wtype is F64 or F32.  The max|entry| words are zeroed by the
-// call.
+// call.  With tc (FP64 only) the trailing updates are exact digit products
+// on the tensor cores instead of FP64 tile products.
 cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
-                              DevStatus* d_status, cudaStream_t s, int* launches);
+                              DevStatus* d_status, cudaStream_t s, int* launches, const InvTc* tc = nullptr);
 
 }  // namespace mbinv

@@ -167,6 +167,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int rem = blockIdx.x - g * tiles_per;
   const int tm = rem / P.tiles_n, tn = rem - (rem / P.tiles_n) * P.tiles_n;
   const Problem pr = probs[g];
+  // tiles past this problem's extent, or wholly inside its skipped columns
+  if (tm * BM >= pr.m || tn * BN >= pr.n || (tn * BN >= pr.skip_c0 && tn * BN + BN <= pr.skip_c1)) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
@@ -300,9 +302,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int r2 = 0; r2 < 32; r2 += 2) {
         const int lr = r2 + rr;
         const int grow = tm * BM + q * 32 + lr;
-        if (grow < P.m && col < P.n) {
+        if (grow < pr.m && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) {
           double y = T[lr * 17 + cc];
-          if (pr.cin) {
+          if (pr.cin && (grow < pr.nocin_r0 || grow >= pr.nocin_r1)) {
             const double ci = pr.cin[(int64_t)grow * pr.ldcin + col];
             y = (P.beta == 1.0) ? ci + y : fma(P.beta, ci, y);
           }

@@ -24,22 +24,26 @@ struct PackDesc {
 };
 
 // One product of a grouped launch:
-//     out = beta * Cin + alpha * A_slab * B_slab^T     (FP64, row-major)
+//     out = beta * Cin + alpha * A_slab * B_slab^T     (FP64, row-major, m x n)
 // over the K blocks [kb0, kb0 + nkb) of the slabs.  Cin may be null; it may
-// also be out itself (each element is read once, then written).
+// also be out itself (each element is read once, then written).  Rows in
+// [nocin_r0, nocin_r1) take no Cin; columns in [skip_c0, skip_c1) are not
+// written (the trailing update of a blocked Gauss-Jordan step).
 struct Problem {
   int a_slab, b_slab;
   const double* cin;
   int64_t ldcin;
   double* out;
   int64_t ldo;
+  int m, n;
+  int nocin_r0, nocin_r1;
+  int skip_c0, skip_c1;
 };
 
 struct Params {
-  int m, n;        // output size
   int kpad;        // padded inner length of the slabs (multiple of tile_k())
   int kb0, nkb;    // K blocks of this launch, nkb <= kMaxKBlocks
-  int tiles_m, tiles_n;
+  int tiles_m, tiles_n;  // tiles of the largest problem
   double alpha, beta;
   const int* ea;   // row exponents of the A slabs: ea[slab * ea_rows + r]
   const int* eb;   // row exponents of the B slabs: eb[slab * eb_rows + r]

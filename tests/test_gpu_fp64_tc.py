@@ -160,3 +160,28 @@ def test_cap_respected(mb):
     c = to_np(small.block(3, 4))
     assert small.last_report["peak_device_bytes"] <= cap
     assert np.array_equal(c, a)
+
+
+@pytest.mark.parametrize("n", [333, 700, 1100])
+def test_single_inverse_k1(mb, n):
+    """k = 1: one pivoted Gauss-Jordan inverse; for n > 128 its trailing
+    updates (panels of 64, the last one ragged) are digit products.  The bar
+    is the FP64 CUDA-core path's own distance to the oracle (same pivots,
+    another rounding order), times 4, or 1e-13."""
+    m = bi.uniform_shift(n, 5, shift=10.0)
+    got = to_np(mb.Context(dev(m), 1, precision=P).block(0, 0))
+    plain = to_np(mb.Context(dev(m), 1).block(0, 0))
+    ref, st = oracle.gj_inverse(m)
+    assert st == oracle.OK
+    e_tc, e_plain = oracle.rel_fro(got, ref), oracle.rel_fro(plain, ref)
+    assert e_tc <= max(4 * e_plain, 1e-13), (e_tc, e_plain)
+
+
+def test_single_inverse_ill_conditioned(mb):
+    """kappa = 1e6: the tensor-core update stays within FP64-path accuracy."""
+    m = bi.haar_svd(600, 1e6, 4)
+    a = to_np(mb.Context(dev(m), 1).block(0, 0))
+    c = to_np(mb.Context(dev(m), 1, precision=P).block(0, 0))
+    ref = np.linalg.inv(m)
+    ea, ec = oracle.rel_fro(a, ref), oracle.rel_fro(c, ref)
+    assert ec <= max(4 * ea, 1e-12), (ea, ec)
