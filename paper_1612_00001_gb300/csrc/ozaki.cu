@@ -108,8 +108,9 @@ __device__ __forceinline__ void digits8(double x, int E, int (&d)[ND]) {
 
 // alpha * 2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64
 // (ties to even); the exponent field is assembled directly unless the
-// result is subnormal or overflows.
-__device__ __forceinline__ double combine(const int (&a)[ND], int e, double alpha) {
+// result is subnormal or overflows.  amode: 0 alpha = 1, 1 alpha = -1, 2 any
+// other alpha (the FP64 comparisons are made once per thread, not per entry).
+__device__ __forceinline__ double combine(const int (&a)[ND], int e, int amode, double alpha) {
   const long long hi = ((a[0] * 128LL + a[1]) * 128LL + a[2]) * 128LL + a[3];
   const long long lo = ((a[4] * 128LL + a[5]) * 128LL + a[6]) * 128LL + a[7];
   const __int128 S = (__int128)hi * (__int128)(1LL << 28) + (__int128)lo;
@@ -131,7 +132,7 @@ __device__ __forceinline__ double combine(const int (&a)[ND], int e, double alph
       ++top;
     }
   }
-  if (alpha == -1.0) neg = !neg;
+  if (amode == 1) neg = !neg;
   const int e2 = top + e;  // value = mant 2^(e2 - 52)
   double v;
   if (e2 >= -1022 && e2 <= 1023) {
@@ -141,7 +142,7 @@ __device__ __forceinline__ double combine(const int (&a)[ND], int e, double alph
     v = scalbn((double)mant, e2 - 52);
     if (neg) v = -v;
   }
-  if (alpha != 1.0 && alpha != -1.0) v = alpha * v;
+  if (amode == 2) v = alpha * v;
   return v;
 }
 
@@ -196,6 +197,28 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+
+  // Epilogue geometry: warp w reads TMEM lanes 32 (w mod 4) .. (rows) and
+  // columns half w / 4; it writes two rows of 16 columns per pass.  Its share
+  // of Cin (zero where a row takes no addend) is fetched now, so that the
+  // loads overlap the main loop instead of stalling the epilogue.
+  const int q = warp & 3, h = warp >> 2;
+  const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + tm * BM + q * 32 + lane];
+  const int rr = lane >> 4, cc = lane & 15;
+  double cpre[2][16];
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    const int col = tn * BN + h * 32 + pass * 16 + cc;
+#pragma unroll
+    for (int r2 = 0; r2 < 16; ++r2) {
+      const int grow = tm * BM + q * 32 + 2 * r2 + rr;
+      cpre[pass][r2] = (pr.cin && grow < pr.m && col < pr.n && (grow < pr.nocin_r0 || grow >= pr.nocin_r1))
+                           ? pr.cin[(int64_t)grow * pr.ldcin + col]
+                           : 0.0;
+    }
+  }
+  const int amode = P.alpha == 1.0 ? 0 : (P.alpha == -1.0 ? 1 : 2);
+  const bool beta1 = P.beta == 1.0;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -271,12 +294,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (!ok || *(volatile int*)failed) {
     if (lane == 0 && P.err) atomicExch(P.err, 1);
   } else {
-    const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, column half
-    const int row = tm * BM + q * 32 + lane;
-    const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + row];
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     double* T = (double*)sA + warp * (32 * 17);  // the A ring is idle once every MMA has completed
-    for (int c0 = h * 32; c0 < h * 32 + 32; c0 += 16) {
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+      const int c0 = h * 32 + pass * 16;
       uint32_t acc[ND][16];
 #pragma unroll
       for (int gg = 0; gg < ND; ++gg) tmem_ld16_async(trow + 64 * gg + c0, acc[gg]);
@@ -291,24 +313,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           int a[ND];
 #pragma unroll
           for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][t]));
-          v = combine(a, ei + fj - 61, P.alpha);
+          v = combine(a, ei + fj - 61, amode, P.alpha);
         }
         T[lane * 17 + t] = v;
       }
       __syncwarp();
-      const int rr = lane >> 4, cc = lane & 15;  // two rows of 16 columns per pass
       const int col = tn * BN + c0 + cc;
-#pragma unroll 4
-      for (int r2 = 0; r2 < 32; r2 += 2) {
-        const int lr = r2 + rr;
+#pragma unroll
+      for (int r2 = 0; r2 < 16; ++r2) {
+        const int lr = 2 * r2 + rr;
         const int grow = tm * BM + q * 32 + lr;
         if (grow < pr.m && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) {
-          double y = T[lr * 17 + cc];
-          if (pr.cin && (grow < pr.nocin_r0 || grow >= pr.nocin_r1)) {
-            const double ci = pr.cin[(int64_t)grow * pr.ldcin + col];
-            y = (P.beta == 1.0) ? ci + y : fma(P.beta, ci, y);
-          }
-          pr.out[(int64_t)grow * pr.ldo + col] = y;
+          const double y = T[lr * 17 + cc];
+          const double ci = cpre[pass][r2];
+          pr.out[(int64_t)grow * pr.ldo + col] = beta1 ? ci + y : fma(P.beta, ci, y);
         }
       }
       __syncwarp();
@@ -325,7 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // bit patterns of |x| order like the values; Inf and NaN sort above every
 // finite value), pass 2 writes the digits.  The source is staged through a
 // 32 x 64 shared tile so that both orientations read it contiguously.
-__global__ void __launch_bounds__(256) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
+__global__ void __launch_bounds__(256, 2) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
                                                        __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
   __shared__ double S[PR][65];
   __shared__ int sE[PR];
@@ -388,7 +406,7 @@ __global__ void __launch_bounds__(256) oz_pack_kernel(const PackDesc* __restrict
     __syncthreads();
     load_tile(k0);
     __syncthreads();
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < 4; ++j) {
       const int rr = warp + 8 * j;
       const int E = sE[rr];
