@@ -84,6 +84,27 @@ __global__ void gj_init_kernel(const InvDesc* __restrict__ descs, int in_dtype) 
   if ((threadIdx.x & 31) == 0) atomicMax(d.amax, (unsigned long long)__double_as_longlong(m));
 }
 
+// Pivot keys: the bit pattern of |x| orders like |x| for every non-NaN x, and
+// a NaN maps to -1 so that it never wins; comparing keys keeps the pivot
+// search off the FP64 pipe (which takes a whole warp instruction even for
+// one active lane).
+__device__ __forceinline__ long long pivot_key(double v) {
+  const long long a = __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL;
+  return a > 0x7FF0000000000000LL ? -1LL : a;
+}
+__device__ __forceinline__ long long pivot_key(float v) {
+  const int a = __float_as_int(v) & 0x7FFFFFFF;
+  return a > 0x7F800000 ? -1LL : (long long)a;
+}
+__device__ __forceinline__ double key_value(long long k, double) {
+  return k < 0 ? __longlong_as_double(0x7FF8000000000000LL) : __longlong_as_double(k);
+}
+__device__ __forceinline__ float key_value(long long k, float) {
+  return k < 0 ? __int_as_float(0x7FC00000) : __int_as_float((int)k);
+}
+__device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(float v) { return (__float_as_int(v) << 1) != 0; }
+
 // A cluster of CL CTAs per matrix factors the panel [p, p + nb) (see the file
 // comment).  CTA q of the cluster keeps rows [q R, (q+1) R) of the panel in
 // its shared memory (R = ceil(b / CL)); the CTAs exchange pivot candidates
@@ -115,7 +136,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   TW* jrow = prow + ldp;                // old row j, for the owner of row r (nb)
   TW* srow = jrow + ldp;                // scaled pivot row (nb)
   int* piv_hist = (int*)(srow + ldp);   // pivot row of every column of the panel (nb)
-  __shared__ TW cand_v[2][NW];
+  __shared__ long long cand_v[2][NW];
   __shared__ int cand_i[2][NW];
   TW* X = (TW*)d.work;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -132,14 +153,14 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
     const int buf = t & 1;
     // ---- this warp's pivot candidate: first row of largest magnitude, rows >= j
     {
-      TW best = (TW)-1;
+      long long best = -1;
       int bi = b;
       for (int i = max(j, r0) + tid; i < r1; i += kPanelThreads) {
-        const TW v = fabs(P[(i - r0) * ldp + t]);
+        const long long v = pivot_key(P[(i - r0) * ldp + t]);
         if (v > best) { best = v; bi = i; }  // NaN never wins
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const TW ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
@@ -148,26 +169,27 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
     cluster.sync();  // #1: the candidates of every warp of every CTA are visible
     // ---- global pivot, computed by every warp from the same CL x NW candidates
     int r;
-    TW gv;
+    long long gk;
     {
-      TW v = (TW)-1;
+      long long v = -1;
       int ix = b;
       for (int u = lane; u < CL * NW; u += 32) {
-        const TW cv = *cluster.map_shared_rank(&cand_v[buf][u % NW], u / NW);
+        const long long cv = *cluster.map_shared_rank(&cand_v[buf][u % NW], u / NW);
         const int ci = *cluster.map_shared_rank(&cand_i[buf][u % NW], u / NW);
         if (cv > v || (cv == v && ci < ix)) { v = cv; ix = ci; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const TW ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
         const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
         if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
       }
       r = ix >= b ? j : ix;  // every candidate NaN: keep the row
-      gv = v;
+      gk = v;
     }
     if (tid == 0) {
       piv_hist[t] = r;
       if (q == 0) {
+        const TW gv = key_value(gk, (TW)0);
         if (!(gv > tol) || !isfinite((double)gv)) {
           atomicExch(&status->singular, 1);
           atomicMin(&status->tag, d.tag);
@@ -202,9 +224,10 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
       }
       const TW* src = (i == r && r != j) ? jrow : xi;
       const TW f = src[t];
+      const bool nz = nonzero(f);
       for (int c = lane; c < nb; c += 32) {
         const TW base = (c == t) ? (TW)0 : src[c];
-        xi[c] = (f != (TW)0) ? base - f * srow[c] : base;
+        xi[c] = nz ? base - f * srow[c] : base;
       }
     }
     __syncthreads();  // the next column's candidates read the eliminated rows
