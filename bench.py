@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed", "fp64_tc"])
+    p.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp32", "mixed", "fp64_tc"])
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--k", type=int, default=8)
     p.add_argument("--blocks-per-step", type=int, default=8)
@@ -385,6 +385,13 @@ def main():
         r = inv_ref[i * b:(i + 1) * b, j * b:(j + 1) * b]
         errs.append(float(np.linalg.norm(outs[q].double().cpu().numpy() - r) / np.linalg.norm(r)))
     del inv_ref
+    # the same block on the plain FP64 CUDA-core path: how far the tensor-core path is from it
+    diff_fp64 = None
+    if args.precision == "fp64_tc":
+        i0, j0 = rank_blocks(k, rank, world, args.warmup + args.steps - 1, bps)[0]
+        with mb.Context(M, k, precision="fp64") as c64:
+            ref64 = c64.block(i0, j0).double().cpu().numpy()
+        diff_fp64 = float(np.linalg.norm(outs[0].double().cpu().numpy() - ref64) / np.linalg.norm(ref64))
 
     # roofline of each kernel family; the dominant one (most device time) heads the line
     pk, pk_src = peaks()
@@ -432,7 +439,8 @@ def main():
                        "blocks_per_step": bps, "precision": args.precision, "slices": args.slices,
                        "refine": args.refine,
                        "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",
-                       "max_rel_err_vs_dense_inverse": max(errs)},
+                       "max_rel_err_vs_dense_inverse": max(errs),
+                       "rel_diff_vs_fp64_path": diff_fp64},
             "roofline": roofline, "gpu_launches": agg["launches"],
             "peak_device_bytes": agg["peak_device_bytes"], "clocks": clk}
     ctx.close()

@@ -299,23 +299,29 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
       const int c0 = h * 32 + pass * 16;
-      uint32_t acc[ND][16];
+      if (tn * BN + c0 >= pr.n) continue;  // columns past this problem (narrow updates)
+      // four columns at a time through the groups: a rolled loop keeps the
+      // code small (instruction-cache friendly) and the registers few
+#pragma unroll 1
+      for (int cq = 0; cq < 16; cq += 4) {
+        uint32_t acc[ND][4];
 #pragma unroll
-      for (int gg = 0; gg < ND; ++gg) tmem_ld16_async(trow + 64 * gg + c0, acc[gg]);
-      tmem_wait();
+        for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
+        tmem_wait();
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int fj = fexp[c0 + t];
-        double v;
-        if (ei >= kNonFinite || fj >= kNonFinite) {
-          v = __longlong_as_double(0x7FF8000000000000LL);
-        } else {
-          int a[ND];
+        for (int t = 0; t < 4; ++t) {
+          const int fj = fexp[c0 + cq + t];
+          double v;
+          if (ei >= kNonFinite || fj >= kNonFinite) {
+            v = __longlong_as_double(0x7FF8000000000000LL);
+          } else {
+            int a[ND];
 #pragma unroll
-          for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][t]));
-          v = combine(a, ei + fj - 61, amode, P.alpha);
+            for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][t]));
+            v = combine(a, ei + fj - 61, amode, P.alpha);
+          }
+          T[lane * 17 + cq + t] = v;
         }
-        T[lane * 17 + t] = v;
       }
       __syncwarp();
       const int col = tn * BN + c0 + cc;
