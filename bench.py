@@ -356,7 +356,9 @@ def main():
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     agg = {"gemm_flops": 0.0, "inv_flops": 0.0, "gemm_device_seconds": 0.0, "inv_device_seconds": 0.0,
-           "launches": 0, "gemm_launches": 0, "inversions": 0, "peak_device_bytes": 0}
+           "launches": 0, "gemm_launches": 0, "inversions": 0, "peak_device_bytes": 0,
+           "pack_device_seconds": 0.0, "inv_panel_device_seconds": 0.0, "inv_panel_flops": 0.0,
+           "inv_update_flops": 0.0}
     torch.cuda.synchronize()
     for s in range(args.steps):
         flush.fill_(s & 0xFF)  # L2 flush, outside the timed interval
@@ -401,31 +403,49 @@ def main():
            "mixed": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
            "fp64_tc": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)")}[args.precision]
     fams = {}
+    tc_src = f"bf16_tflops_sustained ({pk_src})"
     if args.precision == "mixed":
         fams["tc_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * npairs,
                                   "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
                                   "peak": pk["bf16_tflops_sustained"],
-                                  "peak_source": f"bf16_tflops_sustained ({pk_src}), executed BF16 slice products"}
+                                  "peak_source": f"{tc_src}, executed BF16 slice products"}
     elif args.precision == "fp64_tc":
         fams["oz_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * DIGIT_PAIRS,
                                   "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
                                   "peak": pk["bf16_tflops_sustained"],
-                                  "peak_source": f"bf16_tflops_sustained ({pk_src}), executed BF16 digit-pair "
-                                                 f"products ({DIGIT_PAIRS} per FP64 product)"}
+                                  "peak_source": f"{tc_src}, executed BF16 digit-pair products "
+                                                 f"({DIGIT_PAIRS} per FP64 product); Schur products only"}
     else:
         fams["gemm_grouped_kernel"] = {"bound": "alu", "work": agg["gemm_flops"], "dsec": agg["gemm_device_seconds"],
                                        "launches": agg["gemm_launches"], "peak": alu[0], "peak_source": alu[1]}
-    fams["gauss_jordan_inverse"] = {"bound": "alu", "work": agg["inv_flops"], "dsec": agg["inv_device_seconds"],
-                                    "launches": agg["inversions"], "peak": alu[0] if args.precision != "fp32"
-                                    else FP32_NOMINAL_GFLOPS / 1e3, "peak_source": alu[1]}
+    fp_peak = alu
+    fams["gj_panel_kernel"] = {"bound": "alu", "work": agg["inv_panel_flops"],
+                               "dsec": agg["inv_panel_device_seconds"], "launches": None,
+                               "peak": fp_peak[0], "peak_source": fp_peak[1] + "; panel factorisations, 2 b w^2 "
+                                                                  "flop per panel of width w"}
+    upd_dsec = agg["inv_device_seconds"] - agg["inv_panel_device_seconds"]
+    if args.precision == "fp64_tc":
+        fams["gj_trailing_update"] = {"bound": "tensor", "work": agg["inv_update_flops"] * DIGIT_PAIRS,
+                                      "dsec": upd_dsec, "launches": None, "peak": pk["bf16_tflops_sustained"],
+                                      "peak_source": f"{tc_src}, executed digit-pair products of the trailing "
+                                                     "updates; time includes their digit packs and the inverses' "
+                                                     "init/finalize"}
+    else:
+        fams["gj_trailing_update"] = {"bound": "alu", "work": agg["inv_update_flops"], "dsec": upd_dsec,
+                                      "launches": None, "peak": fp_peak[0],
+                                      "peak_source": fp_peak[1] + "; gj_update_kernel, time includes the "
+                                                                  "inverses' init/finalize"}
     kernels = {}
     for name, f in fams.items():
         ach = f["work"] / f["dsec"] / 1e12 if f["dsec"] > 0 else 0.0
         kernels[name] = {"bound": f["bound"], "achieved": ach, "peak": f["peak"], "unit": "TFLOP/s",
                          "frac": ach / f["peak"], "device_seconds": f["dsec"], "peak_source": f["peak_source"]}
-        if name == "oz_gemm_kernel":
+        if args.precision == "fp64_tc" and f["bound"] == "tensor":
             kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
-    dom = max(kernels, key=lambda k: kernels[k]["device_seconds"])
+    if agg["pack_device_seconds"] > 0:
+        kernels["operand_packing"] = {"device_seconds": agg["pack_device_seconds"],
+                                      "note": "digit or slice packing of the Schur operands (HBM/L2 bound)"}
+    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: kernels[k]["device_seconds"])
     roofline = dict(kernels[dom])
     roofline.update({"kernel": dom, "traffic": None, "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
                      "families": kernels})

@@ -106,6 +106,18 @@ typedef struct {
     double inv_device_seconds;  /* profile = 1: device time of the inverse
                                    launches */
     size_t gemm_launches;       /* Schur product launches */
+    double pack_device_seconds; /* profile = 1: device time of operand
+                                   packing (FP64_TC digits, MIXED_BF16
+                                   slices) */
+    double inv_panel_device_seconds; /* profile = 1: the part of
+                                   inv_device_seconds spent in the panel
+                                   factorisations */
+    double inv_panel_flops;     /* algorithmic flops of the panel
+                                   factorisations: 2 b w^2 per panel of
+                                   width w */
+    double inv_update_flops;    /* algorithmic flops of the trailing
+                                   updates: 2 b w (b - w) per panel (with
+                                   inv_panel_flops, 2 b^3 per inverse) */
 } mbinv_report;
 
 typedef struct mbinv_ctx mbinv_ctx;

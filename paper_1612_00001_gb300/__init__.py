@@ -47,7 +47,9 @@ class Report(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("peak_device_bytes", ctypes.c_size_t),
                 ("frames", ctypes.c_size_t), ("inversions", ctypes.c_size_t), ("launches", ctypes.c_size_t),
                 ("failed_pivot", ctypes.c_int64), ("gemm_device_seconds", ctypes.c_double),
-                ("inv_device_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_size_t)]
+                ("inv_device_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_size_t),
+                ("pack_device_seconds", ctypes.c_double), ("inv_panel_device_seconds", ctypes.c_double),
+                ("inv_panel_flops", ctypes.c_double), ("inv_update_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -246,6 +246,16 @@ struct Req {
   int64_t ldd;
 };
 
+// Device seconds and flop split of the last run of env (profile option).
+void add_env_report(mbinv_report* r, const Env& env) {
+  r->gemm_device_seconds += env.gemm_dev_s;
+  r->inv_device_seconds += env.inv_dev_s;
+  r->pack_device_seconds += env.pack_dev_s;
+  r->inv_panel_device_seconds += env.inv_panel_dev_s;
+  r->inv_panel_flops += env.inv_panel_flops;
+  r->inv_update_flops += env.inv_update_flops;
+}
+
 void add_report(mbinv_report* r, const mbinv_ctx* c, const Schedule& S, size_t nreq) {
   if (!r) return;
   const double b3 = (double)c->b * (double)c->b * (double)c->b;
@@ -306,8 +316,7 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
     for (int q = 0; q < G; ++q) add_report(rep, c, *sch[q], 1);
     rep->launches += (size_t)c->env.launches;
     rep->gemm_launches += (size_t)c->env.gemm_launches;
-    rep->gemm_device_seconds += c->env.gemm_dev_s;
-    rep->inv_device_seconds += c->env.inv_dev_s;
+    add_env_report(rep, c->env);
     rep->peak_device_bytes = std::max(rep->peak_device_bytes, c->peak);
     if (s == MBINV_ESINGULAR && rep->failed_pivot < 0)
       for (int q = 0; q < G; ++q)
@@ -801,6 +810,10 @@ static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, 
       rep->gemm_launches += r.gemm_launches;
       rep->gemm_device_seconds += r.gemm_device_seconds;
       rep->inv_device_seconds += r.inv_device_seconds;
+      rep->pack_device_seconds += r.pack_device_seconds;
+      rep->inv_panel_device_seconds += r.inv_panel_device_seconds;
+      rep->inv_panel_flops += r.inv_panel_flops;
+      rep->inv_update_flops += r.inv_update_flops;
       rep->peak_device_bytes = std::max(rep->peak_device_bytes, r.peak_device_bytes);
     }
     if (s != MBINV_OK) return s;
@@ -987,8 +1000,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     if (rep) {
       rep->launches += env.launches;
       rep->gemm_launches += env.gemm_launches;
-      rep->gemm_device_seconds += env.gemm_dev_s;
-      rep->inv_device_seconds += env.inv_dev_s;
+      add_env_report(rep, env);
     }
     peak = std::max(peak, used);
     // the finished members' device memory goes before the next wave

@@ -27,6 +27,8 @@ void Env::release() {
   hdesc.release();
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   events.clear();
+  for (cudaEvent_t e : pevents) cudaEventDestroy(e);
+  pevents.clear();
 }
 
 size_t slot_bytes_for(int b, int precision) {
@@ -140,6 +142,7 @@ size_t digit_bytes(int bmax, size_t ops) {
 mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   E.launches = E.gemm_launches = 0;
   E.gemm_dev_s = E.inv_dev_s = E.pack_dev_s = 0;
+  E.inv_panel_dev_s = E.inv_panel_flops = E.inv_update_flops = 0;
   E.job_singular.assign(jobs.size(), 0);
   if (jobs.empty()) return MBINV_OK;
   const bool mixed = E.precision == MBINV_MIXED_BF16;
@@ -271,6 +274,10 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           d.tag = ops[u].first;
           d.flag = dflags + ops[u].first;
           bm = std::max(bm, J.b);
+          double pf, uf;
+          inv_flop_split(J.b, wt, ozk, &pf, &uf);
+          E.inv_panel_flops += pf;
+          E.inv_update_flops += uf;
           hd[u - c0] = d;
         }
         Launch l{Launch::INV, o, (int)(c1 - c0)};
@@ -529,6 +536,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   CUE(cudaMemsetAsync(E.flags.p, 0, jobs.size() * sizeof(int), E.stream));
   if (mixed || ozk) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
   if (E.profile) CUE(ensure_events(E, 2 * L.size()));
+  size_t pused = 0;  // panel timing events taken
   const InvTc itc{E.inv_tc.p, (int*)E.tcerr.p};
   tc::TcParams P{};
   if (mixed) {
@@ -541,8 +549,22 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
     if (E.profile) CUE(cudaEventRecord(E.events[2 * q], E.stream));
     switch (l.kind) {
       case Launch::INV:
+      {
+        InvTiming tm{nullptr, 0, 0};
+        if (E.profile) {
+          const size_t need = pused + 2 * ((size_t)l.bmax / 32 + 2);
+          while (E.pevents.size() < need) {
+            cudaEvent_t ev;
+            CUE(cudaEventCreate(&ev));
+            E.pevents.push_back(ev);
+          }
+          tm = InvTiming{E.pevents.data() + pused, (int)(need - pused), 0};
+        }
         CUE(run_inverse_batch(l.in_dt, l.out_dt, wt, (const InvDesc*)(dbase + l.off), l.count, l.bmax,
-                              (DevStatus*)E.status.p, E.stream, &E.launches, ozk ? &itc : nullptr));
+                              (DevStatus*)E.status.p, E.stream, &E.launches, ozk ? &itc : nullptr,
+                              E.profile ? &tm : nullptr));
+        pused += tm.n;
+      }
         break;
       case Launch::GEMM:
         CUE(launch_gemm_grouped(l.combo, (const GemmDesc*)(dbase + l.off), l.count, l.tiles, E.stream));
@@ -610,6 +632,11 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
       if (L[q].kind == Launch::INV) E.inv_dev_s += ms * 1e-3;
       else if (L[q].kind == Launch::PACK || L[q].kind == Launch::OZPACK) E.pack_dev_s += ms * 1e-3;
       else E.gemm_dev_s += ms * 1e-3;
+    }
+    for (size_t q = 0; q + 1 < pused; q += 2) {
+      float ms = 0;
+      CUE(cudaEventElapsedTime(&ms, E.pevents[q], E.pevents[q + 1]));
+      E.inv_panel_dev_s += ms * 1e-3;
     }
   }
   if (herr) return MBINV_ETIMEOUT;

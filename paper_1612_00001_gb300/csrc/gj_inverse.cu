@@ -396,7 +396,7 @@ __global__ void gj_finalize_kernel(const InvDesc* __restrict__ descs, int rows_p
 
 template <typename TW>
 cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int count, int b, DevStatus* d_status,
-                        cudaStream_t s, int* launches, const InvTc* tc) {
+                        cudaStream_t s, int* launches, const InvTc* tc, InvTiming* tm) {
   int nl = 0;
   zero_amax_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count);
   ++nl;
@@ -434,8 +434,14 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const bool timed = tm && tm->n + 2 <= tm->cap;
+    if (timed) cudaEventRecord(tm->ev[tm->n], s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status);
     if (e != cudaSuccess) return e;
+    if (timed) {
+      cudaEventRecord(tm->ev[tm->n + 1], s);
+      tm->n += 2;
+    }
     ++nl;
     if (w < b && tc) {  // the trailing update on the tensor cores
       const TcLayout T = tc_layout(b, count);
@@ -502,12 +508,25 @@ int inv_panel_width(int b, int wtype, bool tc) {
 
 size_t inv_tc_bytes(int bmax, int count) { return tc_layout(bmax, count).total; }
 
+void inv_flop_split(int b, int wtype, bool tc, double* panel_flops, double* update_flops) {
+  const int nb = inv_panel_width(b, wtype, tc);
+  double pf = 0, uf = 0;
+  for (int p = 0; p < b; p += nb) {
+    const double w = std::min(nb, b - p);
+    pf += 2.0 * b * w * w;
+    uf += 2.0 * b * w * (b - w);
+  }
+  *panel_flops = pf;
+  *update_flops = uf;
+}
+
 cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
-                              DevStatus* d_status, cudaStream_t s, int* launches, const InvTc* tc) {
+                              DevStatus* d_status, cudaStream_t s, int* launches, const InvTc* tc,
+                              InvTiming* timing) {
   if (count <= 0) return cudaSuccess;
-  if (wtype == F64) return run_batch_t<double>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, tc);
+  if (wtype == F64) return run_batch_t<double>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, tc, timing);
   if (tc) return cudaErrorInvalidValue;
-  return run_batch_t<float>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, nullptr);
+  return run_batch_t<float>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, nullptr, timing);
 }
 
 }  // namespace mbinv

@@ -128,12 +128,23 @@ struct InvTc {
   int* err;       // raised when a wait of the product kernel ran out
 };
 size_t inv_tc_bytes(int bmax, int count);
+// Optional timing of run_inverse_batch: an event is recorded before and after
+// every panel launch (ev[n], ev[n + 1], n += 2) while n + 2 <= cap.
+struct InvTiming {
+  cudaEvent_t* ev;
+  int cap;
+  int n;
+};
+// Panel width and algorithmic flops of the panel factorisations and of the
+// trailing updates of one inverse of order b.
+void inv_flop_split(int b, int wtype, bool tc, double* panel_flops, double* update_flops);
 // Inverts count matrices described by d_desc; b is the largest order among
 // them (each descriptor carries its own).  in_dtype / out_dtype / wtype are
 // DType values; wtype is F64 or F32.  The max|entry| words are zeroed by the
 // call.  With tc (FP64 only) the trailing updates are exact digit products
 // on the tensor cores instead of FP64 tile products.
 cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,
-                              DevStatus* d_status, cudaStream_t s, int* launches, const InvTc* tc = nullptr);
+                              DevStatus* d_status, cudaStream_t s, int* launches, const InvTc* tc = nullptr,
+                              InvTiming* timing = nullptr);
 
 }  // namespace mbinv

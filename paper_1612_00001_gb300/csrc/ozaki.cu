@@ -22,21 +22,25 @@
 // rounding.  GB300's FP64 pipe is narrow, so the epilogue does everything but
 // that last add with integer instructions.
 //
-// Kernel.  One CTA per 128 x 64 output tile, 256 threads, one CTA per SM (the
-// eight 64-column group accumulators take all 512 TMEM columns):
+// Kernel.  Persistent: one CTA per SM (the eight 64-column group
+// accumulators take all 512 TMEM columns) walks the 128 x 64 output tiles of
+// the launch, with three roles:
 //   warp 0, one lane:  TMA producer.  Per K block of 64 it loads all eight
 //                      digits of the B tile in one 3-D copy (64 KB, double
 //                      buffered) and each digit of the A tile (16 KB) into a
-//                      four-deep ring.
+//                      four-deep ring; it runs ahead into the next tile while
+//                      the current one is read out.
 //   warp 1, one lane:  MMA issuer.  For A digit p one tcgen05.mma (two when
 //                      more than four B digits remain) multiplies it by the
 //                      B digits q = 0..7-p stacked along N, writing TMEM
 //                      columns 64 (p + q) - so every pair lands in its group
-//                      G_{p+q} without any data movement.
-//   all warps:         epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..,
-//                      columns half w / 4, combines the groups, and writes
-//                      beta * Cin + alpha * C through a shared-memory stage
-//                      so that rows are read and written contiguously.
+//                      G_{p+q} without any data movement.  It starts a tile
+//                      once the epilogue has read the previous one out.
+//   warps 2-9:         epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..,
+//                      one half of the columns, combines the groups, and
+//                      writes beta * Cin + alpha * C through its own shared-
+//                      memory stage so that rows are read and written
+//                      contiguously; Cin is fetched while the MMAs run.
 // Every mbarrier wait is bounded (about two seconds of %globaltimer); a wait
 // that runs out raises the error word and the CTA drains, frees its TMEM and
 // returns.
@@ -57,7 +61,8 @@ using namespace mbinv::ptx;
 constexpr int ND = kDigits;
 constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int ASTAGES = 4;
-constexpr int THREADS = 256;
+constexpr int NEPI = 8;                   // epilogue warps
+constexpr int THREADS = 64 + 32 * NEPI;   // producer warp, MMA warp, epilogue warps
 constexpr int PR = 32;                                  // slab rows per pack CTA
 constexpr uint32_t A_BYTES = BM * BK * 2;               // one digit of the A tile: 16 KB
 constexpr uint32_t BQ_BYTES = BN * BK * 2;              // one digit of the B tile: 8 KB
@@ -146,31 +151,48 @@ __device__ __forceinline__ double combine(const int (&a)[ND], int e, int amode, 
   return v;
 }
 
+// Decodes grid tile t: problem g, row tile tm, column tile tn; false when the
+// tile lies past its problem's extent or wholly inside its skipped columns.
+__device__ __forceinline__ bool tile_live(const Params& P, const Problem* __restrict__ probs, int t, int* g, int* tm,
+                                          int* tn) {
+  const int tiles_per = P.tiles_m * P.tiles_n;
+  *g = t / tiles_per;
+  const int rem = t - *g * tiles_per;
+  *tm = rem / P.tiles_n;
+  *tn = rem - *tm * P.tiles_n;
+  const Problem& pr = probs[*g];
+  return !(*tm * BM >= pr.m || *tn * BN >= pr.n || (*tn * BN >= pr.skip_c0 && *tn * BN + BN <= pr.skip_c1));
+}
+
+// All eight digits of the B tile of one K block into the next of two buffers.
+__device__ __forceinline__ bool load_b_block(uint8_t* sB, uint64_t* fullB, uint64_t* emptyB, const CUtensorMap* tmB,
+                                             int* nbq, int kb, int tn, int bslab) {
+  const int s = *nbq & 1;
+  if (*nbq >= 2 && !mbar_wait(&emptyB[s], ((uint32_t)(*nbq >> 1) & 1u) ^ 1u)) return false;
+  mbar_expect_tx(&fullB[s], B_BYTES);
+  tma_load_3d(sB + s * B_BYTES, tmB, &fullB[s], kb * BK, tn * BN, bslab * ND);
+  ++*nbq;
+  return true;
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params P,
-                   const Problem* __restrict__ probs) {
+                   const Problem* __restrict__ probs, int total_tiles) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sB = base;                 // 2 x 64 KB
-  uint8_t* sA = base + 2 * B_BYTES;   // ASTAGES x 16 KB
-  uint64_t* fullB = (uint64_t*)(sA + ASTAGES * A_BYTES);
+  uint8_t* sB = base;                          // 2 x 64 KB
+  uint8_t* sA = base + 2 * B_BYTES;            // ASTAGES x 16 KB
+  double* stage = (double*)(sA + ASTAGES * A_BYTES);  // epilogue staging, 4 KB per epilogue warp
+  uint64_t* fullB = (uint64_t*)(stage + NEPI * 32 * 16);
   uint64_t* emptyB = fullB + 2;
   uint64_t* fullA = emptyB + 2;
   uint64_t* emptyA = fullA + ASTAGES;
-  uint64_t* done = emptyA + ASTAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* tfull = emptyA + ASTAGES;   // accumulators of a tile complete (MMA -> epilogue)
+  uint64_t* tempty = tfull + 1;         // accumulators read out (epilogue -> MMA)
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
   int* failed = (int*)(tmem_slot + 1);
-  int* fexp = failed + 1;  // exponents of this tile's 64 output columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_per = P.tiles_m * P.tiles_n;
-  const int g = blockIdx.x / tiles_per;
-  const int rem = blockIdx.x - g * tiles_per;
-  const int tm = rem / P.tiles_n, tn = rem - (rem / P.tiles_n) * P.tiles_n;
-  const Problem pr = probs[g];
-  // tiles past this problem's extent, or wholly inside its skipped columns
-  if (tm * BM >= pr.m || tn * BN >= pr.n || (tn * BN >= pr.skip_c0 && tn * BN + BN <= pr.skip_c1)) return;
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(&fullB[s], 1);
@@ -180,13 +202,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&fullA[s], 1);
       mbar_init(&emptyA[s], 1);
     }
-    mbar_init(done, 1);
+    mbar_init(tfull, 1);
+    mbar_init(tempty, NEPI);
     *failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
   }
-  if (threadIdx.x < BN) fexp[threadIdx.x] = P.eb[(int64_t)pr.b_slab * P.eb_rows + tn * BN + threadIdx.x];
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TMEM_COLS)
@@ -198,144 +220,182 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // Epilogue geometry: warp w reads TMEM lanes 32 (w mod 4) .. (rows) and
-  // columns half w / 4; it writes two rows of 16 columns per pass.  Its share
-  // of Cin (zero where a row takes no addend) is fetched now, so that the
-  // loads overlap the main loop instead of stalling the epilogue.
-  const int q = warp & 3, h = warp >> 2;
-  const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + tm * BM + q * 32 + lane];
-  const int rr = lane >> 4, cc = lane & 15;
-  double cpre[2][16];
-#pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-    const int col = tn * BN + h * 32 + pass * 16 + cc;
-#pragma unroll
-    for (int r2 = 0; r2 < 16; ++r2) {
-      const int grow = tm * BM + q * 32 + 2 * r2 + rr;
-      cpre[pass][r2] = (pr.cin && grow < pr.m && col < pr.n && (grow < pr.nocin_r0 || grow >= pr.nocin_r1))
-                           ? pr.cin[(int64_t)grow * pr.ldcin + col]
-                           : 0.0;
-    }
-  }
-  const int amode = P.alpha == 1.0 ? 0 : (P.alpha == -1.0 ? 1 : 2);
-  const bool beta1 = P.beta == 1.0;
-
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    auto load_b = [&](int u) -> bool {
-      const int s = u & 1;
-      if (u >= 2 && !mbar_wait(&emptyB[s], ((uint32_t)(u >> 1) & 1u) ^ 1u)) return false;
-      mbar_expect_tx(&fullB[s], B_BYTES);
-      tma_load_3d(sB + s * B_BYTES, &tmB, &fullB[s], (P.kb0 + u) * BK, tn * BN, pr.b_slab * ND);
-      return true;
-    };
-    bool ok = load_b(0);
-    for (int u = 0; ok && u < P.nkb; ++u) {
-      for (int p = 0; p < ND; ++p) {
-        const int n = u * ND + p, s = n % ASTAGES;
-        if (n >= ASTAGES && !mbar_wait(&emptyA[s], ((uint32_t)(n / ASTAGES) & 1u) ^ 1u)) {
-          ok = false;
-          break;
-        }
-        if (*(volatile int*)failed) {
-          ok = false;
-          break;
-        }
-        mbar_expect_tx(&fullA[s], A_BYTES);
-        tma_load_3d(sA + s * A_BYTES, &tmA, &fullA[s], (P.kb0 + u) * BK, tm * BM, pr.a_slab * ND + p);
-        // the next B tile goes out early: its buffer was freed with K block u - 1
-        if (p == 1 && u + 1 < P.nkb && !load_b(u + 1)) {
-          ok = false;
-          break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: runs ahead into the next tile while the
+      // epilogue of the current one drains the accumulators
+      int na = 0, nbq = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+        int g, tm, tn;
+        if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
+        const int aslab = probs[g].a_slab, bslab = probs[g].b_slab;
+        ok = load_b_block(sB, fullB, emptyB, &tmB, &nbq, P.kb0, tn, bslab);
+        for (int u = 0; ok && u < P.nkb; ++u) {
+          for (int p = 0; p < ND; ++p) {
+            const int s = na % ASTAGES;
+            if ((na >= ASTAGES && !mbar_wait(&emptyA[s], ((uint32_t)(na / ASTAGES) & 1u) ^ 1u)) ||
+                *(volatile int*)failed) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(&fullA[s], A_BYTES);
+            tma_load_3d(sA + s * A_BYTES, &tmA, &fullA[s], (P.kb0 + u) * BK, tm * BM, aslab * ND + p);
+            ++na;
+            // the next K block's B goes out early: its buffer was freed with block u - 1
+            if (p == 1 && u + 1 < P.nkb && !load_b_block(sB, fullB, emptyB, &tmB, &nbq, P.kb0 + u + 1, tn, bslab)) {
+              ok = false;
+              break;
+            }
+          }
         }
       }
+      if (!ok) atomicExch(failed, 1);
     }
-    if (!ok) atomicExch(failed, 1);
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    bool ok = true;
-    for (int u = 0; ok && u < P.nkb; ++u) {
-      const int sb = u & 1;
-      if (!mbar_wait(&fullB[sb], (uint32_t)(u >> 1) & 1u)) {
-        ok = false;
-        break;
-      }
-      const uint32_t b0 = smem_u32(sB + sb * B_BYTES);
-      for (int p = 0; p < ND; ++p) {
-        const int n = u * ND + p, s = n % ASTAGES;
-        if (!mbar_wait(&fullA[s], (uint32_t)(n / ASTAGES) & 1u)) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int na = 0, nbq = 0, it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+        int g, tm, tn;
+        if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
+        // the epilogue has read the previous tile's accumulators out
+        if (it > 0 && !mbar_wait(tempty, (uint32_t)(it - 1) & 1u)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * A_BYTES);
-        const int nq0 = ND - p < 4 ? ND - p : 4, nq1 = ND - p - nq0;
-        const uint32_t id0 = idesc(64 * nq0), id1 = idesc(64 * (nq1 > 0 ? nq1 : 1));
-#pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          // the first MMAs (digit 0 of the first K block) start all eight groups
-          const uint32_t acc = (u > 0 || p > 0 || kk > 0) ? 1u : 0u;
-          const uint64_t ad = sdesc(a0 + kk * 32);
-          umma(tmem + 64 * p, ad, sdesc(b0 + kk * 32), id0, acc);
-          if (nq1 > 0) umma(tmem + 64 * (p + 4), ad, sdesc(b0 + 4 * BQ_BYTES + kk * 32), id1, acc);
-        }
-        umma_commit(&emptyA[s]);
-      }
-      umma_commit(&emptyB[sb]);
-    }
-    if (!ok) atomicExch(failed, 1);
-    umma_commit(done);  // arrives when every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // ---------------- epilogue
-  const bool ok = mbar_wait(done, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok || *(volatile int*)failed) {
-    if (lane == 0 && P.err) atomicExch(P.err, 1);
-  } else {
-    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    double* T = (double*)sA + warp * (32 * 17);  // the A ring is idle once every MMA has completed
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-      const int c0 = h * 32 + pass * 16;
-      if (tn * BN + c0 >= pr.n) continue;  // columns past this problem (narrow updates)
-      // four columns at a time through the groups: a rolled loop keeps the
-      // code small (instruction-cache friendly) and the registers few
-#pragma unroll 1
-      for (int cq = 0; cq < 16; cq += 4) {
-        uint32_t acc[ND][4];
-#pragma unroll
-        for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
-        tmem_wait();
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int fj = fexp[c0 + cq + t];
-          double v;
-          if (ei >= kNonFinite || fj >= kNonFinite) {
-            v = __longlong_as_double(0x7FF8000000000000LL);
-          } else {
-            int a[ND];
-#pragma unroll
-            for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][t]));
-            v = combine(a, ei + fj - 61, amode, P.alpha);
+        for (int u = 0; ok && u < P.nkb; ++u) {
+          const int sb = nbq & 1;
+          if (!mbar_wait(&fullB[sb], (uint32_t)(nbq >> 1) & 1u)) {
+            ok = false;
+            break;
           }
-          T[lane * 17 + cq + t] = v;
-        }
-      }
-      __syncwarp();
-      const int col = tn * BN + c0 + cc;
+          const uint32_t b0 = smem_u32(sB + sb * B_BYTES);
+          for (int p = 0; p < ND; ++p) {
+            const int s = na % ASTAGES;
+            if (!mbar_wait(&fullA[s], (uint32_t)(na / ASTAGES) & 1u)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * A_BYTES);
+            const int nq0 = ND - p < 4 ? ND - p : 4, nq1 = ND - p - nq0;
+            const uint32_t id0 = idesc(64 * nq0), id1 = idesc(64 * (nq1 > 0 ? nq1 : 1));
 #pragma unroll
-      for (int r2 = 0; r2 < 16; ++r2) {
-        const int lr = 2 * r2 + rr;
-        const int grow = tm * BM + q * 32 + lr;
-        if (grow < pr.m && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) {
-          const double y = T[lr * 17 + cc];
-          const double ci = cpre[pass][r2];
-          pr.out[(int64_t)grow * pr.ldo + col] = beta1 ? ci + y : fma(P.beta, ci, y);
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              // the first MMAs (digit 0 of the first K block) start all eight groups
+              const uint32_t acc = (u > 0 || p > 0 || kk > 0) ? 1u : 0u;
+              const uint64_t ad = sdesc(a0 + kk * 32);
+              umma(tmem + 64 * p, ad, sdesc(b0 + kk * 32), id0, acc);
+              if (nq1 > 0) umma(tmem + 64 * (p + 4), ad, sdesc(b0 + 4 * BQ_BYTES + kk * 32), id1, acc);
+            }
+            umma_commit(&emptyA[s]);
+            ++na;
+          }
+          umma_commit(&emptyB[sb]);
+          ++nbq;
+        }
+        umma_commit(tfull);  // arrives when every MMA of this tile has completed
+        ++it;
+      }
+      if (!ok) atomicExch(failed, 1);
+    }
+  } else {
+    // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w mod 4) ..
+    // (rows of the tile) and one half of the columns; per 16-column pass it
+    // combines the eight groups four columns at a time, stages the FP64 values
+    // (XOR-swizzled rows of 16) and writes two rows of 16 per instruction.
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int rr = lane >> 4, cc = lane & 15;
+    const int amode = P.alpha == 1.0 ? 0 : (P.alpha == -1.0 ? 1 : 2);
+    const bool beta1 = P.beta == 1.0;
+    double* T = stage + (warp - 2) * (32 * 16);
+    int it = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+      int g, tm, tn;
+      if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
+      const Problem pr = probs[g];
+      const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + tm * BM + q * 32 + lane];
+      const int fcol = P.eb[(int64_t)pr.b_slab * P.eb_rows + tn * BN + h * 32 + lane];  // lane = column
+      // this warp's share of Cin (zero where a row takes no addend), fetched
+      // while the tile's MMAs run
+      double cpre[2][16];
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const int col = tn * BN + h * 32 + pass * 16 + cc;
+#pragma unroll
+        for (int r2 = 0; r2 < 16; ++r2) {
+          const int grow = tm * BM + q * 32 + 2 * r2 + rr;
+          cpre[pass][r2] = (pr.cin && grow < pr.m && col < pr.n && (grow < pr.nocin_r0 || grow >= pr.nocin_r1))
+                               ? pr.cin[(int64_t)grow * pr.ldcin + col]
+                               : 0.0;
         }
       }
-      __syncwarp();
+      const bool ok = mbar_wait(tfull, (uint32_t)it & 1u);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok || *(volatile int*)failed) {
+        if (lane == 0 && P.err) atomicExch(P.err, 1);
+        atomicExch(failed, 1);
+        break;
+      }
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      const int npass = (tn * BN + h * 32 >= pr.n) ? 0 : (tn * BN + h * 32 + 16 >= pr.n ? 1 : 2);
+      if (npass == 0) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty);
+      }
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass < npass) {
+        const int c0 = h * 32 + pass * 16;
+#pragma unroll 1
+        for (int cq = 0; cq < 16; cq += 4) {
+          uint32_t acc[ND][4];
+#pragma unroll
+          for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
+          tmem_wait();
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = pass * 16 + cq + u;  // column within this warp's half
+            const int fj = __shfl_sync(0xffffffffu, fcol, c);
+            double v;
+            if (ei >= kNonFinite || fj >= kNonFinite) {
+              v = __longlong_as_double(0x7FF8000000000000LL);
+            } else {
+              int a[ND];
+#pragma unroll
+              for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
+              v = combine(a, ei + fj - 61, amode, P.alpha);
+            }
+            const int cl = cq + u;
+            T[lane * 16 + (cl ^ (lane & 15))] = v;
+          }
+        }
+        if (pass == npass - 1) {
+          // every accumulator of this tile is in registers or staged: the MMA
+          // warp may start the next tile
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty);
+        }
+        __syncwarp();
+        const int col = tn * BN + c0 + cc;
+#pragma unroll
+        for (int r2 = 0; r2 < 16; ++r2) {
+          const int lr = 2 * r2 + rr;
+          const int grow = tm * BM + q * 32 + lr;
+          if (grow < pr.m && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) {
+            const double y = T[lr * 16 + (cc ^ (lr & 15))];
+            const double ci = cpre[pass][r2];
+            pr.out[(int64_t)grow * pr.ldo + col] = beta1 ? ci + y : fma(P.beta, ci, y);
+          }
+        }
+        __syncwarp();
+        }
+      }
+      ++it;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -436,7 +496,7 @@ int tile_m() { return BM; }
 int tile_n() { return BN; }
 int tile_k() { return BK; }
 int pack_rows() { return PR; }
-size_t smem_bytes() { return 2 * B_BYTES + ASTAGES * A_BYTES + 1024 + 512; }
+size_t smem_bytes() { return 2 * B_BYTES + ASTAGES * A_BYTES + NEPI * 32 * 16 * 8 + 1024 + 256; }
 
 cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kpad, __nv_bfloat16* dst, int* exps,
                         cudaStream_t s) {
@@ -465,8 +525,15 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int grid = count * P.tiles_m * P.tiles_n;
-  oz_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, P, d_probs);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int total = count * P.tiles_m * P.tiles_n;
+  oz_gemm_kernel<<<total < sms ? total : sms, THREADS, sm, s>>>(ta, tb, P, d_probs, total);
   return cudaGetLastError();
 }
 
