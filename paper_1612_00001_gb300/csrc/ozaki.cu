@@ -111,11 +111,18 @@ __device__ __forceinline__ void digits8(double x, int E, int (&d)[ND]) {
   d[0] = (int)X;
 }
 
-// alpha * 2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64
-// (ties to even); the exponent field is assembled directly unless the
-// result is subnormal or overflows.  amode: 0 alpha = 1, 1 alpha = -1, 2 any
-// other alpha (the FP64 comparisons are made once per thread, not per entry).
-__device__ __forceinline__ double combine(const int (&a)[ND], int e, int amode, double alpha) {
+// The rare results below the normal range or above it: mant 2^(e2 - 52),
+// through the FP64 pipe (kept out of line so that the common path issues no
+// FP64 instruction).
+__device__ __noinline__ double scale_rare(uint64_t mant, int e2, bool neg) {
+  const double v = scalbn((double)mant, e2 - 52);
+  return neg ? -v : v;
+}
+
+// +-2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64 (ties to
+// even), negated when neg_alpha; the exponent field is assembled directly
+// with integer instructions.
+__device__ __forceinline__ double combine(const int (&a)[ND], int e, bool neg_alpha) {
   const long long hi = ((a[0] * 128LL + a[1]) * 128LL + a[2]) * 128LL + a[3];
   const long long lo = ((a[4] * 128LL + a[5]) * 128LL + a[6]) * 128LL + a[7];
   const __int128 S = (__int128)hi * (__int128)(1LL << 28) + (__int128)lo;
@@ -137,18 +144,11 @@ __device__ __forceinline__ double combine(const int (&a)[ND], int e, int amode, 
       ++top;
     }
   }
-  if (amode == 1) neg = !neg;
+  neg ^= neg_alpha;
   const int e2 = top + e;  // value = mant 2^(e2 - 52)
-  double v;
-  if (e2 >= -1022 && e2 <= 1023) {
-    v = __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)(e2 + 1023) << 52) |
-                                         (mant & 0xFFFFFFFFFFFFFull)));
-  } else {
-    v = scalbn((double)mant, e2 - 52);
-    if (neg) v = -v;
-  }
-  if (amode == 2) v = alpha * v;
-  return v;
+  if (e2 < -1022 || e2 > 1023) return scale_rare(mant, e2, neg);
+  return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)(e2 + 1023) << 52) |
+                                          (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 // Decodes grid tile t: problem g, row tile tm, column tile tn; false when the
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // (XOR-swizzled rows of 16) and writes two rows of 16 per instruction.
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int rr = lane >> 4, cc = lane & 15;
-    const int amode = P.alpha == 1.0 ? 0 : (P.alpha == -1.0 ? 1 : 2);
-    const bool beta1 = P.beta == 1.0;
+    const bool neg_alpha = P.alpha < 0.0;  // alpha is +-1 and beta 0 or 1 (checked at launch)
+    const bool use_cin = P.beta != 0.0;
     double* T = stage + (warp - 2) * (32 * 16);
     int it = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int r2 = 0; r2 < 16; ++r2) {
           const int grow = tm * BM + q * 32 + 2 * r2 + rr;
-          cpre[pass][r2] = (pr.cin && grow < pr.m && col < pr.n && (grow < pr.nocin_r0 || grow >= pr.nocin_r1))
+          cpre[pass][r2] = (use_cin && pr.cin && grow < pr.m && col < pr.n &&
+                            (grow < pr.nocin_r0 || grow >= pr.nocin_r1))
                                ? pr.cin[(int64_t)grow * pr.ldcin + col]
                                : 0.0;
         }
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               int a[ND];
 #pragma unroll
               for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
-              v = combine(a, ei + fj - 61, amode, P.alpha);
+              v = combine(a, ei + fj - 61, neg_alpha);
             }
             const int cl = cq + u;
             T[lane * 16 + (cl ^ (lane & 15))] = v;
@@ -387,9 +388,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int lr = 2 * r2 + rr;
           const int grow = tm * BM + q * 32 + lr;
           if (grow < pr.m && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) {
-            const double y = T[lr * 16 + (cc ^ (lr & 15))];
-            const double ci = cpre[pass][r2];
-            pr.out[(int64_t)grow * pr.ldo + col] = beta1 ? ci + y : fma(P.beta, ci, y);
+            // the one FP64 instruction per entry: the Schur update's add
+            pr.out[(int64_t)grow * pr.ldo + col] = cpre[pass][r2] + T[lr * 16 + (cc ^ (lr & 15))];
           }
         }
         __syncwarp();
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // bit patterns of |x| order like the values; Inf and NaN sort above every
 // finite value), pass 2 writes the digits.  The source is staged through a
 // 32 x 64 shared tile so that both orientations read it contiguously.
-__global__ void __launch_bounds__(256, 2) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
+__global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
                                                        __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
   __shared__ double S[PR][65];
   __shared__ int sE[PR];
@@ -512,7 +512,8 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
   if (count <= 0) return cudaSuccess;
   if (P.kpad % BK || a_rows_pad % BM || b_rows_pad % BN || P.tiles_m * BM > a_rows_pad ||
       P.tiles_n * BN > b_rows_pad || P.nkb < 1 || P.nkb > kMaxKBlocks || P.kb0 < 0 ||
-      (P.kb0 + P.nkb) * BK > P.kpad || P.ea_rows != a_rows_pad || P.eb_rows != b_rows_pad)
+      (P.kb0 + P.nkb) * BK > P.kpad || P.ea_rows != a_rows_pad || P.eb_rows != b_rows_pad ||
+      (P.alpha != 1.0 && P.alpha != -1.0) || (P.beta != 0.0 && P.beta != 1.0))
     return cudaErrorInvalidValue;
   if (((uintptr_t)apk | (uintptr_t)bpk) & 15) return cudaErrorInvalidValue;
   CUtensorMap ta, tb;

@@ -25,6 +25,8 @@ struct PackDesc {
 
 // One product of a grouped launch:
 //     out = beta * Cin + alpha * A_slab * B_slab^T     (FP64, row-major, m x n)
+// with alpha = +-1 and beta = 0 or 1 (the Schur products and updates need no
+// other; the epilogue then spends one FP64 instruction per entry).
 // over the K blocks [kb0, kb0 + nkb) of the slabs.  Cin may be null; it may
 // also be out itself (each element is read once, then written).  Rows in
 // [nocin_r0, nocin_r1) take no Cin; columns in [skip_c0, skip_c1) are not
