@@ -36,11 +36,11 @@
 //                      columns 64 (p + q) - so every pair lands in its group
 //                      G_{p+q} without any data movement.  It starts a tile
 //                      once the epilogue has read the previous one out.
-//   warps 2-9:         epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..,
-//                      one half of the columns, combines the groups, and
-//                      writes beta * Cin + alpha * C through its own shared-
-//                      memory stage so that rows are read and written
-//                      contiguously; Cin is fetched while the MMAs run.
+//   warps 2-17:        epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..
+//                      (a row per thread) and one quarter of the columns,
+//                      combines the groups and writes beta * Cin + alpha * C,
+//                      16 contiguous entries per thread; Cin is fetched while
+//                      the MMAs run.
 // Every mbarrier wait is bounded (about two seconds of %globaltimer); a wait
 // that runs out raises the error word and the CTA drains, frees its TMEM and
 // returns.
@@ -61,7 +61,7 @@ using namespace mbinv::ptx;
 constexpr int ND = kDigits;
 constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int ASTAGES = 4;
-constexpr int NEPI = 8;                   // epilogue warps
+constexpr int NEPI = 16;                  // epilogue warps: 4 lane quarters x 4 column quarters
 constexpr int THREADS = 64 + 32 * NEPI;   // producer warp, MMA warp, epilogue warps
 constexpr int PR = 32;                                  // slab rows per pack CTA
 constexpr uint32_t A_BYTES = BM * BK * 2;               // one digit of the A tile: 16 KB
@@ -182,8 +182,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sB = base;                          // 2 x 64 KB
   uint8_t* sA = base + 2 * B_BYTES;            // ASTAGES x 16 KB
-  double* stage = (double*)(sA + ASTAGES * A_BYTES);  // epilogue staging, 4 KB per epilogue warp
-  uint64_t* fullB = (uint64_t*)(stage + NEPI * 32 * 16);
+  uint64_t* fullB = (uint64_t*)(sA + ASTAGES * A_BYTES);
   uint64_t* emptyB = fullB + 2;
   uint64_t* fullA = emptyB + 2;
   uint64_t* emptyA = fullA + ASTAGES;
@@ -304,36 +303,28 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w mod 4) ..
-    // (rows of the tile) and one half of the columns; per 16-column pass it
-    // combines the eight groups four columns at a time, stages the FP64 values
-    // (XOR-swizzled rows of 16) and writes two rows of 16 per instruction.
-    const int q = warp & 3, h = (warp - 2) >> 2;
-    const int rr = lane >> 4, cc = lane & 15;
+    // (one row of the tile per thread) and one quarter of the columns; it
+    // combines the eight groups two columns at a time and writes each row's
+    // 16 entries (128 contiguous bytes per thread).  Cin is fetched before the
+    // tile's accumulators are complete.
+    const int q = warp & 3, c0 = 16 * ((warp - 2) >> 2);
     const bool neg_alpha = P.alpha < 0.0;  // alpha is +-1 and beta 0 or 1 (checked at launch)
     const bool use_cin = P.beta != 0.0;
-    double* T = stage + (warp - 2) * (32 * 16);
     int it = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
       int g, tm, tn;
       if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
       const Problem pr = probs[g];
-      const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + tm * BM + q * 32 + lane];
-      const int fcol = P.eb[(int64_t)pr.b_slab * P.eb_rows + tn * BN + h * 32 + lane];  // lane = column
-      // this warp's share of Cin (zero where a row takes no addend), fetched
-      // while the tile's MMAs run
-      double cpre[2][16];
+      const int grow = tm * BM + q * 32 + lane;
+      const int col0 = tn * BN + c0;
+      const int ei = P.ea[(int64_t)pr.a_slab * P.ea_rows + grow];
+      const int fcol = P.eb[(int64_t)pr.b_slab * P.eb_rows + col0 + (lane & 15)];  // lane % 16 = column
+      const bool row_ok = grow < pr.m;
+      const bool row_cin = use_cin && pr.cin && row_ok && (grow < pr.nocin_r0 || grow >= pr.nocin_r1);
+      double cpre[16];
 #pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
-        const int col = tn * BN + h * 32 + pass * 16 + cc;
-#pragma unroll
-        for (int r2 = 0; r2 < 16; ++r2) {
-          const int grow = tm * BM + q * 32 + 2 * r2 + rr;
-          cpre[pass][r2] = (use_cin && pr.cin && grow < pr.m && col < pr.n &&
-                            (grow < pr.nocin_r0 || grow >= pr.nocin_r1))
-                               ? pr.cin[(int64_t)grow * pr.ldcin + col]
-                               : 0.0;
-        }
-      }
+      for (int c = 0; c < 16; ++c)
+        cpre[c] = (row_cin && col0 + c < pr.n) ? pr.cin[(int64_t)grow * pr.ldcin + col0 + c] : 0.0;
       const bool ok = mbar_wait(tfull, (uint32_t)it & 1u);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok || *(volatile int*)failed) {
@@ -342,24 +333,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         break;
       }
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-      const int npass = (tn * BN + h * 32 >= pr.n) ? 0 : (tn * BN + h * 32 + 16 >= pr.n ? 1 : 2);
-      if (npass == 0) {
+      double* orow = pr.out + (int64_t)grow * pr.ldo;
+      if (col0 >= pr.n) {  // columns past this problem (narrow updates): nothing to read
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty);
-      }
+      } else {
 #pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
-        if (pass < npass) {
-        const int c0 = h * 32 + pass * 16;
-#pragma unroll 1
-        for (int cq = 0; cq < 16; cq += 4) {
-          uint32_t acc[ND][4];
+        for (int cq = 0; cq < 16; cq += 2) {
+          uint32_t acc[ND][2];
 #pragma unroll
-          for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
+          for (int gg = 0; gg < ND; ++gg) tmem_ld2_async(trow + 64 * gg + c0 + cq, acc[gg]);
           tmem_wait();
+          if (cq == 14) {
+            // every accumulator of this tile has been read: the MMA warp may
+            // start the next tile
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty);
+          }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int c = pass * 16 + cq + u;  // column within this warp's half
+          for (int u = 0; u < 2; ++u) {
+            const int c = cq + u;
             const int fj = __shfl_sync(0xffffffffu, fcol, c);
             double v;
             if (ei >= kNonFinite || fj >= kNonFinite) {
@@ -370,29 +364,10 @@ __global__ void __launch_bounds__(THREADS, 1)
               for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
               v = combine(a, ei + fj - 61, neg_alpha);
             }
-            const int cl = cq + u;
-            T[lane * 16 + (cl ^ (lane & 15))] = v;
-          }
-        }
-        if (pass == npass - 1) {
-          // every accumulator of this tile is in registers or staged: the MMA
-          // warp may start the next tile
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(tempty);
-        }
-        __syncwarp();
-        const int col = tn * BN + c0 + cc;
-#pragma unroll
-        for (int r2 = 0; r2 < 16; ++r2) {
-          const int lr = 2 * r2 + rr;
-          const int grow = tm * BM + q * 32 + lr;
-          if (grow < pr.m && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) {
+            const int col = col0 + c;
             // the one FP64 instruction per entry: the Schur update's add
-            pr.out[(int64_t)grow * pr.ldo + col] = cpre[pass][r2] + T[lr * 16 + (cc ^ (lr & 15))];
+            if (row_ok && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) orow[col] = cpre[c] + v;
           }
-        }
-        __syncwarp();
         }
       }
       ++it;
@@ -496,7 +471,7 @@ int tile_m() { return BM; }
 int tile_n() { return BN; }
 int tile_k() { return BK; }
 int pack_rows() { return PR; }
-size_t smem_bytes() { return 2 * B_BYTES + ASTAGES * A_BYTES + NEPI * 32 * 16 * 8 + 1024 + 256; }
+size_t smem_bytes() { return 2 * B_BYTES + ASTAGES * A_BYTES + 1024 + 256; }
 
 cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kpad, __nv_bfloat16* dst, int* exps,
                         cudaStream_t s) {

@@ -112,6 +112,11 @@ __device__ __forceinline__ void tmem_ld4_async(uint32_t taddr, uint32_t (&r)[4])
                : "r"(taddr));
 }
 
+// Two consecutive accumulator columns of this warp's lanes, without the wait.
+__device__ __forceinline__ void tmem_ld2_async(uint32_t taddr, uint32_t (&r)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void split_bf16(float x, int S, __nv_bfloat16 (&s)[3]) {
