@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--blocks-per-step", type=int, default=8)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-check", action="store_true",
+                   help="skip the comparison of the last block with the plain FP64 path (fp64_tc)")
+    p.add_argument("--inverses", type=int, default=0,
+                   help="time this many independent pivoted inverses of order n (k = 1) in one batch")
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
     p.add_argument("--slices", type=int, default=3)
     p.add_argument("--refine", type=int, default=0)
@@ -242,6 +246,49 @@ def run_batched(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_inverses(args, rank, world, dist):
+    """The leaf pivot inverse alone: args.inverses independent matrices of
+    order n, uniform[-1,1) + (n/8) I, each inverted by the blocked pivoted
+    Gauss-Jordan kernels (a k = 1 request) in one batch per step."""
+    import numpy as np
+    import torch
+
+    import bri_inputs as bi
+    import paper_1612_00001_gb300 as mb
+    n = args.n
+    dt = torch.float64 if args.precision in ("fp64", "fp64_tc") else torch.float32
+    mats = [torch.tensor(bi.uniform_shift(n, s, shift=n / 8), dtype=dt, device="cuda") for s in range(args.inverses)]
+    work = [(M, 1, 0, 0) for M in mats]
+    for s in range(args.warmup):
+        outs, st, rep, rc = mb.batched_blocks(work, precision=args.precision)
+        assert rc == mb.OK, st
+    stream = torch.cuda.current_stream()
+    clocks = _clock_region(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = 0
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        outs, st, rep, rc = mb.batched_blocks(work, precision=args.precision)
+        ev[s][1].record(stream)
+        launches += rep["launches"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
+    inv = np.linalg.inv(bi.uniform_shift(n, 0, shift=n / 8))
+    err = float(np.linalg.norm(outs[0].double().cpu().numpy() - inv) / np.linalg.norm(inv))
+    line = {"metric": "pivoted b x b inverses/s", "value": args.inverses * args.steps / secs, "unit": "inverses/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(args),
+            "data": "synthetic",
+            "config": {"workload": f"{args.inverses} inverses of order {n}, uniform[-1,1)+(n/8)I ({args.precision})",
+                       "tflops_fp64_equivalent": 2.0 * n ** 3 * args.inverses * args.steps / secs / 1e12,
+                       "rel_err_vs_dense_inverse": err},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_backward(args, rank, world, dist):
     """Differentiation: L = sum(W * N_ij), W ~ N(0,1); a step is the forward
     block and dL/dM = -(X_i)^T W (Y_j)^T, the block row and column recomputed
@@ -322,6 +369,8 @@ def main():
     mb.build()
     if args.batched:
         return run_batched(args, rank, world, dist)
+    if args.inverses:
+        return run_inverses(args, rank, world, dist)
     if args.backward:
         return run_backward(args, rank, world, dist)
     n, k = args.n, args.k
@@ -389,7 +438,7 @@ def main():
     del inv_ref
     # the same block on the plain FP64 CUDA-core path: how far the tensor-core path is from it
     diff_fp64 = None
-    if args.precision == "fp64_tc":
+    if args.precision == "fp64_tc" and not args.no_fp64_check:
         i0, j0 = rank_blocks(k, rank, world, args.warmup + args.steps - 1, bps)[0]
         with mb.Context(M, k, precision="fp64") as c64:
             ref64 = c64.block(i0, j0).double().cpu().numpy()
