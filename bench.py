@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp32", "mixed", "fp64_tc"])
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--k", type=int, default=8)
-    p.add_argument("--blocks-per-step", type=int, default=8)
+    p.add_argument("--blocks-per-step", type=int, default=32)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-check", action="store_true",
@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
     p.add_argument("--slices", type=int, default=3)
     p.add_argument("--refine", type=int, default=0)
-    p.add_argument("--together", type=int, default=8,
+    p.add_argument("--together", type=int, default=32,
                    help="run each step's blocks as independent runs, this many executed together level by level "
                         "in grouped launches (0: one run after the other)")
     p.add_argument("--matrix", default="uniform", choices=["uniform", "haar", "spd"])
@@ -523,8 +523,12 @@ def main():
         e2e_steps = max(1, min(args.steps, 2))
         for s in range(e2e_steps):
             with mb.Context(mh, k, precision=args.precision, slices=args.slices, refine=args.refine) as hc:
-                for q, (i, j) in enumerate(block_list(k, s * bps, bps)):
-                    hc.block(i, j, out=houts[q])
+                ij = block_list(k, s * bps, bps)
+                if args.together:
+                    hc.blocks(ij, outs=houts, width=args.together)
+                else:
+                    for q, (i, j) in enumerate(ij):
+                        hc.block(i, j, out=houts[q])
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         es = dt.itemsize if hasattr(dt, "itemsize") else (8 if dt == torch.float64 else 4)
