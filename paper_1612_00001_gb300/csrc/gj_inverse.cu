@@ -115,7 +115,7 @@ __device__ __forceinline__ bool nonzero(float v) { return (__float_as_int(v) << 
 // two cluster barriers.
 template <typename TW>
 __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* __restrict__ descs, int p, int nb,
-                                                                 DevStatus* status) {
+                                                                 DevStatus* status, int active_only) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -129,8 +129,12 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   const int ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
   nb = min(nb, b - p);
   if (nb <= 0) return;
-  const int R = (b + CL - 1) / CL;
-  const int r0 = min(b, q * R), r1 = min(b, r0 + R);
+  // rows the panel eliminates: all of them, or (active_only) only the rows
+  // not yet used as pivots, [p, b) - the others' panel columns then follow
+  // from one product with the inverse of the pivot block (see run_batch_t)
+  const int row0 = active_only ? p : 0;
+  const int R = (b - row0 + CL - 1) / CL;
+  const int r0 = min(b, row0 + q * R), r1 = min(b, r0 + R);
   TW* P = (TW*)smem_raw;                // P[(i - r0) * ldp + t] is X[i][p + t]
   TW* prow = P + (size_t)R * ldp;       // pivot row before scaling (nb)
   TW* jrow = prow + ldp;                // old row j, for the owner of row r (nb)
@@ -198,13 +202,13 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
         d.perm[j] = r;
       }
     }
-    const int oj = j / R, orr = r / R;  // owners of rows j and r
+    const int oj = (j - row0) / R, orr = (r - row0) / R;  // owners of rows j and r
     // ---- read the pivot row (old row r) and, for the owner of r, old row j
     {
-      const TW* src = cluster.map_shared_rank(P, orr) + (size_t)(r - orr * R) * ldp;
+      const TW* src = cluster.map_shared_rank(P, orr) + (size_t)(r - row0 - orr * R) * ldp;
       for (int c = tid; c < nb; c += kPanelThreads) prow[c] = src[c];
       if (q == orr && r != j) {
-        const TW* sj = cluster.map_shared_rank(P, oj) + (size_t)(j - oj * R) * ldp;
+        const TW* sj = cluster.map_shared_rank(P, oj) + (size_t)(j - row0 - oj * R) * ldp;
         for (int c = tid; c < nb; c += kPanelThreads) jrow[c] = sj[c];
       }
     }
@@ -335,6 +339,34 @@ __global__ void gj_tc_setup_kernel(const InvDesc* __restrict__ descs, int count,
   pr[u] = q;
 }
 
+// Descriptors of the product that completes the panel columns J = [p, p + w)
+// of the rows already used as pivots, [0, p), which the panel kernel leaves
+// alone (active_only): in Gauss-Jordan form every non-pivot row of the panel
+// ends as -X_old[i, J] A^-1, with A^-1 = X[P, J] the pivot rows' panel
+// columns after the panel, so
+//     X[0:p, J] = -X[0:p, J] X[p:p+w, J]     (one digit product, K = w).
+__global__ void gj_tc_done_setup_kernel(const InvDesc* __restrict__ descs, int count, int p, int nb,
+                                        oz::PackDesc* __restrict__ pa, oz::PackDesc* __restrict__ pb,
+                                        oz::Problem* __restrict__ pr) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= count) return;
+  const InvDesc d = descs[u];
+  const int b = d.b;
+  const int w = min(nb, b - p);
+  const bool live = p > 0 && w > 0;
+  double* X = (double*)d.work;
+  pa[u] = oz::PackDesc{X + (live ? p : 0), b, live ? p : 0, live ? w : 0, 0, u};
+  pb[u] = oz::PackDesc{X + (live ? (int64_t)p * b + p : 0), b, live ? w : 0, live ? w : 0, 1, u};
+  oz::Problem q{};
+  q.a_slab = q.b_slab = u;
+  q.cin = nullptr;
+  q.out = X + (live ? p : 0);
+  q.ldcin = q.ldo = b;
+  q.m = live ? p : 0;
+  q.n = live ? w : 0;
+  pr[u] = q;
+}
+
 struct TcLayout {
   int rpa, rpb;
   size_t da, db, ea, eb, pa, pb, pr, total;
@@ -440,14 +472,14 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cfg.numAttrs = 1;
     const bool timed = tm && tm->n + 2 <= tm->cap;
     if (timed) cudaEventRecord(tm->ev[tm->n], s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status, tc && w < b ? 1 : 0);
     if (e != cudaSuccess) return e;
     if (timed) {
       cudaEventRecord(tm->ev[tm->n + 1], s);
       tm->n += 2;
     }
     ++nl;
-    if (w < b && tc) {  // the trailing update on the tensor cores
+    if (w < b && tc) {  // the rows done before this panel, then the trailing update, on the tensor cores
       const TcLayout T = tc_layout(b, count);
       char* base = (char*)tc->scratch;
       auto* pa = (oz::PackDesc*)(base + T.pa);
@@ -457,27 +489,35 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       auto* db = (__nv_bfloat16*)(base + T.db);
       int* ea = (int*)(base + T.ea);
       int* eb = (int*)(base + T.eb);
-      gj_tc_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
-      e = oz::launch_pack(pa, count, T.rpa, oz::tile_k(), da, ea, s);
-      if (e != cudaSuccess) return e;
-      e = oz::launch_pack(pb, count, T.rpb, oz::tile_k(), db, eb, s);
-      if (e != cudaSuccess) return e;
       oz::Params Q{};
       Q.kpad = oz::tile_k();
       Q.kb0 = 0;
       Q.nkb = 1;
       Q.tiles_m = T.rpa / oz::tile_m();
       Q.tiles_n = T.rpb / oz::tile_n();
-      Q.alpha = 1.0;
-      Q.beta = 1.0;
       Q.ea = ea;
       Q.eb = eb;
       Q.ea_rows = T.rpa;
       Q.eb_rows = T.rpb;
       Q.err = tc->err;
-      e = oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
-      if (e != cudaSuccess) return e;
-      nl += 4;
+      auto product = [&](double alpha, double beta) -> cudaError_t {
+        cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, oz::tile_k(), da, ea, s);
+        if (e2 != cudaSuccess) return e2;
+        e2 = oz::launch_pack(pb, count, T.rpb, oz::tile_k(), db, eb, s);
+        if (e2 != cudaSuccess) return e2;
+        Q.alpha = alpha;
+        Q.beta = beta;
+        nl += 3;
+        return oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
+      };
+      if (p > 0) {
+        gj_tc_done_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
+        ++nl;
+        if ((e = product(-1.0, 0.0)) != cudaSuccess) return e;
+      }
+      gj_tc_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
+      ++nl;
+      if ((e = product(1.0, 1.0)) != cudaSuccess) return e;
     } else if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
       using Cfg = TileCfg<TW>;
       dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);
@@ -517,8 +557,11 @@ void inv_flop_split(int b, int wtype, bool tc, double* panel_flops, double* upda
   double pf = 0, uf = 0;
   for (int p = 0; p < b; p += nb) {
     const double w = std::min(nb, b - p);
-    pf += 2.0 * b * w * w;
-    uf += 2.0 * b * w * (b - w);
+    // with tensor-core updates a panel eliminates only the rows not yet used
+    // as pivots; the others' panel columns come from a product
+    const double rows = (tc && w < b) ? b - p : b;
+    pf += 2.0 * rows * w * w;
+    uf += 2.0 * b * w * (b - w) + 2.0 * (b - rows) * w * w;
   }
   *panel_flops = pf;
   *update_flops = uf;
