@@ -368,7 +368,7 @@ __global__ void gj_tc_done_setup_kernel(const InvDesc* __restrict__ descs, int c
 }
 
 struct TcLayout {
-  int rpa, rpb;
+  int rpa, rpb, kpad;
   size_t da, db, ea, eb, pa, pb, pr, total;
 };
 
@@ -377,7 +377,10 @@ TcLayout tc_layout(int bmax, int count) {
   TcLayout L;
   L.rpa = (bmax + oz::tile_m() - 1) / oz::tile_m() * oz::tile_m();
   L.rpb = (bmax + oz::tile_n() - 1) / oz::tile_n() * oz::tile_n();
-  const size_t K = oz::tile_k();
+  // the inner length of the updates is the panel width
+  const int nb = inv_panel_width(bmax, F64, true);
+  L.kpad = (std::min(nb, bmax) + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
+  const size_t K = L.kpad;
   size_t o = 0;
   L.da = o;
   o += al((size_t)count * oz::kDigits * L.rpa * K * 2);
@@ -490,9 +493,9 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       int* ea = (int*)(base + T.ea);
       int* eb = (int*)(base + T.eb);
       oz::Params Q{};
-      Q.kpad = oz::tile_k();
+      Q.kpad = T.kpad;
       Q.kb0 = 0;
-      Q.nkb = 1;
+      Q.nkb = T.kpad / oz::tile_k();  // at most kMaxKBlocks: panels are far narrower than 512
       Q.tiles_m = T.rpa / oz::tile_m();
       Q.tiles_n = T.rpb / oz::tile_n();
       Q.ea = ea;
@@ -501,9 +504,9 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       Q.eb_rows = T.rpb;
       Q.err = tc->err;
       auto product = [&](double alpha, double beta) -> cudaError_t {
-        cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, oz::tile_k(), da, ea, s);
+        cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, T.kpad, da, ea, s);
         if (e2 != cudaSuccess) return e2;
-        e2 = oz::launch_pack(pb, count, T.rpb, oz::tile_k(), db, eb, s);
+        e2 = oz::launch_pack(pb, count, T.rpb, T.kpad, db, eb, s);
         if (e2 != cudaSuccess) return e2;
         Q.alpha = alpha;
         Q.beta = beta;
