@@ -63,7 +63,10 @@ constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int ASTAGES = 4;
 constexpr int NEPI = 16;                  // epilogue warps: 4 lane quarters x 4 column quarters
 constexpr int THREADS = 64 + 32 * NEPI;   // producer warp, MMA warp, epilogue warps
-constexpr int PR = 32;                                  // slab rows per pack CTA
+constexpr int PR = 16;                                  // slab rows per pack CTA
+constexpr int PKC = 512;                                // K entries a pack CTA stages at a time
+constexpr int PMAXR = 64;                               // most slab rows per pack CTA
+constexpr int kPackSmemMax = 68 * 1024;                 // bound on rpc * (kc + 1) doubles
 constexpr uint32_t A_BYTES = BM * BK * 2;               // one digit of the A tile: 16 KB
 constexpr uint32_t BQ_BYTES = BN * BK * 2;              // one digit of the B tile: 8 KB
 constexpr uint32_t B_BYTES = ND * BQ_BYTES;             // all digits of the B tile: 64 KB
@@ -380,86 +383,111 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// One CTA per 32 slab rows: pass 1 finds each row's largest magnitude (the
-// bit patterns of |x| order like the values; Inf and NaN sort above every
-// finite value), pass 2 writes the digits.  The source is staged through a
-// 32 x 64 shared tile so that both orientations read it contiguously.
+// One CTA per rpc slab rows (64 for K <= 128, down to 16 for K >= 512: about
+// 66 KB staged either way).  The source rows (or columns, transposed) are
+// staged in shared memory up to 512 entries of K at a time: a slab of K <= 512
+// is read from global memory once, all its loads in flight together; longer
+// K takes two passes over chunks.  Pass 1 finds each row's largest magnitude
+// (the bit patterns of |x| order like the values; Inf and NaN sort above every
+// finite value), pass 2 writes the digits as pairs of BF16 (128 contiguous
+// bytes per warp instruction).
 __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
-                                                       __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
-  __shared__ double S[PR][65];
-  __shared__ int sE[PR];
+                                                       int rpc, __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
+  extern __shared__ double S[];  // [rpc][kc + 1]
+  __shared__ int sE[PMAXR];
+  __shared__ unsigned long long smx[PMAXR];  // running row maxima (bit patterns)
   const PackDesc d = descs[blockIdx.y];
-  const int r0 = blockIdx.x * PR;
+  const int r0 = blockIdx.x * rpc;
+  const int rw = rpc / 8;  // rows per warp
   const int R = d.transpose ? d.cols : d.rows, KD = d.transpose ? d.rows : d.cols;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  auto load_tile = [&](int k0) {
+  const int kc = kpad < PKC ? kpad : PKC;  // staged chunk of K
+  const int lds = kc + 1;
+  const int chunks = (kpad + kc - 1) / kc;
+  auto load_chunk = [&](int k0) {
+    const int kw = min(kc, kpad - k0);
     if (!d.transpose) {
-#pragma unroll
-      for (int it = 0; it < 8; ++it) {
-        const int rr = (tid >> 6) + 4 * it, kk = tid & 63;
-        const int r = r0 + rr, k = k0 + kk;
-        S[rr][kk] = (r < R && k < KD) ? d.src[(int64_t)r * d.ld + k] : 0.0;
+      // thread (row group, column): for kw < 256 several rows go out at once
+      const int tk = kw < 256 ? kw : 256;  // threads per row
+      const int rg = tid / tk, kk0 = tid - rg * tk, rstep = 256 / tk;
+      if (rg < rstep) {
+#pragma unroll 4
+        for (int rr = rg; rr < rpc; rr += rstep) {
+          const int r = r0 + rr;
+          for (int kk = kk0; kk < kw; kk += tk) {
+            const int k = k0 + kk;
+            S[rr * lds + kk] = (r < R && k < KD) ? d.src[(int64_t)r * d.ld + k] : 0.0;
+          }
+        }
       }
     } else {
-#pragma unroll
-      for (int it = 0; it < 8; ++it) {
-        const int rr = tid & 31, kk = (tid >> 5) + 8 * it;
-        const int r = r0 + rr, k = k0 + kk;
-        S[rr][kk] = (r < R && k < KD) ? d.src[(int64_t)k * d.ld + r] : 0.0;
+      const int rr = tid & (rpc - 1);
+      const int r = r0 + rr;
+#pragma unroll 4
+      for (int kk = tid / rpc; kk < kw; kk += 256 / rpc) {
+        const int k = k0 + kk;
+        S[rr * lds + kk] = (r < R && k < KD) ? d.src[(int64_t)k * d.ld + r] : 0.0;
       }
     }
   };
-  unsigned long long mx[4] = {0, 0, 0, 0};
-  if (r0 < R) {
-    for (int k0 = 0; k0 < KD; k0 += 64) {
-      __syncthreads();
-      load_tile(k0);
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int rr = warp + 8 * j;
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const unsigned long long bits =
-              (unsigned long long)__double_as_longlong(S[rr][2 * lane + hh]) & 0x7FFFFFFFFFFFFFFFull;
-          mx[j] = bits > mx[j] ? bits : mx[j];
-        }
+  // ---- pass 1: largest magnitude of each row (warp w: rows w rw .. w rw + rw - 1)
+  for (int c = 0; c < chunks; ++c) {
+    const int k0 = c * kc, kw = min(kc, kpad - k0);
+    if (r0 >= R) break;
+    if (c > 0) __syncthreads();
+    load_chunk(k0);
+    __syncthreads();
+    for (int h = 0; h < rw; ++h) {
+      const int rr = warp * rw + h;
+      const double* row = S + rr * lds;
+      unsigned long long mx = 0;
+      for (int kk = lane; kk < kw; kk += 32) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(row[kk]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = bits > mx ? bits : mx;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+      }
+      if (lane == 0) smx[rr] = (c > 0 && smx[rr] > mx) ? smx[rr] : mx;
     }
   }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx[j], o);
-      mx[j] = y > mx[j] ? y : mx[j];
-    }
-    if (lane == 0) {
-      const int rr = warp + 8 * j;
-      const int ex = (int)(mx[j] >> 52);
-      // 2^E > max|x|: E = ex - 1022 for a normal maximum
-      const int E = mx[j] == 0 ? 0 : (ex == 0x7ff ? kNonFinite : (ex == 0 ? -1022 : ex - 1022));
-      sE[rr] = E;
-      exps[(int64_t)d.slab * rows_pad + r0 + rr] = E;
-    }
+  __syncthreads();
+  for (int rr = tid; rr < rpc; rr += 256) {
+    const unsigned long long m = r0 < R ? smx[rr] : 0ull;
+    const int ex = (int)(m >> 52);
+    // 2^E > max|x|: E = ex - 1022 for a normal maximum
+    const int E = m == 0 ? 0 : (ex == 0x7ff ? kNonFinite : (ex == 0 ? -1022 : ex - 1022));
+    sE[rr] = E;
+    exps[(int64_t)d.slab * rows_pad + r0 + rr] = E;
   }
-  for (int k0 = 0; k0 < kpad; k0 += 64) {
+  // ---- pass 2: digits (a single chunk is still staged and is not read again)
+  for (int c = 0; c < chunks; ++c) {
+    const int k0 = c * kc, kw = min(kc, kpad - k0);
     __syncthreads();
-    load_tile(k0);
-    __syncthreads();
+    if (chunks > 1 || r0 >= R) {
+      load_chunk(k0);
+      __syncthreads();
+    }
 #pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      const int rr = warp + 8 * j;
+    for (int h = 0; h < rw; ++h) {
+      const int rr = warp * rw + h;
       const int E = sE[rr];
-      int d0[ND], d1[ND];
-      digits8(S[rr][2 * lane], E, d0);
-      digits8(S[rr][2 * lane + 1], E, d1);
+      const double* row = S + rr * lds;
+      __nv_bfloat16* out = dst + ((int64_t)d.slab * ND * rows_pad + r0 + rr) * kpad + k0;
+#pragma unroll 1
+      for (int kk = 2 * lane; kk < kw; kk += 64) {
+        int d0[ND], d1[ND];
+        digits8(row[kk], E, d0);
+        digits8(row[kk + 1], E, d1);
 #pragma unroll
-      for (int p = 0; p < ND; ++p) {
-        __nv_bfloat162 v;
-        v.x = __float2bfloat16_rn((float)d0[p]);
-        v.y = __float2bfloat16_rn((float)d1[p]);
-        *(__nv_bfloat162*)&dst[(((int64_t)d.slab * ND + p) * rows_pad + r0 + rr) * kpad + k0 + 2 * lane] = v;
+        for (int p = 0; p < ND; ++p) {
+          __nv_bfloat162 v;
+          v.x = __float2bfloat16_rn((float)d0[p]);
+          v.y = __float2bfloat16_rn((float)d1[p]);
+          *(__nv_bfloat162*)&out[(int64_t)p * rows_pad * kpad + kk] = v;
+        }
       }
     }
   }
@@ -477,8 +505,21 @@ cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kp
                         cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (rows_pad % PR || kpad % BK || ((uintptr_t)dst & 3)) return cudaErrorInvalidValue;
-  dim3 grid(rows_pad / PR, count);
-  oz_pack_kernel<<<grid, 256, 0, s>>>(d_descs, rows_pad, kpad, dst, exps);
+  static bool attr = false;
+  if (!attr) {
+    // the largest stage: 64 rows x 129 or 16 rows x 513 entries, about 66 KB
+    cudaError_t e = cudaFuncSetAttribute(oz_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPackSmemMax);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int kc = kpad < PKC ? kpad : PKC;
+  // rows per CTA: about 66 KB of staged entries, 16..64 rows (rows_pad is a multiple of 64)
+  int rpc = PR * (PKC / kc);
+  rpc = rpc > PMAXR ? PMAXR : rpc;
+  if (rows_pad % rpc) rpc = PR;
+  if ((size_t)rpc * (kc + 1) * sizeof(double) > (size_t)kPackSmemMax) return cudaErrorInvalidValue;
+  dim3 grid(rows_pad / rpc, count);
+  oz_pack_kernel<<<grid, 256, rpc * (kc + 1) * sizeof(double), s>>>(d_descs, rows_pad, kpad, rpc, dst, exps);
   return cudaGetLastError();
 }
 
