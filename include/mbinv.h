@@ -77,7 +77,8 @@ typedef struct {
     size_t device_cap_bytes;    /* bound on the library's device memory
                                    (workspace plus its own copy of M);
                                    0 = no bound */
-    int refine_steps;           /* MIXED_BF16 only: 0 or 1 */
+    int refine_steps;           /* 0 or 1: one two-sided refinement step
+                                   (see mbinv_block), any precision */
     int bf16_slices;            /* MIXED_BF16 only: operands split into
                                    1, 2 or 3 BF16 slices (1, 3 or 6
                                    products) */
@@ -159,9 +160,13 @@ mbinv_status mbinv_create(mbinv_ctx **out, int64_t n, int64_t k, int dtype, cons
  * (i, k-1), [[M, 0], [C', I]] for (k-1, j), B' and C'^T uniform in [-1, 1)
  * drawn by SplitMix64 from pad_seed; the top-left n x n block of each
  * bordered inverse is M^-1.  report may be NULL.
- * MIXED_BF16 with refine_steps = 1 also computes block row i and block column
- * j of the inverse with the same sweep and returns
- * X_i E_j + (E_i^T - X_i M) Y_j, the residual taken in FP64. */
+ * With refine_steps = 1 the call also computes block row i (X_i) and block
+ * column j (Y_j) of the inverse with the same sweep (kept in FP32 on the
+ * FP32-valued paths, FP64 on FP64 and FP64_TC) and returns
+ * X_i E_j + (E_i^T - X_i M) Y_j, the residual and the correction taken in
+ * FP64: the result's error is -dX M dY, the product of the sweep's errors
+ * (the method is not in the paper).  MBINV_ENOTCONV when the residual's
+ * scaled norm is not below 1. */
 mbinv_status mbinv_block(mbinv_ctx *ctx, int64_t i, int64_t j, void *out, int64_t ldo, mbinv_report *report);
 
 /* Several blocks of M^-1, each by its own run of the recursion (Sec. 3.1-3.2,
@@ -170,7 +175,8 @@ mbinv_status mbinv_block(mbinv_ctx *ctx, int64_t i, int64_t j, void *out, int64_
  * Sec. 8).  ij holds count pairs (i, j); outs[t] (host or device, M's dtype)
  * receives block (ij[2t], ij[2t+1]) with leading dimension ldos[t].  width
  * bounds how many runs go together (0 = 8), and the cap may lower it.  With
- * MIXED_BF16 and refine_steps = 1 every block is refined as in mbinv_block. */
+ * refine_steps = 1 every block is refined as in mbinv_block, each needed
+ * block row and column computed once. */
 mbinv_status mbinv_blocks(mbinv_ctx *ctx, int64_t count, const int64_t *ij, void *const *outs, const int64_t *ldos,
                           int width, mbinv_report *report);
 

@@ -437,8 +437,9 @@ mbinv_status row_or_col(mbinv_ctx* c, int64_t t, bool row, void* out, int64_t ld
   return blocks_to(c, ij, outs, ldos, (int)c->k, rep);
 }
 
-// Mixed path with one two-sided refinement step (refined_blocks below):
-//   X_i = block row i, Y_j = block column j of M^-1 from the mixed sweep,
+// One two-sided refinement step (refined_blocks below), on any path:
+//   X_i = block row i, Y_j = block column j of M^-1 from the sweep (kept in
+//         FP32 on the FP32-valued paths, FP64 on FP64 and FP64_TC),
 //   R   = E_i^T - X_i M                      (FP64 accumulation)
 //   N_ij <- X_i E_j + R Y_j                  (FP64)
 // With dX, dY the errors of X_i, Y_j the result differs from N_ij by
@@ -492,12 +493,15 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
     rows.emplace(p.first, (int)rows.size());
     cols.emplace(p.second, (int)cols.size());
   }
+  // the sweeps' values in their own precision: FP64 on the FP64-valued paths
+  const int xt = (c->opt.precision == MBINV_FP64 || c->opt.precision == MBINV_FP64_TC) ? F64 : F32;
+  const size_t xs = dtype_size(xt);
   const size_t rsz = (size_t)b * n, csz = (size_t)n * b;
-  CU(c->rowbuf.ensure(rows.size() * rsz * 4 + 256));
-  CU(c->colbuf.ensure(cols.size() * csz * 4 + 256));
+  CU(c->rowbuf.ensure(rows.size() * rsz * xs + 256));
+  CU(c->colbuf.ensure(cols.size() * csz * xs + 256));
   CU(c->resid.ensure(rows.size() * rsz * 8 + v.size() * (size_t)b * b * 8 + 512));
-  float* X = (float*)c->rowbuf.p;  // X_i at X + rows[i] * rsz, leading dimension n
-  float* Y = (float*)c->colbuf.p;  // Y_j at Y + cols[j] * csz, leading dimension b
+  char* X = (char*)c->rowbuf.p;  // X_i at X + (rows[i] * rsz) * xs, leading dimension n
+  char* Y = (char*)c->colbuf.p;  // Y_j at Y + (cols[j] * csz) * xs, leading dimension b
   // every block of the needed rows and columns, each computed once
   std::vector<std::pair<int64_t, int64_t>> ij;
   std::vector<void*> dst;
@@ -506,7 +510,7 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
   for (auto& r : rows)
     for (int64_t q = 0; q < k; ++q) {
       ij.emplace_back(r.first, q);
-      dst.push_back(X + r.second * rsz + q * b);
+      dst.push_back(X + (r.second * rsz + q * b) * xs);
       ld.push_back(n);
       if (cols.count(q)) copies.emplace_back(r.first, q);
     }
@@ -514,18 +518,18 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
     for (int64_t q = 0; q < k; ++q) {
       if (rows.count(q)) continue;
       ij.emplace_back(q, cc.first);
-      dst.push_back(Y + cc.second * csz + q * b * b);
+      dst.push_back(Y + (cc.second * csz + q * b * b) * xs);
       ld.push_back(b);
     }
   const int saved_dtype = c->dtype;
-  c->dtype = F32;  // the sweeps write FP32 blocks
+  c->dtype = xt;  // the sweeps write blocks in the working type
   mbinv_status s = blocks_to(c, ij, dst, ld, kDefaultWidth, rep);
   c->dtype = saved_dtype;
   if (s != MBINV_OK) return s;
   for (auto& p : copies) {
     const int64_t bi = block_extent(c, p.first), bj = block_extent(c, p.second);
-    CU(cudaMemcpy2DAsync(Y + cols[p.second] * csz + p.first * b * b, (size_t)b * 4,
-                         X + rows[p.first] * rsz + p.second * b, (size_t)n * 4, (size_t)bj * 4, (size_t)bi,
+    CU(cudaMemcpy2DAsync(Y + (cols[p.second] * csz + p.first * b * b) * xs, (size_t)b * xs,
+                         X + (rows[p.first] * rsz + p.second * b) * xs, (size_t)n * xs, (size_t)bj * xs, (size_t)bi,
                          cudaMemcpyDeviceToDevice, c->stream));
   }
   // R_i = -X_i M + E_i^T
@@ -533,9 +537,9 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
   double* Nb = R + rows.size() * rsz;
   std::vector<GemmDesc> ds;
   for (auto& r : rows)
-    ds.push_back(gdesc(X + r.second * rsz, n, c->dM, c->ldm, nullptr, 0, R + r.second * rsz, n,
+    ds.push_back(gdesc(X + r.second * rsz * xs, n, c->dM, c->ldm, nullptr, 0, R + r.second * rsz, n,
                        (int)block_extent(c, r.first), (int)n, (int)n, -1.0, 0.0));
-  s = gemm_list(c, c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64, ds);
+  s = gemm_list(c, xt == F64 ? G_F64 : (c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64), ds);
   if (s != MBINV_OK) return s;
   double rmax = 0;
   for (auto& r : rows) {
@@ -558,13 +562,18 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
     const int64_t i = v[t].first, j = v[t].second;
     const int64_t bi = block_extent(c, i), bj = block_extent(c, j);
     double* Nt = Nb + t * (size_t)b * b;
-    convert_kernel<float, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
-        X + rows[i] * rsz + j * b, n, Nt, bj, bi, bj);
+    const char* Xij = X + (rows[i] * rsz + j * b) * xs;
+    if (xt == F64)
+      convert_kernel<double, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+          (const double*)Xij, n, Nt, bj, bi, bj);
+    else
+      convert_kernel<float, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+          (const float*)Xij, n, Nt, bj, bi, bj);
     CU(cudaGetLastError());
-    ds.push_back(gdesc(R + rows[i] * rsz, n, Y + cols[j] * csz, b, Nt, bj, Nt, bj, (int)bi, (int)bj, (int)n, 1.0,
-                       1.0));
+    ds.push_back(gdesc(R + rows[i] * rsz, n, Y + cols[j] * csz * xs, b, Nt, bj, Nt, bj, (int)bi, (int)bj, (int)n,
+                       1.0, 1.0));
   }
-  s = gemm_list(c, G_F64F32_F64, ds);
+  s = gemm_list(c, xt == F64 ? G_F64 : G_F64F32_F64, ds);
   if (s != MBINV_OK) return s;
   const size_t es = dtype_size(c->dtype);
   for (size_t t = 0; t < v.size(); ++t) {
@@ -742,7 +751,7 @@ static mbinv_status mbinv_block_impl(mbinv_ctx* c, int64_t i, int64_t j, void* o
   start_report(rep);
   auto t0 = std::chrono::steady_clock::now();
   mbinv_status s;
-  if (c->opt.precision == MBINV_MIXED_BF16 && c->opt.refine_steps > 0 && !c->in_sweep) {
+  if (c->opt.refine_steps > 0 && !c->in_sweep) {
     c->in_sweep = true;
     s = refined_blocks(c, {{i, j}}, {out}, {ldo}, rep);
     c->in_sweep = false;
@@ -769,7 +778,7 @@ static mbinv_status mbinv_blocks_impl(mbinv_ctx* c, int64_t count, const int64_t
   start_report(rep);
   auto t0 = std::chrono::steady_clock::now();
   mbinv_status s = MBINV_OK;
-  if (c->opt.precision == MBINV_MIXED_BF16 && c->opt.refine_steps > 0) {
+  if (c->opt.refine_steps > 0) {
     c->in_sweep = true;
     s = refined_blocks(c, v, o, l, rep);
     c->in_sweep = false;
@@ -900,7 +909,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     if (opt->struct_size != sizeof(mbinv_options)) return MBINV_EINVAL;
     o = *opt;
   }
-  if (o.precision == MBINV_MIXED_BF16 && o.refine_steps > 0) return MBINV_ENOTSUP;
+  if (o.refine_steps > 0) return MBINV_ENOTSUP;
   // one context per problem (its device matrix and plan), all run together
   std::vector<mbinv_ctx*> ctxs((size_t)count, nullptr);
   mbinv_status first = MBINV_OK;
