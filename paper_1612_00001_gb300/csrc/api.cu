@@ -23,6 +23,7 @@
 #include "../../include/mbinv.h"
 #include "exec.h"
 #include "mbinv_internal.h"
+#include "ozaki.h"
 
 using namespace mbinv;
 
@@ -462,6 +463,96 @@ mbinv_status gemm_list(mbinv_ctx* c, int combo, std::vector<GemmDesc>& ds) {
   return MBINV_OK;
 }
 
+// C = beta Cin + alpha A B for every op (FP64, row-major; alpha +-1, beta 0 or
+// 1; one inner length k for all) as FP64-accurate digit products on the
+// tensor cores: each distinct A and B is packed once, then one grouped launch
+// per K chunk of 512.  The sweep's digit buffers are reused: the sweep is over.
+struct OzOp {
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  const double* cin;
+  int64_t ldcin;
+  double* C;
+  int64_t ldc;
+  int m, n;
+};
+
+mbinv_status oz_list(mbinv_ctx* c, const std::vector<OzOp>& ops, int k, double alpha, double beta) {
+  if (ops.empty()) return MBINV_OK;
+  auto up = [](size_t x, size_t q) { return (x + q - 1) / q * q; };
+  std::map<const double*, int> aslab, bslab;
+  std::vector<oz::PackDesc> pa, pb;
+  int mmax = 1, nmax = 1;
+  for (const OzOp& o : ops) {
+    mmax = std::max(mmax, o.m);
+    nmax = std::max(nmax, o.n);
+    if (aslab.emplace(o.A, (int)pa.size()).second) pa.push_back(oz::PackDesc{o.A, o.lda, o.m, k, 0, (int)pa.size()});
+    if (bslab.emplace(o.B, (int)pb.size()).second) pb.push_back(oz::PackDesc{o.B, o.ldb, k, o.n, 1, (int)pb.size()});
+  }
+  const int rpa = (int)up(mmax, oz::tile_m()), rpb = (int)up(nmax, oz::tile_n()), kpad = (int)up(k, oz::tile_k());
+  const int nkb = kpad / oz::tile_k(), nchunk = (nkb + oz::kMaxKBlocks - 1) / oz::kMaxKBlocks;
+  Env& E = c->env;
+  CU(E.apk.ensure(pa.size() * (size_t)oz::kDigits * rpa * kpad * 2));
+  CU(E.bpk.ensure(pb.size() * (size_t)oz::kDigits * rpb * kpad * 2));
+  CU(E.oexp.ensure((pa.size() * rpa + pb.size() * rpb) * 4 + 256));
+  CU(E.tcerr.ensure(256));
+  int* ea = (int*)E.oexp.p;
+  int* eb = ea + pa.size() * rpa;
+  // descriptors: A packs, B packs, then the problems of every K chunk
+  const size_t oa = 0, ob = up(pa.size() * sizeof(oz::PackDesc), 256),
+               op = ob + up(pb.size() * sizeof(oz::PackDesc), 256), per = up(ops.size() * sizeof(oz::Problem), 256);
+  std::vector<char> h(op + nchunk * per);
+  std::memcpy(h.data() + oa, pa.data(), pa.size() * sizeof(oz::PackDesc));
+  std::memcpy(h.data() + ob, pb.data(), pb.size() * sizeof(oz::PackDesc));
+  for (int ch = 0; ch < nchunk; ++ch) {
+    oz::Problem* pr = (oz::Problem*)(h.data() + op + ch * per);
+    for (size_t t = 0; t < ops.size(); ++t) {
+      const OzOp& o = ops[t];
+      oz::Problem q{};
+      q.a_slab = aslab[o.A];
+      q.b_slab = bslab[o.B];
+      q.cin = ch == 0 ? o.cin : o.C;  // later chunks add to what the first wrote
+      q.ldcin = ch == 0 ? o.ldcin : o.ldc;
+      q.out = o.C;
+      q.ldo = o.ldc;
+      q.m = o.m;
+      q.n = o.n;
+      pr[t] = q;
+    }
+  }
+  CU(c->gemmdesc.ensure(h.size() + 256));
+  char* d = (char*)c->gemmdesc.p;
+  CU(cudaMemcpyAsync(d, h.data(), h.size(), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), c->stream));
+  CU(oz::launch_pack((const oz::PackDesc*)(d + oa), (int)pa.size(), rpa, kpad, (__nv_bfloat16*)E.apk.p, ea,
+                     c->stream));
+  CU(oz::launch_pack((const oz::PackDesc*)(d + ob), (int)pb.size(), rpb, kpad, (__nv_bfloat16*)E.bpk.p, eb,
+                     c->stream));
+  oz::Params Q{};
+  Q.kpad = kpad;
+  Q.tiles_m = rpa / oz::tile_m();
+  Q.tiles_n = rpb / oz::tile_n();
+  Q.alpha = alpha;
+  Q.ea = ea;
+  Q.eb = eb;
+  Q.ea_rows = rpa;
+  Q.eb_rows = rpb;
+  Q.err = (int*)E.tcerr.p;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    Q.kb0 = ch * oz::kMaxKBlocks;
+    Q.nkb = std::min(oz::kMaxKBlocks, nkb - Q.kb0);
+    Q.beta = ch == 0 ? beta : 1.0;
+    CU(oz::launch_gemm((const __nv_bfloat16*)E.apk.p, (int)pa.size(), rpa, (const __nv_bfloat16*)E.bpk.p,
+                       (int)pb.size(), rpb, Q, (const oz::Problem*)(d + op + ch * per), (int)ops.size(), c->stream));
+  }
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return herr ? MBINV_ETIMEOUT : MBINV_OK;
+}
+
 GemmDesc gdesc(const void* A, int64_t lda, const void* B, int64_t ldb, const void* Cin, int64_t ldcin, void* C,
                int64_t ldc, int m, int n, int k, double alpha, double beta) {
   GemmDesc d{};
@@ -532,14 +623,20 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
                          X + (rows[p.first] * rsz + p.second * b) * xs, (size_t)n * xs, (size_t)bj * xs, (size_t)bi,
                          cudaMemcpyDeviceToDevice, c->stream));
   }
-  // R_i = -X_i M + E_i^T
+  // R_i = -X_i M + E_i^T (FP64_TC: as digit products on the tensor cores)
   double* R = (double*)c->resid.p;
   double* Nb = R + rows.size() * rsz;
+  const bool tcr = c->opt.precision == MBINV_FP64_TC && c->mdt == F64;
   std::vector<GemmDesc> ds;
-  for (auto& r : rows)
+  std::vector<OzOp> zs;
+  for (auto& r : rows) {
     ds.push_back(gdesc(X + r.second * rsz * xs, n, c->dM, c->ldm, nullptr, 0, R + r.second * rsz, n,
                        (int)block_extent(c, r.first), (int)n, (int)n, -1.0, 0.0));
-  s = gemm_list(c, xt == F64 ? G_F64 : (c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64), ds);
+    zs.push_back(OzOp{(const double*)(X + r.second * rsz * xs), n, (const double*)c->dM, c->ldm, nullptr, 0,
+                      R + r.second * rsz, n, (int)block_extent(c, r.first), (int)n});
+  }
+  s = tcr ? oz_list(c, zs, (int)n, -1.0, 0.0)
+          : gemm_list(c, xt == F64 ? G_F64 : (c->mdt == F64 ? G_F32F64_F64 : G_F32IN_F64), ds);
   if (s != MBINV_OK) return s;
   double rmax = 0;
   for (auto& r : rows) {
@@ -558,6 +655,7 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
   }
   // N_ij = X_i E_j + R_i Y_j
   ds.clear();
+  zs.clear();
   for (size_t t = 0; t < v.size(); ++t) {
     const int64_t i = v[t].first, j = v[t].second;
     const int64_t bi = block_extent(c, i), bj = block_extent(c, j);
@@ -572,8 +670,10 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
     CU(cudaGetLastError());
     ds.push_back(gdesc(R + rows[i] * rsz, n, Y + cols[j] * csz * xs, b, Nt, bj, Nt, bj, (int)bi, (int)bj, (int)n,
                        1.0, 1.0));
+    zs.push_back(OzOp{R + rows[i] * rsz, n, (const double*)(Y + cols[j] * csz * xs), b, Nt, bj, Nt, bj, (int)bi,
+                      (int)bj});
   }
-  s = gemm_list(c, xt == F64 ? G_F64 : G_F64F32_F64, ds);
+  s = tcr ? oz_list(c, zs, (int)n, 1.0, 1.0) : gemm_list(c, xt == F64 ? G_F64 : G_F64F32_F64, ds);
   if (s != MBINV_OK) return s;
   const size_t es = dtype_size(c->dtype);
   for (size_t t = 0; t < v.size(); ++t) {
