@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp32", "mixed", "fp64_tc"])
     p.add_argument("--n", type=int, default=4096)
     p.add_argument("--k", type=int, default=8)
-    p.add_argument("--blocks-per-step", type=int, default=32)
+    p.add_argument("--blocks-per-step", type=int, default=64)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-check", action="store_true",
@@ -55,7 +55,9 @@ def parse():
                    help="time this many independent pivoted inverses of order n (k = 1) in one batch")
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
     p.add_argument("--slices", type=int, default=3)
-    p.add_argument("--refine", type=int, default=0)
+    p.add_argument("--refine", type=int, default=None,
+                   help="two-sided refinement steps (0 or 1); default 1 on fp64_tc and fp64, where it meets the "
+                        "1e-10 target at k = 8, else 0")
     p.add_argument("--together", type=int, default=32,
                    help="run each step's blocks as independent runs, this many executed together level by level "
                         "in grouped launches (0: one run after the other)")
@@ -65,7 +67,10 @@ def parse():
                    help="batched workload: this many independent matrices of uneven n and k, one block each")
     p.add_argument("--backward", action="store_true",
                    help="differentiation workload: one block forward and the adjoint backward per step")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.refine is None:
+        args.refine = 1 if args.precision in ("fp64_tc", "fp64") else 0
+    return args
 
 
 def peaks():
@@ -440,7 +445,7 @@ def main():
     diff_fp64 = None
     if args.precision == "fp64_tc" and not args.no_fp64_check:
         i0, j0 = rank_blocks(k, rank, world, args.warmup + args.steps - 1, bps)[0]
-        with mb.Context(M, k, precision="fp64") as c64:
+        with mb.Context(M, k, precision="fp64", refine=args.refine) as c64:
             ref64 = c64.block(i0, j0).double().cpu().numpy()
         diff_fp64 = float(np.linalg.norm(outs[0].double().cpu().numpy() - ref64) / np.linalg.norm(ref64))
 
