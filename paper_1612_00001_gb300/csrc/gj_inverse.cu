@@ -102,8 +102,6 @@ __device__ __forceinline__ double key_value(long long k, double) {
 __device__ __forceinline__ float key_value(long long k, float) {
   return k < 0 ? __int_as_float(0x7FC00000) : __int_as_float((int)k);
 }
-__device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) << 1) != 0; }
-__device__ __forceinline__ bool nonzero(float v) { return (__float_as_int(v) << 1) != 0; }
 
 // A cluster of CL CTAs per matrix factors the panel [p, p + nb) (see the file
 // comment).  CTA q of the cluster keeps rows [q R, (q+1) R) of the panel in
@@ -228,10 +226,12 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
       }
       const TW* src = (i == r && r != j) ? jrow : xi;
       const TW f = src[t];
-      const bool nz = nonzero(f);
+      // no test for f == 0: base - 0 * s is base for every finite s, and a
+      // non-finite scaled pivot row has already marked the matrix singular;
+      // the guarded form cost FP64 issue slots (20% of the panel time)
       for (int c = lane; c < nb; c += 32) {
         const TW base = (c == t) ? (TW)0 : src[c];
-        xi[c] = nz ? base - f * srow[c] : base;
+        xi[c] = base - f * srow[c];
       }
     }
     __syncthreads();  // the next column's candidates read the eliminated rows
