@@ -496,31 +496,35 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       Q.kpad = T.kpad;
       Q.kb0 = 0;
       Q.nkb = T.kpad / oz::tile_k();  // at most kMaxKBlocks: panels are far narrower than 512
-      Q.tiles_m = T.rpa / oz::tile_m();
-      Q.tiles_n = T.rpb / oz::tile_n();
       Q.ea = ea;
       Q.eb = eb;
       Q.ea_rows = T.rpa;
       Q.eb_rows = T.rpb;
       Q.err = tc->err;
-      auto product = [&](double alpha, double beta) -> cudaError_t {
+      Q.contiguous = 1;  // the skipped panel columns recur every tiles_n tiles
+      auto product = [&](double alpha, double beta, int tiles_m, int tiles_n) -> cudaError_t {
         cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, T.kpad, da, ea, s);
         if (e2 != cudaSuccess) return e2;
         e2 = oz::launch_pack(pb, count, T.rpb, T.kpad, db, eb, s);
         if (e2 != cudaSuccess) return e2;
         Q.alpha = alpha;
         Q.beta = beta;
+        Q.tiles_m = tiles_m;
+        Q.tiles_n = tiles_n;
         nl += 3;
         return oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
       };
       if (p > 0) {
         gj_tc_done_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
         ++nl;
-        if ((e = product(-1.0, 0.0)) != cudaSuccess) return e;
+        // p x w outputs per matrix: the tile grid of the largest
+        if ((e = product(-1.0, 0.0, (p + oz::tile_m() - 1) / oz::tile_m(), (w + oz::tile_n() - 1) / oz::tile_n())) !=
+            cudaSuccess)
+          return e;
       }
       gj_tc_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
       ++nl;
-      if ((e = product(1.0, 1.0)) != cudaSuccess) return e;
+      if ((e = product(1.0, 1.0, T.rpa / oz::tile_m(), T.rpb / oz::tile_n())) != cudaSuccess) return e;
     } else if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
       using Cfg = TileCfg<TW>;
       dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);

@@ -122,35 +122,32 @@ __device__ __noinline__ double scale_rare(uint64_t mant, int e2, bool neg) {
   return neg ? -v : v;
 }
 
-// +-2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64 (ties to
-// even), negated when neg_alpha; the exponent field is assembled directly
-// with integer instructions.
+// +-2^e * S with S = sum_g a_g 128^(7 - g) (|a_g| < 2^24, so |S| < 2^75),
+// rounded once to FP64 (ties to even), negated when neg_alpha; 64-bit integer
+// instructions only, the exponent field assembled directly.  S is carried as
+// H 2^28 + l with 0 <= l < 2^28, then as sign and magnitude Hm 2^28 + lm.
 __device__ __forceinline__ double combine(const int (&a)[ND], int e, bool neg_alpha) {
-  const long long hi = ((a[0] * 128LL + a[1]) * 128LL + a[2]) * 128LL + a[3];
-  const long long lo = ((a[4] * 128LL + a[5]) * 128LL + a[6]) * 128LL + a[7];
-  const __int128 S = (__int128)hi * (__int128)(1LL << 28) + (__int128)lo;
-  if (S == 0) return 0.0;
-  bool neg = S < 0;
-  const unsigned __int128 U = neg ? (unsigned __int128)(-S) : (unsigned __int128)S;
-  const uint64_t uh = (uint64_t)(U >> 64), ul = (uint64_t)U;
-  int top = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);  // leading bit, <= 74
-  uint64_t mant;
-  if (top <= 52) {
-    mant = ul << (52 - top);
-  } else {
-    const int sh = top - 52;  // 1 .. 22
-    mant = (uint64_t)(U >> sh);
-    const uint64_t rem = ul & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1))) ++mant;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++top;
-    }
-  }
-  neg ^= neg_alpha;
-  const int e2 = top + e;  // value = mant 2^(e2 - 52)
-  if (e2 < -1022 || e2 > 1023) return scale_rare(mant, e2, neg);
-  return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)(e2 + 1023) << 52) |
+  long long H = (long long)a[0] * (1 << 21) + (long long)a[1] * (1 << 14) + (long long)a[2] * 128 + a[3];
+  const long long L = (long long)a[4] * (1 << 21) + (long long)a[5] * (1 << 14) + (long long)a[6] * 128 + a[7];
+  H += L >> 28;  // floor: the low part becomes the non-negative l
+  const uint32_t l = (uint32_t)L & 0x0FFFFFFFu;
+  const bool neg = H < 0;
+  // -(H 2^28 + l) = (-H - 1) 2^28 + (2^28 - l) when l > 0
+  const uint64_t Hm = neg ? (uint64_t)(-H) - (l != 0u ? 1u : 0u) : (uint64_t)H;
+  const uint32_t lm = (neg && l != 0u) ? (1u << 28) - l : l;
+  if ((Hm | lm) == 0) return 0.0;
+  const int top = Hm ? 91 - __clzll((long long)Hm) : 31 - __clz((int)lm);  // leading bit of |S|, <= 74
+  const int sh = top > 52 ? top - 52 : 0;                                  // bits rounded off, <= 22
+  uint64_t mant = (Hm << (28 - sh)) | (uint64_t)(lm >> sh);                // floor(|S| / 2^sh)
+  const uint32_t rmask = (1u << sh) - 1u, rem = lm & rmask, half = (rmask >> 1) + 1u;
+  mant += (rem > half || (rem == half && (mant & 1u))) ? 1u : 0u;
+  mant <<= (sh ? 0 : 52 - top);  // leading bit to 52 (53 after a carry out of the rounding)
+  const bool neg_out = neg != neg_alpha;
+  const int e2 = top + e;        // value = mant 2^(e2 - 52)
+  const int e2n = e2 + (int)(mant >> 53);
+  if (e2n < -1022 || e2n > 1023) return scale_rare(mant, e2, neg_out);
+  // a carry out of the rounding leaves mant = 2^53, whose low 52 bits are zero
+  return __longlong_as_double((long long)(((uint64_t)neg_out << 63) | ((uint64_t)(e2n + 1023) << 52) |
                                           (mant & 0xFFFFFFFFFFFFFull)));
 }
 
@@ -221,6 +218,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // The tiles of this CTA: a contiguous range, or every gridDim.x-th one.
+  const int t_begin = P.contiguous ? (int)((int64_t)blockIdx.x * total_tiles / gridDim.x) : (int)blockIdx.x;
+  const int t_end = P.contiguous ? (int)((int64_t)(blockIdx.x + 1) * total_tiles / gridDim.x) : total_tiles;
+  const int t_step = P.contiguous ? 1 : (int)gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // epilogue of the current one drains the accumulators
       int na = 0, nbq = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+      for (int t = t_begin; ok && t < t_end; t += t_step) {
         int g, tm, tn;
         if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
         const int aslab = probs[g].a_slab, bslab = probs[g].b_slab;
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ---------------- MMA issuer
       int na = 0, nbq = 0, it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
+      for (int t = t_begin; ok && t < t_end; t += t_step) {
         int g, tm, tn;
         if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
         // the epilogue has read the previous tile's accumulators out
@@ -313,8 +314,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3, c0 = 16 * ((warp - 2) >> 2);
     const bool neg_alpha = P.alpha < 0.0;  // alpha is +-1 and beta 0 or 1 (checked at launch)
     const bool use_cin = P.beta != 0.0;
+    const bool small_k = P.nkb == 1;  // one K block of 64
     int it = 0;
-    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    for (int t = t_begin; t < t_end; t += t_step) {
       int g, tm, tn;
       if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
       const Problem pr = probs[g];
@@ -363,8 +365,16 @@ __global__ void __launch_bounds__(THREADS, 1)
               v = __longlong_as_double(0x7FF8000000000000LL);
             } else {
               int a[ND];
+              if (small_k) {
+                // |G_g| <= 8 * 64 * 2^12 = 2^21: adding 1.5 * 2^23 puts the
+                // integer in the low mantissa bits (an FP32 add, not a conversion)
 #pragma unroll
-              for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
+                for (int gg = 0; gg < ND; ++gg)
+                  a[gg] = __float_as_int(__uint_as_float(acc[gg][u]) + 12582912.0f) - 0x4B400000;
+              } else {
+#pragma unroll
+                for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
+              }
               v = combine(a, ei + fj - 61, neg_alpha);
             }
             const int col = col0 + c;
