@@ -104,14 +104,22 @@ __device__ __forceinline__ void digits8(double x, int E, int (&d)[ND]) {
     }
     X = (bits >> 63) ? -(int64_t)u : (int64_t)u;
   }
+  // The balanced digits (d_1..d_7 in [-64, 63]) are the base-128 digits of
+  // X + B, B = 64 (1 + 128 + ... + 128^7), each less 64: X + B lies in
+  // (0, 2^57) for |X| <= 2^55, and every digit comes from its own shift.
+  constexpr long long kBias = 64LL * (((1LL << 56) - 1) / 127);
+  const uint64_t Y = (uint64_t)(X + kBias);
+  d[0] = (int)(Y >> 49) - 64;
 #pragma unroll
-  for (int p = ND - 1; p >= 1; --p) {
-    int r = (int)(X & 127);
-    if (r >= 64) r -= 128;
-    d[p] = r;
-    X = (X - r) / 128;  // exact
-  }
-  d[0] = (int)X;
+  for (int p = 1; p < ND; ++p) d[p] = (int)((Y >> (7 * (ND - 1 - p))) & 127u) - 64;
+}
+
+// The BF16 pair of two digits (|d| <= 64: exact in BF16): each digit becomes
+// an FP32 through the mantissa of 1.5 * 2^23 (integer add, FP32 subtract).
+__device__ __forceinline__ __nv_bfloat162 digit_pair(int a, int b) {
+  const float fa = __int_as_float(0x4B400000 + a) - 12582912.0f;
+  const float fb = __int_as_float(0x4B400000 + b) - 12582912.0f;
+  return __floats2bfloat162_rn(fa, fb);
 }
 
 // The rare results below the normal range or above it: mant 2^(e2 - 52),
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
                                                        int rpc, __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
   extern __shared__ double S[];  // [rpc][kc + 1]
   __shared__ int sE[PMAXR];
-  __shared__ unsigned long long smx[PMAXR];  // running row maxima (bit patterns)
+  __shared__ unsigned smx[PMAXR];  // running row maxima (high words of the bit patterns)
   const PackDesc d = descs[blockIdx.y];
   const int r0 = blockIdx.x * rpc;
   const int rw = rpc / 8;  // rows per warp
@@ -447,26 +455,25 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
     if (c > 0) __syncthreads();
     load_chunk(k0);
     __syncthreads();
+    // the exponent of the largest magnitude is in the high words alone (a row
+    // whose high words are all zero holds zeros and subnormals, whose digits
+    // are zero whatever E is)
     for (int h = 0; h < rw; ++h) {
       const int rr = warp * rw + h;
       const double* row = S + rr * lds;
-      unsigned long long mx = 0;
+      unsigned mx = 0;
       for (int kk = lane; kk < kw; kk += 32) {
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(row[kk]) & 0x7FFFFFFFFFFFFFFFull;
-        mx = bits > mx ? bits : mx;
+        const unsigned hi = (unsigned)__double2hiint(row[kk]) & 0x7FFFFFFFu;
+        mx = hi > mx ? hi : mx;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = y > mx ? y : mx;
-      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
       if (lane == 0) smx[rr] = (c > 0 && smx[rr] > mx) ? smx[rr] : mx;
     }
   }
   __syncthreads();
   for (int rr = tid; rr < rpc; rr += 256) {
-    const unsigned long long m = r0 < R ? smx[rr] : 0ull;
-    const int ex = (int)(m >> 52);
+    const unsigned m = r0 < R ? smx[rr] : 0u;
+    const int ex = (int)(m >> 20);
     // 2^E > max|x|: E = ex - 1022 for a normal maximum
     const int E = m == 0 ? 0 : (ex == 0x7ff ? kNonFinite : (ex == 0 ? -1022 : ex - 1022));
     sE[rr] = E;
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
       load_chunk(k0);
       __syncthreads();
     }
-#pragma unroll 1
+#pragma unroll 2
     for (int h = 0; h < rw; ++h) {
       const int rr = warp * rw + h;
       const int E = sE[rr];
@@ -492,12 +499,8 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
         digits8(row[kk], E, d0);
         digits8(row[kk + 1], E, d1);
 #pragma unroll
-        for (int p = 0; p < ND; ++p) {
-          __nv_bfloat162 v;
-          v.x = __float2bfloat16_rn((float)d0[p]);
-          v.y = __float2bfloat16_rn((float)d1[p]);
-          *(__nv_bfloat162*)&out[(int64_t)p * rows_pad * kpad + kk] = v;
-        }
+        for (int p = 0; p < ND; ++p)
+          *(__nv_bfloat162*)&out[(int64_t)p * rows_pad * kpad + kk] = digit_pair(d0[p], d1[p]);
       }
     }
   }
