@@ -114,6 +114,13 @@ __device__ __forceinline__ void digits8(double x, int E, int (&d)[ND]) {
   for (int p = 1; p < ND; ++p) d[p] = (int)((Y >> (7 * (ND - 1 - p))) & 127u) - 64;
 }
 
+// 8-byte asynchronous copy global -> shared; ok = false writes zeros and
+// reads nothing.
+__device__ __forceinline__ void cp_async8(void* dst, const double* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(ok ? 8 : 0)
+               : "memory");
+}
+
 // The BF16 pair of two digits (|d| <= 64: exact in BF16): each digit becomes
 // an FP32 through the mantissa of 1.5 * 2^23 (integer add, FP32 subtract).
 __device__ __forceinline__ __nv_bfloat162 digit_pair(int a, int b) {
@@ -422,6 +429,9 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
   const int kc = kpad < PKC ? kpad : PKC;  // staged chunk of K
   const int lds = kc + 1;
   const int chunks = (kpad + kc - 1) / kc;
+  // Stages entries [k0, k0 + kw) of the CTA's rows with asynchronous copies
+  // (every copy of the stage in flight at once, none through registers);
+  // entries past the source are zero-filled.
   auto load_chunk = [&](int k0) {
     const int kw = min(kc, kpad - k0);
     if (!d.transpose) {
@@ -429,24 +439,25 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
       const int tk = kw < 256 ? kw : 256;  // threads per row
       const int rg = tid / tk, kk0 = tid - rg * tk, rstep = 256 / tk;
       if (rg < rstep) {
-#pragma unroll 4
         for (int rr = rg; rr < rpc; rr += rstep) {
           const int r = r0 + rr;
           for (int kk = kk0; kk < kw; kk += tk) {
             const int k = k0 + kk;
-            S[rr * lds + kk] = (r < R && k < KD) ? d.src[(int64_t)r * d.ld + k] : 0.0;
+            const bool ok = r < R && k < KD;
+            cp_async8(&S[rr * lds + kk], ok ? d.src + (int64_t)r * d.ld + k : d.src, ok);
           }
         }
       }
     } else {
       const int rr = tid & (rpc - 1);
       const int r = r0 + rr;
-#pragma unroll 4
       for (int kk = tid / rpc; kk < kw; kk += 256 / rpc) {
         const int k = k0 + kk;
-        S[rr * lds + kk] = (r < R && k < KD) ? d.src[(int64_t)k * d.ld + r] : 0.0;
+        const bool ok = r < R && k < KD;
+        cp_async8(&S[rr * lds + kk], ok ? d.src + (int64_t)k * d.ld + r : d.src, ok);
       }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   };
   // ---- pass 1: largest magnitude of each row (warp w: rows w rw .. w rw + rw - 1)
   for (int c = 0; c < chunks; ++c) {
