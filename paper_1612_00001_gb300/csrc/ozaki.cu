@@ -425,6 +425,9 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
   const int r0 = blockIdx.x * rpc;
   const int rw = rpc / 8;  // rows per warp
   const int R = d.transpose ? d.cols : d.rows, KD = d.transpose ? d.rows : d.cols;
+  // slab rows past the last 128-row tile that holds a source row are never
+  // read (a product reads only the tiles of its problem's extent): leave them
+  if (r0 >= (R + 127) / 128 * 128) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kc = kpad < PKC ? kpad : PKC;  // staged chunk of K
   const int lds = kc + 1;
