@@ -447,12 +447,22 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   // and keep a CTA's rows within about 72 KB so that three CTAs share an SM
   // (their per-column barriers and pivot exchanges then overlap one another's
   // eliminations: measured 18% less panel time than one 135 KB CTA per SM)
-  int CL = 8;
-  while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
-  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > 72 * 1024) CL <<= 1;
-  while (CL < 8 && ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
-  const size_t psmem = ((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW);
-  if (psmem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+  // (m rows eliminated per matrix: b, or with tensor-core updates only the
+  // b - p rows not yet used as pivots, so later panels take smaller clusters)
+  auto cluster_for = [&](int m) {
+    int CL = 8;
+    while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
+    // fewer, fuller CTAs while the smaller cluster still covers every SM
+    while (CL > 1 && count * (CL / 2) >= 152 && (m + CL / 2 - 1) / (CL / 2) * (nb + 1) * sizeof(TW) <= 64 * 1024)
+      CL >>= 1;
+    while (CL < 8 && ((size_t)((m + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > 72 * 1024) CL <<= 1;
+    while (CL < 8 && ((size_t)((m + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
+    return CL;
+  };
+  {
+    const int CL = cluster_for(b);
+    if (((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
@@ -461,10 +471,12 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   }
   for (int p = 0; p < b; p += nb) {
     const int w = std::min(nb, b - p);  // widest panel of this step (b is the largest order)
+    const int m = tc && w < b ? b - p : b;
+    const int CL = cluster_for(m);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * CL, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
-    cfg.dynamicSmemBytes = ((size_t)((b + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
+    cfg.dynamicSmemBytes = ((size_t)((m + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
