@@ -103,6 +103,18 @@ __device__ __forceinline__ float key_value(long long k, float) {
   return k < 0 ? __int_as_float(0x7FC00000) : __int_as_float((int)k);
 }
 
+// Warp-wide argmax of (key, row): the largest key, and among equal keys the
+// smallest row, in three warp reductions (the key's high word, its low word
+// among the lanes that hold the largest high word, then the row).
+__device__ __forceinline__ void warp_argmax(long long& key, int& row) {
+  const int hi = (int)(key >> 32);
+  const unsigned lo = (unsigned)key;
+  const int mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+  row = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? row : 0x7fffffff);
+  key = (long long)(((unsigned long long)(unsigned)mh << 32) | ml);
+}
+
 // A cluster of CL CTAs per matrix factors the panel [p, p + nb) (see the file
 // comment).  CTA q of the cluster keeps rows [q R, (q+1) R) of the panel in
 // its shared memory (R = ceil(b / CL)); the CTAs exchange pivot candidates
@@ -122,6 +134,13 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
   const int q = (int)cluster.block_rank();
   const InvDesc d = descs[blockIdx.x / CL];
   const int b = d.b;
+  // a cluster of one CTA synchronises as a CTA
+  auto csync = [&]() {
+    if (CL == 1)
+      __syncthreads();
+    else
+      cluster.sync();
+  };
   // matrices of a batch may differ in order: this one's panel may be narrower
   // or already past its end (the whole cluster leaves together)
   const int ldp = nb + 1;  // odd stride: a column read by consecutive rows spreads over banks
@@ -161,14 +180,10 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
         const long long v = pivot_key(P[(i - r0) * ldp + t]);
         if (v > best) { best = v; bi = i; }  // NaN never wins
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
+      warp_argmax(best, bi);
       if (lane == 0) { cand_v[buf][warp] = best; cand_i[buf][warp] = bi; }
     }
-    cluster.sync();  // #1: the candidates of every warp of every CTA are visible
+    csync();  // #1: the candidates of every warp of every CTA are visible
     // ---- global pivot, computed by every warp from the same CL x NW candidates
     int r;
     long long gk;
@@ -180,11 +195,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
         const int ci = *cluster.map_shared_rank(&cand_i[buf][u % NW], u / NW);
         if (cv > v || (cv == v && ci < ix)) { v = cv; ix = ci; }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
-        if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; }
-      }
+      warp_argmax(v, ix);
       r = ix >= b ? j : ix;  // every candidate NaN: keep the row
       gk = v;
     }
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
         for (int c = tid; c < nb; c += kPanelThreads) jrow[c] = sj[c];
       }
     }
-    cluster.sync();  // #2: every CTA has read rows j and r; prow and jrow are complete
+    csync();  // #2: every CTA has read rows j and r; prow and jrow are complete
     // ---- scale the pivot row and eliminate column j (warp per row, lane per
     // column).  Row j receives the scaled pivot row; row r, when it moved,
     // starts from the old row j (jrow).
