@@ -28,6 +28,11 @@ if ROOT not in sys.path:
 
 METRIC = "inverse blocks/sec & GEMM % of tensor peak, mixed vs FP64 at ≤1e-10 rel err"
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
+# DRAM bytes per algorithmic flop of the FP64_TC panel factorisation, from one
+# ncu capture (profiles/gj_panel_kernel_fp64tc_b512_x300.md: a launch of 300
+# panels of 512 rows x 64 columns read and wrote 253.3 MB for 1.258 GFLOP).
+# With 64 columns a panel's flops and its row traffic both grow with its rows.
+PANEL_DRAM_BYTES_PER_FLOP = 253.33e6 / (300 * 2 * 512 * 64 * 64)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
 
@@ -412,7 +417,7 @@ def main():
     agg = {"gemm_flops": 0.0, "inv_flops": 0.0, "gemm_device_seconds": 0.0, "inv_device_seconds": 0.0,
            "launches": 0, "gemm_launches": 0, "inversions": 0, "peak_device_bytes": 0,
            "pack_device_seconds": 0.0, "inv_panel_device_seconds": 0.0, "inv_panel_flops": 0.0,
-           "inv_update_flops": 0.0}
+           "inv_update_flops": 0.0, "inv_panel_launches": 0}
     torch.cuda.synchronize()
     for s in range(args.steps):
         flush.fill_(s & 0xFF)  # L2 flush, outside the timed interval
@@ -474,7 +479,7 @@ def main():
                                        "launches": agg["gemm_launches"], "peak": alu[0], "peak_source": alu[1]}
     fp_peak = alu
     fams["gj_panel_kernel"] = {"bound": "alu", "work": agg["inv_panel_flops"],
-                               "dsec": agg["inv_panel_device_seconds"], "launches": None,
+                               "dsec": agg["inv_panel_device_seconds"], "launches": agg["inv_panel_launches"],
                                "peak": fp_peak[0], "peak_source": fp_peak[1] + "; panel factorisations, 2 b w^2 "
                                                                   "flop per panel of width w"}
     upd_dsec = agg["inv_device_seconds"] - agg["inv_panel_device_seconds"]
@@ -494,6 +499,13 @@ def main():
         ach = f["work"] / f["dsec"] / 1e12 if f["dsec"] > 0 else 0.0
         kernels[name] = {"bound": f["bound"], "achieved": ach, "peak": f["peak"], "unit": "TFLOP/s",
                          "frac": ach / f["peak"], "device_seconds": f["dsec"], "peak_source": f["peak_source"]}
+        if f.get("launches"):
+            kernels[name]["launches"] = f["launches"]
+        if name == "gj_panel_kernel" and args.precision == "fp64_tc" and f.get("launches"):
+            # DRAM bytes of an average launch (ncu bytes per flop x its flops)
+            kernels[name]["traffic"] = PANEL_DRAM_BYTES_PER_FLOP * f["work"] / f["launches"]
+            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                                               "scaled by algorithmic flops to the average launch")
         if args.precision == "fp64_tc" and f["bound"] == "tensor":
             kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
     if agg["pack_device_seconds"] > 0:
@@ -501,7 +513,7 @@ def main():
                                       "note": "digit or slice packing of the Schur operands (HBM/L2 bound)"}
     dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: kernels[k]["device_seconds"])
     roofline = dict(kernels[dom])
-    roofline.update({"kernel": dom, "traffic": None, "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
+    roofline.update({"kernel": dom, "traffic": kernels[dom].get("traffic"), "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
                      "families": kernels})
 
     line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,

@@ -119,6 +119,8 @@ typedef struct {
     double inv_update_flops;    /* algorithmic flops of the trailing
                                    updates: 2 b w (b - w) per panel (with
                                    inv_panel_flops, 2 b^3 per inverse) */
+    size_t inv_panel_launches;  /* profile = 1: panel factorisation launches
+                                   timed in inv_panel_device_seconds */
 } mbinv_report;
 
 typedef struct mbinv_ctx mbinv_ctx;

@@ -49,7 +49,8 @@ class Report(ctypes.Structure):
                 ("failed_pivot", ctypes.c_int64), ("gemm_device_seconds", ctypes.c_double),
                 ("inv_device_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_size_t),
                 ("pack_device_seconds", ctypes.c_double), ("inv_panel_device_seconds", ctypes.c_double),
-                ("inv_panel_flops", ctypes.c_double), ("inv_update_flops", ctypes.c_double)]
+                ("inv_panel_flops", ctypes.c_double), ("inv_update_flops", ctypes.c_double),
+                ("inv_panel_launches", ctypes.c_size_t)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -255,6 +255,7 @@ void add_env_report(mbinv_report* r, const Env& env) {
   r->inv_panel_device_seconds += env.inv_panel_dev_s;
   r->inv_panel_flops += env.inv_panel_flops;
   r->inv_update_flops += env.inv_update_flops;
+  r->inv_panel_launches += env.inv_panel_launches;
 }
 
 void add_report(mbinv_report* r, const mbinv_ctx* c, const Schedule& S, size_t nreq) {
@@ -923,6 +924,7 @@ static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, 
       rep->inv_panel_device_seconds += r.inv_panel_device_seconds;
       rep->inv_panel_flops += r.inv_panel_flops;
       rep->inv_update_flops += r.inv_update_flops;
+      rep->inv_panel_launches += r.inv_panel_launches;
       rep->peak_device_bytes = std::max(rep->peak_device_bytes, r.peak_device_bytes);
     }
     if (s != MBINV_OK) return s;

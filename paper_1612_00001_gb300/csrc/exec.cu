@@ -143,6 +143,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   E.launches = E.gemm_launches = 0;
   E.gemm_dev_s = E.inv_dev_s = E.pack_dev_s = 0;
   E.inv_panel_dev_s = E.inv_panel_flops = E.inv_update_flops = 0;
+  E.inv_panel_launches = 0;
   E.job_singular.assign(jobs.size(), 0);
   if (jobs.empty()) return MBINV_OK;
   const bool mixed = E.precision == MBINV_MIXED_BF16;
@@ -637,6 +638,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
       float ms = 0;
       CUE(cudaEventElapsedTime(&ms, E.pevents[q], E.pevents[q + 1]));
       E.inv_panel_dev_s += ms * 1e-3;
+      ++E.inv_panel_launches;
     }
   }
   if (herr) return MBINV_ETIMEOUT;

@@ -78,6 +78,7 @@ struct Env {
   int launches = 0, gemm_launches = 0;
   double gemm_dev_s = 0, inv_dev_s = 0, pack_dev_s = 0;
   double inv_panel_dev_s = 0, inv_panel_flops = 0, inv_update_flops = 0;
+  size_t inv_panel_launches = 0;
   std::vector<cudaEvent_t> pevents;  // panel timing (profile)
   std::vector<int> job_singular;  // per request
   cudaError_t last_error = cudaSuccess;
