@@ -524,7 +524,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       Q.ea_rows = T.rpa;
       Q.eb_rows = T.rpb;
       Q.err = tc->err;
-      Q.contiguous = 1;  // the skipped panel columns recur every tiles_n tiles
+      Q.coprime_grid = 1;  // the skipped panel columns recur every tiles_n tiles
       auto product = [&](double alpha, double beta, int tiles_m, int tiles_n) -> cudaError_t {
         cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, T.kpad, da, ea, s);
         if (e2 != cudaSuccess) return e2;

@@ -233,10 +233,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  // The tiles of this CTA: a contiguous range, or every gridDim.x-th one.
-  const int t_begin = P.contiguous ? (int)((int64_t)blockIdx.x * total_tiles / gridDim.x) : (int)blockIdx.x;
-  const int t_end = P.contiguous ? (int)((int64_t)(blockIdx.x + 1) * total_tiles / gridDim.x) : total_tiles;
-  const int t_step = P.contiguous ? 1 : (int)gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -244,7 +240,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // epilogue of the current one drains the accumulators
       int na = 0, nbq = 0;
       bool ok = true;
-      for (int t = t_begin; ok && t < t_end; t += t_step) {
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
         int g, tm, tn;
         if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
         const int aslab = probs[g].a_slab, bslab = probs[g].b_slab;
@@ -275,7 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ---------------- MMA issuer
       int na = 0, nbq = 0, it = 0;
       bool ok = true;
-      for (int t = t_begin; ok && t < t_end; t += t_step) {
+      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
         int g, tm, tn;
         if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
         // the epilogue has read the previous tile's accumulators out
@@ -331,7 +327,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool use_cin = P.beta != 0.0;
     const bool small_k = P.nkb == 1;  // one K block of 64
     int it = 0;
-    for (int t = t_begin; t < t_end; t += t_step) {
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
       int g, tm, tn;
       if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
       const Problem pr = probs[g];
@@ -577,7 +573,19 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
     if (sms <= 0) sms = 1;
   }
   const int total = count * P.tiles_m * P.tiles_n;
-  oz_gemm_kernel<<<total < sms ? total : sms, THREADS, sm, s>>>(ta, tb, P, d_probs, total);
+  int grid = total < sms ? total : sms;
+  if (P.coprime_grid) {
+    auto gcd = [](int a, int b) {
+      while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+      }
+      return a;
+    };
+    while (grid > 1 && gcd(grid, P.tiles_n) != 1) --grid;
+  }
+  oz_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, P, d_probs, total);
   return cudaGetLastError();
 }
 

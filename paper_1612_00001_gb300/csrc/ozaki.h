@@ -51,10 +51,11 @@ struct Params {
   const int* eb;   // row exponents of the B slabs: eb[slab * eb_rows + r]
   int ea_rows, eb_rows;
   int* err;        // raised when a bounded wait ran out
-  // 0: CTA c takes tiles c, c + grid, ... (CTAs side by side share operand
-  // tiles in L2); 1: CTA c takes one contiguous range of tiles (balanced when
-  // dead tiles recur with the tile grid's period, as skipped columns do)
-  int contiguous;
+  // CTA c takes tiles c, c + grid, ... (CTAs side by side share operand
+  // tiles in L2).  1: the grid size is made coprime with tiles_n, so that
+  // dead tiles recurring with the column period (skipped columns) fall on
+  // every CTA alike instead of on the CTAs whose index shares the period
+  int coprime_grid;
 };
 
 int tile_m();  // 128 output rows per CTA
