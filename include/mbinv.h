@@ -178,7 +178,7 @@ mbinv_status mbinv_block(mbinv_ctx *ctx, int64_t i, int64_t j, void *out, int64_
  * receives block (ij[2t], ij[2t+1]) with leading dimension ldos[t].  width
  * bounds how many runs go together (0 = 8), and the cap may lower it.  With
  * refine_steps = 1 every block is refined as in mbinv_block, each needed
- * block row and column computed once. */
+ * block row and column computed once (their runs width together). */
 mbinv_status mbinv_blocks(mbinv_ctx *ctx, int64_t count, const int64_t *ij, void *const *outs, const int64_t *ldos,
                           int width, mbinv_report *report);
 

@@ -574,11 +574,12 @@ GemmDesc gdesc(const void* A, int64_t lda, const void* B, int64_t ldb, const voi
 }
 
 // Refinement of many blocks at once: the block rows X_i and block columns Y_j
-// they need are computed once (every block of them by its own run, all runs
+// they need are computed once (every block of them by its own run, width runs
 // executed together), then one residual E_i^T - X_i M per distinct row and
 // one correction X_i E_j + R_i Y_j per block, each set in one grouped launch.
 mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, int64_t>>& v,
-                            const std::vector<void*>& outs, const std::vector<int64_t>& ldos, mbinv_report* rep) {
+                            const std::vector<void*>& outs, const std::vector<int64_t>& ldos, int width,
+                            mbinv_report* rep) {
   const int64_t n = c->n, b = c->b, k = c->k;
   std::map<int64_t, int> rows, cols;
   for (auto& p : v) {
@@ -615,7 +616,7 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
     }
   const int saved_dtype = c->dtype;
   c->dtype = xt;  // the sweeps write blocks in the working type
-  mbinv_status s = blocks_to(c, ij, dst, ld, kDefaultWidth, rep);
+  mbinv_status s = blocks_to(c, ij, dst, ld, width, rep);
   c->dtype = saved_dtype;
   if (s != MBINV_OK) return s;
   for (auto& p : copies) {
@@ -854,7 +855,7 @@ static mbinv_status mbinv_block_impl(mbinv_ctx* c, int64_t i, int64_t j, void* o
   mbinv_status s;
   if (c->opt.refine_steps > 0 && !c->in_sweep) {
     c->in_sweep = true;
-    s = refined_blocks(c, {{i, j}}, {out}, {ldo}, rep);
+    s = refined_blocks(c, {{i, j}}, {out}, {ldo}, kDefaultWidth, rep);
     c->in_sweep = false;
   } else {
     s = blocks_to(c, {{i, j}}, {out}, {ldo}, 1, rep);
@@ -881,7 +882,7 @@ static mbinv_status mbinv_blocks_impl(mbinv_ctx* c, int64_t count, const int64_t
   mbinv_status s = MBINV_OK;
   if (c->opt.refine_steps > 0) {
     c->in_sweep = true;
-    s = refined_blocks(c, v, o, l, rep);
+    s = refined_blocks(c, v, o, l, width > 0 ? width : kDefaultWidth, rep);
     c->in_sweep = false;
   } else {
     s = blocks_to(c, v, o, l, width > 0 ? width : kDefaultWidth, rep);
