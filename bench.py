@@ -33,6 +33,11 @@ FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
 # panels of 512 rows x 64 columns read and wrote 253.3 MB for 1.258 GFLOP).
 # With 64 columns a panel's flops and its row traffic both grow with its rows.
 PANEL_DRAM_BYTES_PER_FLOP = 253.33e6 / (300 * 2 * 512 * 64 * 64)
+# The same for the FP64_TC trailing-update digit product (per FP64-equivalent
+# flop), from profiles/oz_gemm_kernel_trailing_update_b512_x300.md: one launch
+# updating 300 matrices of order 512 (panel of 64, 448 other columns) read
+# and wrote 1.274 GB for 8.81 GFLOP.
+UPDATE_DRAM_BYTES_PER_FLOP = 1.274e9 / (300 * 2 * 512 * 64 * 448)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
 
@@ -485,7 +490,8 @@ def main():
     upd_dsec = agg["inv_device_seconds"] - agg["inv_panel_device_seconds"]
     if args.precision == "fp64_tc":
         fams["gj_trailing_update"] = {"bound": "tensor", "work": agg["inv_update_flops"] * DIGIT_PAIRS,
-                                      "dsec": upd_dsec, "launches": None, "peak": pk["bf16_tflops_sustained"],
+                                      "dsec": upd_dsec, "launches": agg["inv_panel_launches"],
+                                      "peak": pk["bf16_tflops_sustained"],
                                       "peak_source": f"{tc_src}, executed digit-pair products of the trailing "
                                                      "updates; time includes their digit packs and the inverses' "
                                                      "init/finalize"}
@@ -506,6 +512,12 @@ def main():
             kernels[name]["traffic"] = PANEL_DRAM_BYTES_PER_FLOP * f["work"] / f["launches"]
             kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
                                                "scaled by algorithmic flops to the average launch")
+        if name == "gj_trailing_update" and args.precision == "fp64_tc" and f.get("launches"):
+            # one trailing update per panel launch; FP64-equivalent flops
+            kernels[name]["traffic"] = UPDATE_DRAM_BYTES_PER_FLOP * agg["inv_update_flops"] / f["launches"]
+            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one trailing-"
+                                               "update oz_gemm_kernel launch, scaled by algorithmic flops to the "
+                                               "average update (its digit packs and done-rows products excluded)")
         if args.precision == "fp64_tc" and f["bound"] == "tensor":
             kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
     if agg["pack_device_seconds"] > 0:
