@@ -43,12 +43,6 @@ constexpr int kPanelThreads = 256;
 constexpr int kMaxPanelWidth = 256;
 constexpr int kSmemLimit = 200 * 1024;
 
-template <typename T>
-__device__ __forceinline__ T load_as(const void* p, int dtype, int64_t idx) {
-  if (dtype == F64) return (T)((const double*)p)[idx];
-  return (T)((const float*)p)[idx];
-}
-
 template <typename TW>
 __device__ __forceinline__ TW eps_of();
 template <>
@@ -61,27 +55,39 @@ __global__ void zero_amax_kernel(const InvDesc* __restrict__ d, int count) {
   if (t < count) *d[t].amax = 0ull;
 }
 
-// work = (TW) src; amax = max |src| (as the bit pattern of a non-negative
+// work = (TW) src; amax = max |src| as the bit pattern of a non-negative
 // double: the integer order of those patterns is their numeric order, and a
-// NaN compares above every number, which makes the matrix singular).
+// NaN's pattern is above every number's, which makes the matrix singular.
+// CTA x takes rows x, x + gridDim.x, ..., its threads the columns; the
+// maximum is kept on the bit patterns (integer instructions, no FP64).
+template <typename TW, typename TI>
+__device__ __forceinline__ unsigned long long init_rows(const InvDesc& d, const TI* __restrict__ src, TW* w) {
+  const int b = d.b;
+  unsigned long long m = 0;
+  for (int r = blockIdx.x; r < b; r += gridDim.x) {
+    const TI* s = src + (int64_t)r * d.lds;
+    TW* o = w + (int64_t)r * b;
+    for (int c = threadIdx.x; c < b; c += blockDim.x) {
+      const double v = (double)s[c];
+      o[c] = (TW)v;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+      m = a > m ? a : m;
+    }
+  }
+  return m;
+}
+
 template <typename TW>
 __global__ void gj_init_kernel(const InvDesc* __restrict__ descs, int in_dtype) {
   const InvDesc d = descs[blockIdx.y];
-  const int64_t nel = (int64_t)d.b * d.b;
   TW* w = (TW*)d.work;
-  double m = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nel; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / d.b, c = e % d.b;
-    const double v = load_as<double>(d.src, in_dtype, r * d.lds + c);
-    w[e] = (TW)v;
-    const double a = fabs(v);
-    if (!(a <= m)) m = a;
-  }
+  unsigned long long m = in_dtype == F64 ? init_rows<TW>(d, (const double*)d.src, w)
+                                         : init_rows<TW>(d, (const float*)d.src, w);
   for (int o = 16; o > 0; o >>= 1) {
-    const double x = __shfl_xor_sync(0xffffffffu, m, o);
-    if (!(x <= m)) m = x;
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+    m = x > m ? x : m;
   }
-  if ((threadIdx.x & 31) == 0) atomicMax(d.amax, (unsigned long long)__double_as_longlong(m));
+  if ((threadIdx.x & 31) == 0) atomicMax(d.amax, m);
 }
 
 // Pivot keys: the bit pattern of |x| orders like |x| for every non-NaN x, and
@@ -271,8 +277,10 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
     }
   }
   cluster.sync();  // every row exchange of the other columns is done
-  // W = X[J, :] (the trailing update reads the pivot rows of the other columns)
-  if (nb < b) {
+  // W = X[J, :] (the CUDA-core trailing update reads the pivot rows of the
+  // other columns from W; the tensor-core one packs them from X itself, where
+  // they stay unchanged until that pack)
+  if (nb < b && !active_only) {
     TW* W = (TW*)d.wrow;
     const int64_t tot = (int64_t)nb * b;
     const int64_t per = (tot + CL - 1) / CL;
@@ -323,8 +331,9 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const InvDesc* __restric
 
 // Descriptors of the tensor-core trailing update of panel [p, p + nb): the
 // panel columns T = X[:, J] as the left operand (by rows), the pivot rows
-// W = X[J, :] as the right one (by columns), out = X with the rows of J taking
-// no addend and the columns of J left alone.  A matrix past its last panel,
+// W = X[J, :] as the right one (by columns; read in place: the panel left
+// them there and nothing writes them before this pack), out = X with the rows
+// of J taking no addend and the columns of J left alone.  A matrix past its last panel,
 // or whose panel is the whole matrix, gets an empty problem.
 __global__ void gj_tc_setup_kernel(const InvDesc* __restrict__ descs, int count, int p, int nb,
                                    oz::PackDesc* __restrict__ pa, oz::PackDesc* __restrict__ pb,
@@ -337,7 +346,7 @@ __global__ void gj_tc_setup_kernel(const InvDesc* __restrict__ descs, int count,
   const bool live = w > 0 && w < b;
   double* X = (double*)d.work;
   pa[u] = oz::PackDesc{X + (live ? p : 0), b, live ? b : 0, live ? w : 0, 0, u};
-  pb[u] = oz::PackDesc{(const double*)d.wrow, b, live ? w : 0, live ? b : 0, 1, u};
+  pb[u] = oz::PackDesc{X + (live ? (int64_t)p * b : 0), b, live ? w : 0, live ? b : 0, 1, u};
   oz::Problem q{};
   q.a_slab = q.b_slab = u;
   q.cin = X;
@@ -411,13 +420,13 @@ TcLayout tc_layout(int bmax, int count) {
   return L;
 }
 
-// out[r][c] = X[r][col_of[c]], where col_of undoes the row interchanges as
-// column interchanges taken in reverse order.
-template <typename TW, typename TO>
-__global__ void gj_finalize_kernel(const InvDesc* __restrict__ descs, int rows_per_cta) {
+// The row interchanges perm[0..b) undone as column interchanges taken in
+// reverse order: perm is overwritten with col_of, the source column of every
+// output column (one CTA per matrix, once, instead of once per output CTA).
+__global__ void gj_colperm_kernel(const InvDesc* __restrict__ descs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* col_of = (int*)smem_raw;
-  const InvDesc d = descs[blockIdx.y];
+  const InvDesc d = descs[blockIdx.x];
   const int b = d.b;
   for (int c = threadIdx.x; c < b; c += blockDim.x) col_of[c] = c;
   __syncthreads();
@@ -431,6 +440,18 @@ __global__ void gj_finalize_kernel(const InvDesc* __restrict__ descs, int rows_p
       }
     }
   }
+  __syncthreads();
+  for (int c = threadIdx.x; c < b; c += blockDim.x) d.perm[c] = col_of[c];
+}
+
+// out[r][c] = X[r][col_of[c]] with col_of from gj_colperm_kernel (in perm).
+template <typename TW, typename TO>
+__global__ void gj_finalize_kernel(const InvDesc* __restrict__ descs, int rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* col_of = (int*)smem_raw;
+  const InvDesc d = descs[blockIdx.y];
+  const int b = d.b;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) col_of[c] = d.perm[c];
   __syncthreads();
   const TW* X = (const TW*)d.work;
   TO* out = (TO*)d.dst;
@@ -559,6 +580,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     const int rows = 8;
     dim3 g((b + rows - 1) / rows, count);
     const size_t sm = (size_t)b * sizeof(int);
+    gj_colperm_kernel<<<count, 128, sm, s>>>(d_desc);
+    ++nl;
     if (out_dtype == F64)
       gj_finalize_kernel<TW, double><<<g, 256, sm, s>>>(d_desc, rows);
     else
