@@ -30,9 +30,9 @@ METRIC = "inverse blocks/sec & GEMM % of tensor peak, mixed vs FP64 at ≤1e-10 
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
 # DRAM bytes per algorithmic flop of the FP64_TC panel factorisation, from one
 # ncu capture (profiles/gj_panel_kernel_fp64tc_b512_x300.md: a launch of 300
-# panels of 512 rows x 64 columns read and wrote 253.3 MB for 1.258 GFLOP).
+# panels of 512 rows x 64 columns read and wrote 99.4 MB for 1.258 GFLOP).
 # With 64 columns a panel's flops and its row traffic both grow with its rows.
-PANEL_DRAM_BYTES_PER_FLOP = 253.33e6 / (300 * 2 * 512 * 64 * 64)
+PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
 # The same for the FP64_TC trailing-update digit product (per FP64-equivalent
 # flop), from profiles/oz_gemm_kernel_trailing_update_b512_x300.md: one launch
 # updating 300 matrices of order 512 (panel of 64, 448 other columns) read
