@@ -38,6 +38,10 @@ PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
 # updating 300 matrices of order 512 (panel of 64, 448 other columns) read
 # and wrote 1.274 GB for 8.81 GFLOP.
 UPDATE_DRAM_BYTES_PER_FLOP = 1.274e9 / (300 * 2 * 512 * 64 * 448)
+# The same for the FP64_TC Schur products, from
+# profiles/oz_gemm_kernel_schur_products_n4096_k8.md: one launch of 7 products
+# of order 512 read and wrote 289.1 MB for 1.879 GFLOP.
+SCHUR_DRAM_BYTES_PER_FLOP = 289.07e6 / (7 * 2 * 512 ** 3)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
 
@@ -68,7 +72,7 @@ def parse():
     p.add_argument("--refine", type=int, default=None,
                    help="two-sided refinement steps (0 or 1); default 1 on fp64_tc and fp64, where it meets the "
                         "1e-10 target at k = 8, else 0")
-    p.add_argument("--together", type=int, default=32,
+    p.add_argument("--together", type=int, default=64,
                    help="run each step's blocks as independent runs, this many executed together level by level "
                         "in grouped launches (0: one run after the other)")
     p.add_argument("--matrix", default="uniform", choices=["uniform", "haar", "spd"])
@@ -512,6 +516,10 @@ def main():
             kernels[name]["traffic"] = PANEL_DRAM_BYTES_PER_FLOP * f["work"] / f["launches"]
             kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
                                                "scaled by algorithmic flops to the average launch")
+        if name == "oz_gemm_kernel" and f.get("launches"):
+            kernels[name]["traffic"] = SCHUR_DRAM_BYTES_PER_FLOP * agg["gemm_flops"] / f["launches"]
+            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one Schur-product "
+                                               "launch, scaled by algorithmic flops to the average launch")
         if name == "gj_trailing_update" and args.precision == "fp64_tc" and f.get("launches"):
             # one trailing update per panel launch; FP64-equivalent flops
             kernels[name]["traffic"] = UPDATE_DRAM_BYTES_PER_FLOP * agg["inv_update_flops"] / f["launches"]
