@@ -66,3 +66,47 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
     assert L.mbinv_create(ctypes.byref(h), 16, 4, 0, buf, 8, None) == mb.EINVAL
     assert L.mbinv_block(None, 0, 0, buf, 4, None) == mb.EINVAL
     assert L.mbinv_batched_blocks(-1, None, 0, None, None) == mb.EINVAL
+
+
+# C type of a header field -> the ctypes type its mirror must use
+_CTYPES = {"double": ctypes.c_double, "size_t": ctypes.c_size_t, "int64_t": ctypes.c_int64, "int": ctypes.c_int,
+           "uint64_t": ctypes.c_uint64, "mbinv_precision": ctypes.c_int}
+
+
+def header_struct(name):
+    """Fields (name, C type, array length) of `typedef struct {...} name;` in include/mbinv.h."""
+    text = open(os.path.join(ROOT, "include", "mbinv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        dm = re.match(r"(const\s+)?(\w+)\s*(\*?)\s*(.*)", decl)
+        ctype, ptr, names = dm.group(2), dm.group(3), dm.group(4)
+        for nm in names.split(","):
+            nm = nm.strip()
+            star = ptr or nm.startswith("*")
+            nm = nm.lstrip("*").strip()
+            am = re.match(r"(\w+)\[(\d+)\]", nm)
+            fields.append((am.group(1) if am else nm, "void*" if star else ctype, int(am.group(2)) if am else 1))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("mbinv_report", "Report"), ("mbinv_options", "Options"),
+                                          ("mbinv_problem", "Problem")])
+def test_binding_structs_match_header(cname, pyname):
+    """The ctypes mirrors declare the header's fields in the header's order
+    with the same types (a drifted struct would shift every later field)."""
+    import paper_1612_00001_gb300 as mb
+    py = getattr(mb, pyname)._fields_
+    hdr = header_struct(cname)
+    assert [f[0] for f in py] == [h[0] for h in hdr], (cname, [f[0] for f in py], [h[0] for h in hdr])
+    for (fname, ftype), (hname, htype, count) in zip(py, hdr):
+        want = ctypes.c_void_p if htype == "void*" else _CTYPES[htype]
+        if count > 1:
+            want = want * count
+        assert ctypes.sizeof(ftype) == ctypes.sizeof(want) and getattr(ftype, "_type_", None) == getattr(
+            want, "_type_", None), (cname, fname, ftype, htype)
