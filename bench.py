@@ -128,12 +128,13 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = None  # samples go to a temporary file, summarised by stop()
 
     def start(self):
+        import tempfile
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"mbinv_clocks{self.idx}_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
@@ -142,6 +143,7 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            self._remove()
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
@@ -149,6 +151,21 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
+        try:
+            return self._summary()
+        finally:
+            self._remove()
+
+    def _remove(self):
+        try:
+            if getattr(self, "f", None) is not None and not self.f.closed:
+                self.f.close()
+            if self.path:
+                os.remove(self.path)
+        except OSError:
+            pass
+
+    def _summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
