@@ -122,13 +122,13 @@ __device__ __forceinline__ void warp_argmax(long long& key, int& row) {
 }
 
 // A cluster of CL CTAs per matrix factors the panel [p, p + nb) (see the file
-// comment).  CTA q of the cluster keeps rows [q R, (q+1) R) of the panel in
-// its shared memory (R = ceil(b / CL)); the CTAs exchange pivot candidates
-// and the pivot row through distributed shared memory, so that the
-// per-column work (the elimination of nb columns from every row) is spread
-// over CL SMs instead of one.  Every warp of every CTA takes the same pivot
-// decision from the same candidates, so one column costs two CTA barriers and
-// two cluster barriers.
+// comment).  CTA q of the cluster keeps rows [row0 + q R, row0 + (q+1) R) of
+// the panel in its shared memory (R = ceil((b - row0) / CL)); the CTAs
+// exchange pivot candidates and the pivot row through distributed shared
+// memory, so that the per-column work (the elimination of nb columns from
+// every row) is spread over CL SMs instead of one.  Every warp of every CTA
+// takes the same pivot decision from the same candidates, so one column costs
+// two CTA barriers and two cluster barriers (CTA barriers when CL = 1).
 template <typename TW>
 __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* __restrict__ descs, int p, int nb,
                                                                  DevStatus* status, int active_only) {
