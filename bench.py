@@ -95,6 +95,85 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def roofline_of(args, agg, secs):
+    """The roofline of each kernel family from the step aggregates (algorithmic
+    work / device time against its peak, DRAM traffic per launch where an ncu
+    capture gives bytes per flop); the dominant family (most device time)
+    heads the result, the others are under "families"."""
+    pk, pk_src = peaks()
+    npairs = {1: 1, 2: 3, 3: 6}[args.slices] if args.precision == "mixed" else 1
+    alu = {"fp64": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
+           "fp32": (FP32_NOMINAL_GFLOPS / 1e3, "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+           "mixed": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
+           "fp64_tc": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)")}[args.precision]
+    fams = {}
+    tc_src = f"bf16_tflops_sustained ({pk_src})"
+    if args.precision == "mixed":
+        fams["tc_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * npairs,
+                                  "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
+                                  "peak": pk["bf16_tflops_sustained"],
+                                  "peak_source": f"{tc_src}, executed BF16 slice products"}
+    elif args.precision == "fp64_tc":
+        fams["oz_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * DIGIT_PAIRS,
+                                  "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
+                                  "peak": pk["bf16_tflops_sustained"],
+                                  "peak_source": f"{tc_src}, executed BF16 digit-pair products "
+                                                 f"({DIGIT_PAIRS} per FP64 product); Schur products only"}
+    else:
+        fams["gemm_grouped_kernel"] = {"bound": "alu", "work": agg["gemm_flops"], "dsec": agg["gemm_device_seconds"],
+                                       "launches": agg["gemm_launches"], "peak": alu[0], "peak_source": alu[1]}
+    fp_peak = alu
+    fams["gj_panel_kernel"] = {"bound": "alu", "work": agg["inv_panel_flops"],
+                               "dsec": agg["inv_panel_device_seconds"], "launches": agg["inv_panel_launches"],
+                               "peak": fp_peak[0], "peak_source": fp_peak[1] + "; panel factorisations, 2 b w^2 "
+                                                                  "flop per panel of width w"}
+    upd_dsec = agg["inv_device_seconds"] - agg["inv_panel_device_seconds"]
+    if args.precision == "fp64_tc":
+        fams["gj_trailing_update"] = {"bound": "tensor", "work": agg["inv_update_flops"] * DIGIT_PAIRS,
+                                      "dsec": upd_dsec, "launches": agg["inv_panel_launches"],
+                                      "peak": pk["bf16_tflops_sustained"],
+                                      "peak_source": f"{tc_src}, executed digit-pair products of the trailing "
+                                                     "updates; time includes their digit packs and the inverses' "
+                                                     "init/finalize"}
+    else:
+        fams["gj_trailing_update"] = {"bound": "alu", "work": agg["inv_update_flops"], "dsec": upd_dsec,
+                                      "launches": None, "peak": fp_peak[0],
+                                      "peak_source": fp_peak[1] + "; gj_update_kernel, time includes the "
+                                                                  "inverses' init/finalize"}
+    kernels = {}
+    for name, f in fams.items():
+        ach = f["work"] / f["dsec"] / 1e12 if f["dsec"] > 0 else 0.0
+        kernels[name] = {"bound": f["bound"], "achieved": ach, "peak": f["peak"], "unit": "TFLOP/s",
+                         "frac": ach / f["peak"], "device_seconds": f["dsec"], "peak_source": f["peak_source"]}
+        if f.get("launches"):
+            kernels[name]["launches"] = f["launches"]
+        if name == "gj_panel_kernel" and args.precision == "fp64_tc" and f.get("launches"):
+            # DRAM bytes of an average launch (ncu bytes per flop x its flops)
+            kernels[name]["traffic"] = PANEL_DRAM_BYTES_PER_FLOP * f["work"] / f["launches"]
+            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                                               "scaled by algorithmic flops to the average launch")
+        if name == "oz_gemm_kernel" and f.get("launches"):
+            kernels[name]["traffic"] = SCHUR_DRAM_BYTES_PER_FLOP * agg["gemm_flops"] / f["launches"]
+            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one Schur-product "
+                                               "launch, scaled by algorithmic flops to the average launch")
+        if name == "gj_trailing_update" and args.precision == "fp64_tc" and f.get("launches"):
+            # one trailing update per panel launch; FP64-equivalent flops
+            kernels[name]["traffic"] = UPDATE_DRAM_BYTES_PER_FLOP * agg["inv_update_flops"] / f["launches"]
+            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one trailing-"
+                                               "update oz_gemm_kernel launch, scaled by algorithmic flops to the "
+                                               "average update (its digit packs and done-rows products excluded)")
+        if args.precision == "fp64_tc" and f["bound"] == "tensor":
+            kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
+    if agg["pack_device_seconds"] > 0:
+        kernels["operand_packing"] = {"device_seconds": agg["pack_device_seconds"],
+                                      "note": "digit or slice packing of the Schur operands (HBM/L2 bound)"}
+    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: kernels[k]["device_seconds"])
+    roofline = dict(kernels[dom])
+    roofline.update({"kernel": dom, "traffic": kernels[dom].get("traffic"), "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
+                     "families": kernels})
+    return roofline
+
+
 def make_matrix(args, n):
     import bri_inputs as bi
     if args.matrix == "haar":
@@ -480,78 +559,7 @@ def main():
             ref64 = c64.block(i0, j0).double().cpu().numpy()
         diff_fp64 = float(np.linalg.norm(outs[0].double().cpu().numpy() - ref64) / np.linalg.norm(ref64))
 
-    # roofline of each kernel family; the dominant one (most device time) heads the line
-    pk, pk_src = peaks()
-    npairs = {1: 1, 2: 3, 3: 6}[args.slices] if args.precision == "mixed" else 1
-    alu = {"fp64": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
-           "fp32": (FP32_NOMINAL_GFLOPS / 1e3, "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
-           "mixed": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)"),
-           "fp64_tc": (FP64_NOMINAL_GFLOPS / 1e3, "nominal FP64 1.25 TFLOP/s (DFMA)")}[args.precision]
-    fams = {}
-    tc_src = f"bf16_tflops_sustained ({pk_src})"
-    if args.precision == "mixed":
-        fams["tc_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * npairs,
-                                  "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
-                                  "peak": pk["bf16_tflops_sustained"],
-                                  "peak_source": f"{tc_src}, executed BF16 slice products"}
-    elif args.precision == "fp64_tc":
-        fams["oz_gemm_kernel"] = {"bound": "tensor", "work": agg["gemm_flops"] * DIGIT_PAIRS,
-                                  "dsec": agg["gemm_device_seconds"], "launches": agg["gemm_launches"],
-                                  "peak": pk["bf16_tflops_sustained"],
-                                  "peak_source": f"{tc_src}, executed BF16 digit-pair products "
-                                                 f"({DIGIT_PAIRS} per FP64 product); Schur products only"}
-    else:
-        fams["gemm_grouped_kernel"] = {"bound": "alu", "work": agg["gemm_flops"], "dsec": agg["gemm_device_seconds"],
-                                       "launches": agg["gemm_launches"], "peak": alu[0], "peak_source": alu[1]}
-    fp_peak = alu
-    fams["gj_panel_kernel"] = {"bound": "alu", "work": agg["inv_panel_flops"],
-                               "dsec": agg["inv_panel_device_seconds"], "launches": agg["inv_panel_launches"],
-                               "peak": fp_peak[0], "peak_source": fp_peak[1] + "; panel factorisations, 2 b w^2 "
-                                                                  "flop per panel of width w"}
-    upd_dsec = agg["inv_device_seconds"] - agg["inv_panel_device_seconds"]
-    if args.precision == "fp64_tc":
-        fams["gj_trailing_update"] = {"bound": "tensor", "work": agg["inv_update_flops"] * DIGIT_PAIRS,
-                                      "dsec": upd_dsec, "launches": agg["inv_panel_launches"],
-                                      "peak": pk["bf16_tflops_sustained"],
-                                      "peak_source": f"{tc_src}, executed digit-pair products of the trailing "
-                                                     "updates; time includes their digit packs and the inverses' "
-                                                     "init/finalize"}
-    else:
-        fams["gj_trailing_update"] = {"bound": "alu", "work": agg["inv_update_flops"], "dsec": upd_dsec,
-                                      "launches": None, "peak": fp_peak[0],
-                                      "peak_source": fp_peak[1] + "; gj_update_kernel, time includes the "
-                                                                  "inverses' init/finalize"}
-    kernels = {}
-    for name, f in fams.items():
-        ach = f["work"] / f["dsec"] / 1e12 if f["dsec"] > 0 else 0.0
-        kernels[name] = {"bound": f["bound"], "achieved": ach, "peak": f["peak"], "unit": "TFLOP/s",
-                         "frac": ach / f["peak"], "device_seconds": f["dsec"], "peak_source": f["peak_source"]}
-        if f.get("launches"):
-            kernels[name]["launches"] = f["launches"]
-        if name == "gj_panel_kernel" and args.precision == "fp64_tc" and f.get("launches"):
-            # DRAM bytes of an average launch (ncu bytes per flop x its flops)
-            kernels[name]["traffic"] = PANEL_DRAM_BYTES_PER_FLOP * f["work"] / f["launches"]
-            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                                               "scaled by algorithmic flops to the average launch")
-        if name == "oz_gemm_kernel" and f.get("launches"):
-            kernels[name]["traffic"] = SCHUR_DRAM_BYTES_PER_FLOP * agg["gemm_flops"] / f["launches"]
-            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one Schur-product "
-                                               "launch, scaled by algorithmic flops to the average launch")
-        if name == "gj_trailing_update" and args.precision == "fp64_tc" and f.get("launches"):
-            # one trailing update per panel launch; FP64-equivalent flops
-            kernels[name]["traffic"] = UPDATE_DRAM_BYTES_PER_FLOP * agg["inv_update_flops"] / f["launches"]
-            kernels[name]["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one trailing-"
-                                               "update oz_gemm_kernel launch, scaled by algorithmic flops to the "
-                                               "average update (its digit packs and done-rows products excluded)")
-        if args.precision == "fp64_tc" and f["bound"] == "tensor":
-            kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
-    if agg["pack_device_seconds"] > 0:
-        kernels["operand_packing"] = {"device_seconds": agg["pack_device_seconds"],
-                                      "note": "digit or slice packing of the Schur operands (HBM/L2 bound)"}
-    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: kernels[k]["device_seconds"])
-    roofline = dict(kernels[dom])
-    roofline.update({"kernel": dom, "traffic": kernels[dom].get("traffic"), "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
-                     "families": kernels})
+    roofline = roofline_of(args, agg, secs)
 
     line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
