@@ -205,3 +205,26 @@ def test_refinement_reaches_1e10_at_k8(mb, prec):
         ref = inv[i * b:(i + 1) * b, j * b:(j + 1) * b]
         e0, e1 = oracle.rel_fro(p0, ref), oracle.rel_fro(r1, ref)
         assert e1 <= 1e-10 and e1 <= e0 / 100, (i, j, e0, e1)
+
+
+def test_full_size_bench_configuration(mb):
+    """n = 4096, k = 8 (b = 512) in the bench's launch configuration: all 64
+    blocks as independent runs executed together, one refinement step.  Every
+    block within 1e-10 of the dense inverse; a sampled block against the
+    oracle, which itself sits its own recursion error away from the dense
+    inverse: the two may differ by no more than that error and the 1e-10 bar."""
+    n, k = 4096, 8
+    b = n // k
+    m = bi.uniform_shift(n, 0)
+    ij = [(i, j) for i in range(k) for j in range(k)]
+    with mb.Context(dev(m), k, precision=P, refine=1) as ctx:
+        outs = [to_np(x) for x in ctx.blocks(ij, width=len(ij))]
+    inv = np.linalg.inv(m)
+    errs = {(i, j): oracle.rel_fro(o, inv[i * b:(i + 1) * b, j * b:(j + 1) * b]) for (i, j), o in zip(ij, outs)}
+    worst = max(errs.values())
+    assert worst <= 1e-10, (worst, max(errs, key=errs.get))
+    i, j = 3, 5
+    ref = oracle_block(m, k, i, j)
+    e_oracle = oracle.rel_fro(ref, inv[i * b:(i + 1) * b, j * b:(j + 1) * b])
+    got = outs[ij.index((i, j))]
+    assert oracle.rel_fro(got, ref) <= e_oracle + 2e-10, (oracle.rel_fro(got, ref), e_oracle)
