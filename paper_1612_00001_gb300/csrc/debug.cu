@@ -6,6 +6,7 @@
 
 #include <vector>
 
+#include "mbinv_internal.h"
 #include "ozaki.h"
 #include "tc_gemm.h"
 
@@ -154,4 +155,26 @@ extern "C" int mbinv_debug_oz_gemm(const double* A, const double* B, const doubl
   cudaFree(dp);
   cudaFree(derr);
   return rc;
+}
+
+// Host-only hook of the planner (no CUDA call): for block (i, j) of a k x k
+// grid, out[0] distinct frames, out[1] order-2 (leaf) frames, out[2] inverses
+// of the schedule (distinct pivots plus the root), out[3] peak value slots,
+// out[4] product work and out[5] inverse work, both in units of b^3 (2 per
+// b x b x b product, 2 per b x b inverse).  0, or -1 for invalid arguments.
+extern "C" int mbinv_debug_plan(int k, int i, int j, int pad_last, double* out) {
+  if (k < 1 || i < 0 || j < 0 || i >= k || j >= k || !out) return -1;
+  try {
+    const Plan P = build_plan(k, i, j, pad_last != 0);
+    const Schedule S = build_schedule(P, 0);
+    out[0] = (double)S.frames;
+    out[1] = (double)P.leaves;
+    out[2] = (double)S.inversions;
+    out[3] = (double)S.nslots;
+    out[4] = S.gemm_flops_units;
+    out[5] = S.inv_units;
+  } catch (...) {
+    return -1;
+  }
+  return 0;
 }
