@@ -80,3 +80,20 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     c.start()
     r = c.stop()
     assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` times the oracle on the host and prints one
+    JSON line with the same metric and unit, marked as the reference."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "256", "--k",
+                          "4", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300,
+                         cwd=ROOT, check=True).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "blocks/s"
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "blocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
