@@ -336,8 +336,9 @@ def test_augmented_matrix_larger_k(n, k):
         assert st == oracle.OK, (i, j)
         r0, r1 = i * b, min((i + 1) * b, n)
         c0, c1 = j * b, min((j + 1) * b, n)
-        # the recursion's own rounding sensitivity grows with k (1e-10 at k = 8)
-        bound = 1e-11 + 100 * oracle.sensitivity_floor(g, k, i, j, pad_last=True)
+        # the parity rule against truth: the fixed bar plus 10 x the recursion's
+        # own rounding sensitivity, which grows with k (1e-10 at k = 8)
+        bound = 1e-11 + 10 * oracle.sensitivity_floor(g, k, i, j, pad_last=True)
         assert oracle.rel_fro(n_ij[:r1 - r0, :c1 - c0], ref[r0:r1, c0:c1]) < bound, (i, j)
     g, _, _ = oracle.augment(m, k)
     _, st, _ = oracle.bri_block(g, k, 0, 1, pad_last=False)
@@ -386,4 +387,72 @@ def test_adjoint_against_central_differences():
 
 def test_sensitivity_floor_small_for_dominant_matrix():
     m = bi.uniform_shift(64, 1)
-    assert oracle.sensitivity_floor(m, 4, 0, 0) < 1e-14
+    f = oracle.sensitivity_floor(m, 4, 0, 0)
+    assert 0.0 < f < 1e-14
+
+
+def _scalar_floor(a, b_, c, d):
+    """The floor of the k = 2, b = 1 case written out in IEEE double (Python
+    floats, one rounding per operation, no fused multiply-add): the root is
+    the leaf a - b d^-1 c (Eq. invSchur, E = (A - B D^-1 C)^-1), evaluated as
+    b * (d^-1 * c) and as (b * d^-1) * c; N_00 is the inverse of each."""
+    dinv = 1.0 / d
+    n1 = 1.0 / (a - b_ * (dinv * c))
+    n2 = 1.0 / (a - (b_ * dinv) * c)
+    return abs(n2 - n1) / abs(n1), n1
+
+
+def test_sensitivity_floor_pinned_on_scalars():
+    """k = 2 with b = 1: every step of both evaluation orders is a single
+    IEEE operation, so the floor is fixed by the arithmetic itself.  It must
+    equal the written-out relative difference exactly, be nonzero where the
+    two orders round differently, and be exactly zero where every operation
+    is exact."""
+    found_nonzero = 0
+    for t in range(40):
+        v = bi.uniform_pm1(77, t, 4)
+        b_, c, d = float(v[1]) + 2.0, float(v[2]) + 2.0, float(v[3]) + 4.0
+        # a close to b c / d: the difference cancels, so a rounding of the
+        # product shows in N_00
+        a = b_ * c / d + 1e-3 * float(v[0])
+        m = np.array([[a, b_], [c, d]])
+        want, n00 = _scalar_floor(a, b_, c, d)
+        got, st, _ = oracle.bri_block(m, 2, 0, 0)
+        assert st == oracle.OK and got[0, 0] == n00
+        assert oracle.sensitivity_floor(m, 2, 0, 0) == want
+        found_nonzero += want > 0.0
+    # the re-association really rounds differently on generic inputs
+    assert found_nonzero >= 10
+    # small integers and a power-of-two pivot: every product and difference
+    # is exact in both orders, so the floor is exactly zero
+    m = np.array([[7.0, 3.0], [5.0, 4.0]])
+    assert oracle.sensitivity_floor(m, 2, 0, 0) == 0.0
+
+
+def test_sensitivity_floor_zero_when_products_are_exact():
+    """k = 4, b = 2, block upper triangular with power-of-two diagonal blocks
+    and small integers above: every pivot inverse and every Schur product is
+    exact in either order, so the two evaluations agree bit for bit (floor
+    exactly zero) and equal the dense inverse; strictly lower requests are
+    structurally singular (Sec. 1: the inverted submatrices must be
+    nonsingular)."""
+    b, k = 2, 4
+    m = np.zeros((k * b, k * b))
+    for t in range(k):
+        m[t * b:(t + 1) * b, t * b:(t + 1) * b] = np.diag([2.0 ** (t + 1), 2.0 ** t])
+    ints = [1.0, -2.0, 3.0, 1.0, -1.0, 2.0]
+    q = 0
+    for r in range(k):
+        for c in range(r + 1, k):
+            m[r * b, c * b + 1] = ints[q % 6]
+            m[r * b + 1, c * b] = ints[(q + 1) % 6]
+            q += 1
+    inv = np.linalg.inv(m)
+    for i, j in [(0, 0), (0, 2), (1, 2), (1, 3), (3, 3)]:
+        n_ij, st, _ = oracle.bri_block(m, k, i, j)
+        assert st == oracle.OK
+        assert np.allclose(n_ij, inv[i * b:(i + 1) * b, j * b:(j + 1) * b], rtol=0, atol=1e-15), (i, j)
+        assert oracle.sensitivity_floor(m, k, i, j) == 0.0, (i, j)
+    # a generic perturbation of the same matrix makes it nonzero
+    m2 = m + 1e-3 * bi.uniform_pm1(5, 0, (k * b) ** 2).reshape(k * b, k * b)
+    assert oracle.sensitivity_floor(m2, k, 1, 2) > 0.0

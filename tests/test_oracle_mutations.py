@@ -57,7 +57,7 @@ def _bind(L):
 
 def build_mutant(tmp, name):
     text = open(SRC).read()
-    old, new = MUTATIONS[name]
+    old, new = {**MUTATIONS, **FLOOR_MUTATIONS}[name]
     assert old in text, f"mutation site of {name} not found"
     src = os.path.join(tmp, f"{name}.c")
     open(src, "w").write(text.replace(old, new, 1))
@@ -139,6 +139,40 @@ def pins_pass(L):
     return True
 
 
+# Mistakes in the re-associated evaluation that the sensitivity floor rests on
+# (the parity rule's 10 x floor): the scalar pin of the floor must fail.
+FLOOR_MUTATIONS = {
+    # the re-associated order silently evaluated like the plain one
+    "reassoc_ignored": ("if (!R->reassoc) {", "if (1) {"),
+}
+
+
+def floor_pins_pass(L):
+    """k = 2, b = 1: the floor written out in IEEE double (see
+    tests/test_oracle.py) against the mutant's two evaluation orders."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    nonzero = 0
+    for t in range(40):
+        v = bi.uniform_pm1(77, t, 4)
+        b_, c, d = float(v[1]) + 2.0, float(v[2]) + 2.0, float(v[3]) + 4.0
+        a = b_ * c / d + 1e-3 * float(v[0])
+        dinv = 1.0 / d
+        n1 = 1.0 / (a - b_ * (dinv * c))
+        n2 = 1.0 / (a - (b_ * dinv) * c)
+        m = np.ascontiguousarray(np.array([[a, b_], [c, d]]))
+        got = []
+        for reassoc in (0, 1):
+            out = np.empty((1, 1))
+            stats = (ctypes.c_int64 * 4)()
+            if L.orc_bri_block(m.ctypes.data_as(dp), 2, 2, 1, 0, 0, 1, reassoc, 0, out.ctypes.data_as(dp), stats):
+                return False
+            got.append(out[0, 0])
+        if got[0] != n1 or got[1] != n2:
+            return False
+        nonzero += n1 != n2
+    return nonzero >= 10
+
+
 @pytest.fixture(scope="module")
 def tmpdir_():
     d = tempfile.mkdtemp(prefix="oracle_mut_")
@@ -153,9 +187,16 @@ def test_unmutated_copy_passes(tmpdir_):
     so = os.path.join(tmpdir_, "clean.so")
     subprocess.run(["gcc", "-O1", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", src, "-o", so, "-lm"],
                    check=True)
-    assert pins_pass(_bind(ctypes.CDLL(so)))
+    L = _bind(ctypes.CDLL(so))
+    assert pins_pass(L)
+    assert floor_pins_pass(L)
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(tmpdir_, name):
     assert not pins_pass(build_mutant(tmpdir_, name)), f"mutation {name} survived the pins"
+
+
+@pytest.mark.parametrize("name", sorted(FLOOR_MUTATIONS))
+def test_planted_floor_mistake_is_caught(tmpdir_, name):
+    assert not floor_pins_pass(build_mutant(tmpdir_, name)), f"mutation {name} survived the floor pin"
