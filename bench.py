@@ -39,9 +39,10 @@ PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
 # and wrote 1.274 GB for 8.81 GFLOP.
 UPDATE_DRAM_BYTES_PER_FLOP = 1.274e9 / (300 * 2 * 512 * 64 * 448)
 # The same for the FP64_TC Schur products, from
-# profiles/oz_gemm_kernel_schur_products_n4096_k8.md: one launch of 7 products
-# of order 512 read and wrote 289.1 MB for 1.879 GFLOP.
-SCHUR_DRAM_BYTES_PER_FLOP = 289.07e6 / (7 * 2 * 512 ** 3)
+# profiles/oz_gemm_kernel_schur_products_n4096_k8_together4.md: two grouped
+# launches of 400 products of order 512 each (84 waves) read and wrote
+# 1.936 GB and 4.033 GB - the algorithmic bytes of their distinct operands.
+SCHUR_DRAM_BYTES_PER_FLOP = (1.128e9 + 0.808e9 + 3.206e9 + 0.827e9) / (800 * 2 * 512 ** 3)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
 
@@ -64,7 +65,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-check", action="store_true",
-                   help="skip the comparison of the last block with the plain FP64 path (fp64_tc)")
+                   help="skip the plain FP64 arm (fp64_tc): its blocks/s on the same step and the distance of the "
+                        "last step's first block to it")
     p.add_argument("--inverses", type=int, default=0,
                    help="time this many independent pivoted inverses of order n (k = 1) in one batch")
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
@@ -163,15 +165,58 @@ def roofline_of(args, agg, secs):
                                                "update oz_gemm_kernel launch, scaled by algorithmic flops to the "
                                                "average update (its digit packs and done-rows products excluded)")
         if args.precision == "fp64_tc" and f["bound"] == "tensor":
+            # the method's own work: FP64-equivalent flops, against the BF16
+            # rate the kernel runs on and against GB300's nominal FP64 rate
             kernels[name]["fp64_equivalent_tflops"] = ach / DIGIT_PAIRS
+            kernels[name]["frac_fp64_equivalent_of_bf16"] = ach / DIGIT_PAIRS / f["peak"]
+            kernels[name]["x_nominal_fp64"] = ach / DIGIT_PAIRS / (FP64_NOMINAL_GFLOPS / 1e3)
     if agg["pack_device_seconds"] > 0:
-        kernels["operand_packing"] = {"device_seconds": agg["pack_device_seconds"],
-                                      "note": "digit or slice packing of the Schur operands (HBM/L2 bound)"}
-    dom = max((k for k in kernels if "bound" in kernels[k]), key=lambda k: kernels[k]["device_seconds"])
+        gbs = agg.get("pack_bytes", 0.0) / agg["pack_device_seconds"] / 1e9
+        kernels["oz_pack_kernel" if args.precision == "fp64_tc" else "pack_kernel"] = {
+            "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "device_seconds": agg["pack_device_seconds"],
+            "peak_source": f"hbm_gbs ({pk_src}); algorithmic bytes: each operand entry read once, its digits "
+                           "(or slices) written once, one exponent per row"}
+    dom = max((k for k in kernels if "bound" in kernels[k] and kernels[k]["unit"] == "TFLOP/s"),
+              key=lambda k: kernels[k]["device_seconds"])
     roofline = dict(kernels[dom])
     roofline.update({"kernel": dom, "traffic": kernels[dom].get("traffic"), "step_tflops": (agg["gemm_flops"] + agg["inv_flops"]) / secs / 1e12,
                      "families": kernels})
     return roofline
+
+
+def fp64_path_arm(args, M, k, b, bps, rank, world, first_block, m_host):
+    """The plain FP64 path (CUDA-core products and inverses) on the bench's
+    step: one untimed step, then one step timed with CUDA events; its blocks/s,
+    its error against the dense inverse, and how far the headline path's first
+    block of the last step lies from the FP64 path's."""
+    import numpy as np
+    import torch
+
+    import paper_1612_00001_gb300 as mb
+    stream = torch.cuda.current_stream()
+    outs = [torch.empty((b, b), dtype=torch.float64, device="cuda") for _ in range(bps)]
+    last = args.warmup + args.steps - 1
+    ij = rank_blocks(k, rank, world, last, bps)
+    with mb.Context(M, k, precision="fp64", refine=args.refine) as c64:
+        c64.blocks(ij, outs=outs, width=args.together or 1)  # untimed: plans and workspace
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c64.blocks(ij, outs=outs, width=args.together or 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    inv = np.linalg.inv(m_host)
+    errs = []
+    for q, (i, j) in enumerate(ij):
+        r = inv[i * b:(i + 1) * b, j * b:(j + 1) * b]
+        errs.append(float(np.linalg.norm(outs[q].double().cpu().numpy() - r) / np.linalg.norm(r)))
+    ref64 = outs[0].double().cpu().numpy()
+    diff = float(np.linalg.norm(first_block.double().cpu().numpy() - ref64) / np.linalg.norm(ref64))
+    return {"value": bps / secs, "unit": "blocks/s", "ms_per_step": 1e3 * secs, "steps": 1,
+            "max_rel_err_vs_dense_inverse": max(errs), "refine": args.refine,
+            "rel_diff_of_headline_block": diff}
 
 
 def make_matrix(args, n):
@@ -522,7 +567,7 @@ def main():
     agg = {"gemm_flops": 0.0, "inv_flops": 0.0, "gemm_device_seconds": 0.0, "inv_device_seconds": 0.0,
            "launches": 0, "gemm_launches": 0, "inversions": 0, "peak_device_bytes": 0,
            "pack_device_seconds": 0.0, "inv_panel_device_seconds": 0.0, "inv_panel_flops": 0.0,
-           "inv_update_flops": 0.0, "inv_panel_launches": 0}
+           "inv_update_flops": 0.0, "inv_panel_launches": 0, "pack_bytes": 0.0, "frames": 0, "request_frames": 0}
     torch.cuda.synchronize()
     for s in range(args.steps):
         flush.fill_(s & 0xFF)  # L2 flush, outside the timed interval
@@ -551,14 +596,11 @@ def main():
         r = inv_ref[i * b:(i + 1) * b, j * b:(j + 1) * b]
         errs.append(float(np.linalg.norm(outs[q].double().cpu().numpy() - r) / np.linalg.norm(r)))
     del inv_ref
-    # the same block on the plain FP64 CUDA-core path: how far the tensor-core path is from it
-    diff_fp64 = None
+    # the plain FP64 CUDA-core path on the same step (same blocks, same
+    # refinement, same runs merged): the "mixed vs FP64" half of the metric
+    fp64_arm = None
     if args.precision == "fp64_tc" and not args.no_fp64_check:
-        i0, j0 = rank_blocks(k, rank, world, args.warmup + args.steps - 1, bps)[0]
-        with mb.Context(M, k, precision="fp64", refine=args.refine) as c64:
-            ref64 = c64.block(i0, j0).double().cpu().numpy()
-        diff_fp64 = float(np.linalg.norm(outs[0].double().cpu().numpy() - ref64) / np.linalg.norm(ref64))
-
+        fp64_arm = fp64_path_arm(args, M, k, b, bps, rank, world, outs[0], m_host)
     roofline = roofline_of(args, agg, secs)
 
     line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
@@ -571,7 +613,10 @@ def main():
                        "refine": args.refine,
                        "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",
                        "max_rel_err_vs_dense_inverse": max(errs),
-                       "rel_diff_vs_fp64_path": diff_fp64},
+                       "frames_evaluated_per_step": agg["frames"] // args.steps,
+                       "frames_of_the_runs_alone_per_step": agg["request_frames"] // args.steps},
+            "fp64_path": fp64_arm,
+            "speedup_vs_fp64_path": (value / fp64_arm["value"]) if fp64_arm else None,
             "roofline": roofline, "gpu_launches": agg["launches"],
             "peak_device_bytes": agg["peak_device_bytes"], "clocks": clk}
     ctx.close()

@@ -96,8 +96,13 @@ typedef struct {
     double inv_flops;           /* 2 b^3 per b x b inverse */
     double seconds;             /* wall time of the call */
     double rel_residual;        /* refined path: ||E_i^T - X_i M||_F / sqrt(b) */
-    size_t peak_device_bytes;   /* planned high-water mark of the workspace */
-    size_t frames;              /* distinct frames evaluated */
+    size_t peak_device_bytes;   /* high-water mark of the library's device
+                                   memory during the call: the bytes it held
+                                   allocated (its copy of M included),
+                                   counted at every allocation and free */
+    size_t frames;              /* frames evaluated: frames that compute the
+                                   same value are evaluated once for all the
+                                   requests of a call (see request_frames) */
     size_t inversions;          /* b x b inverses performed */
     size_t launches;            /* kernel launches issued */
     int64_t failed_pivot;       /* on MBINV_ESINGULAR: index of the failing
@@ -121,6 +126,14 @@ typedef struct {
                                    inv_panel_flops, 2 b^3 per inverse) */
     size_t inv_panel_launches;  /* profile = 1: panel factorisation launches
                                    timed in inv_panel_device_seconds */
+    size_t request_frames;      /* frames the requests would evaluate run
+                                   one by one (each request's own distinct
+                                   frames, summed); frames <= request_frames */
+    size_t planned_device_bytes; /* the planner's reckoning of the same
+                                   high-water mark, made before any launch */
+    double pack_bytes;          /* algorithmic bytes of operand packing:
+                                   FP64_TC 8 B read and 16 B of digits
+                                   written per operand entry, 4 B per row */
 } mbinv_report;
 
 typedef struct mbinv_ctx mbinv_ctx;
@@ -172,21 +185,29 @@ mbinv_status mbinv_create(mbinv_ctx **out, int64_t n, int64_t k, int dtype, cons
 mbinv_status mbinv_block(mbinv_ctx *ctx, int64_t i, int64_t j, void *out, int64_t ldo, mbinv_report *report);
 
 /* Several blocks of M^-1, each by its own run of the recursion (Sec. 3.1-3.2,
- * the k^2-runs reading of Sec. 5), the runs executed together: step t of every
- * run goes out in the same grouped launches (the blocks are independent,
- * Sec. 8).  ij holds count pairs (i, j); outs[t] (host or device, M's dtype)
- * receives block (ij[2t], ij[2t+1]) with leading dimension ldos[t].  width
- * bounds how many runs go together (0 = 8), and the cap may lower it.  With
- * refine_steps = 1 every block is refined as in mbinv_block, each needed
- * block row and column computed once (their runs width together). */
+ * the k^2-runs reading of Sec. 5), the runs executed together.  Their frames
+ * are merged by what they compute - a frame that several runs (or several
+ * branches of one run) compute from the same operand frames is evaluated
+ * once, the reuse across branches that Sec. 8 proposes - and every level of
+ * the merged recursion goes out in grouped launches.  A merged frame rounds
+ * exactly as in each run alone, so every block equals, bit for bit, the block
+ * its run alone returns.  ij holds count pairs (i, j); outs[t] (host or
+ * device, M's dtype) receives block (ij[2t], ij[2t+1]) with leading dimension
+ * ldos[t].  width bounds how many runs are merged (0 = 8), and the cap may
+ * lower it.  With refine_steps = 1 every block is refined as in mbinv_block,
+ * each needed block row and column computed once (their runs merged width at
+ * a time). */
 mbinv_status mbinv_blocks(mbinv_ctx *ctx, int64_t count, const int64_t *ij, void *const *outs, const int64_t *ldos,
                           int width, mbinv_report *report);
 
-/* All blocks of M^-1 by k^2 independent runs (Sec. 5), one block row's runs
- * together at a time.  out is n x n with leading dimension ldo (host or
- * device).  done (may be NULL) is a k*k row-major bitmap of blocks to skip; cb
- * (may be NULL) is called for each finished block after its block row
- * completes, so a caller can checkpoint and resume. */
+/* All blocks of M^-1 by k^2 runs (Sec. 5).  Without a cap all runs are
+ * merged as in mbinv_blocks (k = 8: 6116 distinct frames instead of 64 x 270);
+ * under a cap one block row at a time, split further if the cap asks.  out is
+ * n x n with leading dimension ldo (host or device).  done (may be NULL) is a
+ * k*k row-major bitmap of blocks to skip; cb (may be NULL) is called for each
+ * finished block once its chunk (all blocks, or its block row under a cap) is
+ * written, so a caller can checkpoint and resume: blocks computed in a resumed
+ * call are bit for bit those of an uninterrupted one. */
 mbinv_status mbinv_all_blocks(mbinv_ctx *ctx, void *out, int64_t ldo, const uint8_t *done, mbinv_block_done_cb cb,
                               void *user, mbinv_report *report);
 

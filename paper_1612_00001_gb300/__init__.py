@@ -50,7 +50,8 @@ class Report(ctypes.Structure):
                 ("inv_device_seconds", ctypes.c_double), ("gemm_launches", ctypes.c_size_t),
                 ("pack_device_seconds", ctypes.c_double), ("inv_panel_device_seconds", ctypes.c_double),
                 ("inv_panel_flops", ctypes.c_double), ("inv_update_flops", ctypes.c_double),
-                ("inv_panel_launches", ctypes.c_size_t)]
+                ("inv_panel_launches", ctypes.c_size_t), ("request_frames", ctypes.c_size_t),
+                ("planned_device_bytes", ctypes.c_size_t), ("pack_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

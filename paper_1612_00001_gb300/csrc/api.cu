@@ -34,13 +34,19 @@ cudaError_t& last_cuda_error() {
   return e;
 }
 
-#define CU(x)                   \
-  do {                          \
-    cudaError_t e_ = (x);       \
-    if (e_ != cudaSuccess) {    \
-      last_cuda_error() = e_;   \
-      return MBINV_ECUDA;       \
-    }                           \
+// A CUDA error becomes MBINV_ECUDA, except an allocation the cap refused,
+// which becomes MBINV_ENOMEM_CAP.
+#define CU(x)                                                \
+  do {                                                       \
+    cudaError_t e_ = (x);                                    \
+    if (e_ != cudaSuccess) {                                 \
+      if (e_ == cudaErrorMemoryAllocation && cap_refused()) { \
+        cap_refused() = false;                               \
+        return MBINV_ENOMEM_CAP;                             \
+      }                                                      \
+      last_cuda_error() = e_;                                \
+      return MBINV_ECUDA;                                    \
+    }                                                        \
   } while (0)
 
 bool is_device_ptr(const void* p) {
@@ -119,9 +125,22 @@ struct mbinv_ctx {
   int border_mode = -1;
   DevBuf slots, outtmp, rowbuf, colbuf, resid, gbuf, wbuf, dmbuf, gemmdesc;
   Env env;
-  std::map<std::pair<int, int>, std::pair<Plan, Schedule>> plans;
-  size_t peak = 0;
+  MemTrack track;  // every device byte the context holds
+  std::vector<DevBuf*> bufs() {
+    std::vector<DevBuf*> v = {&own_M, &slots, &outtmp, &rowbuf, &colbuf, &resid, &gbuf, &wbuf, &dmbuf, &gemmdesc};
+    for (DevBuf* d : env.bufs()) v.push_back(d);
+    return v;
+  }
+  // the buffers of the sweep (value slots and the executor's workspace)
+  std::vector<DevBuf*> sweep_bufs() {
+    std::vector<DevBuf*> v = {&slots};
+    for (DevBuf* d : env.bufs()) v.push_back(d);
+    return v;
+  }
+  // plans by request group (the requests whose frames are merged)
+  std::map<std::vector<std::pair<int, int>>, std::pair<Plan, Schedule>> plans;
   bool in_sweep = false;
+  int depth = 0;  // nesting of entry-point calls on this context
 };
 
 namespace {
@@ -156,89 +175,109 @@ int max_inv_chunk(int b, int prec) {
   return (int)std::max<size_t>(1, std::min<size_t>(1 << 20, kInvScratchBudget / per));
 }
 
-// Memory of running G requests together (beyond M).
-size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int G, int inv_chunk) {
+// Memory of running one (merged) schedule, beyond M.
+size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int inv_chunk) {
   const int prec = c->opt.precision;
-  size_t bytes = (size_t)G * S.nslots * slot_bytes_for((int)c->b, prec);
+  size_t bytes = (size_t)S.nslots * slot_bytes_for((int)c->b, prec);
   bytes += inv_scratch_bytes((int)c->b, prec, inv_chunk);
-  if (prec == MBINV_MIXED_BF16) {
-    size_t ops = 0;
-    for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
-    bytes += pack_bytes((int)c->b, c->opt.bf16_slices, ops * G);
-  }
-  if (prec == MBINV_FP64_TC) {
-    size_t ops = 0;
-    for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
-    bytes += digit_bytes((int)c->b, ops * G);
-  }
   size_t ops = 0;
-  for (const Step& st : S.steps) ops += st.inv.size() + st.gemm.size();
-  bytes += (size_t)G * ops * 2 * sizeof(GemmDesc) + S.steps.size() * 1024 + (64u << 10);  // descriptors
+  for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
+  if (prec == MBINV_MIXED_BF16) bytes += pack_bytes((int)c->b, c->opt.bf16_slices, ops);
+  if (prec == MBINV_FP64_TC) bytes += digit_bytes((int)c->b, ops);
+  size_t all = 0;
+  for (const Step& st : S.steps) all += st.inv.size() + st.gemm.size();
+  bytes += all * 2 * sizeof(GemmDesc) + S.steps.size() * 1024 + (64u << 10);  // descriptors
   return bytes;
 }
 
-// The plan of request (i, j), with its Schur-temporary chunk and inverse chunk
-// chosen to fit the cap for G simultaneous requests.
-mbinv_status get_plan(mbinv_ctx* c, int64_t i, int64_t j, int G, const Schedule** out) {
-  auto key = std::make_pair((int)i, (int)j);
-  auto it = c->plans.find(key);
-  if (c->k == 1) {
-    // the recursion degenerates to one inversion of M
-    if (it == c->plans.end()) {
-      Schedule S;
-      Step st;
-      st.kind = Step::INV;
-      InvOp io;
-      io.src.kind = Ref::MBLK;
-      io.dst.kind = Ref::OUT;
-      st.inv.push_back(io);
-      S.steps.push_back(st);
-      S.inv_units = 2;
-      S.inversions = 1;
-      S.max_inv_batch = 1;
-      S.inv_chunk = 1;
-      if (c->opt.device_cap_bytes && c->own_M.bytes + run_bytes(c, S, 1, 1) > c->opt.device_cap_bytes)
-        return MBINV_ENOMEM_CAP;
-      it = c->plans.emplace(key, std::make_pair(Plan{}, std::move(S))).first;
-    }
+// Device bytes held outside the sweep's workspace (M, output staging,
+// refinement buffers): what a sweep's plan must fit beside.
+size_t base_bytes(mbinv_ctx* c) {
+  // a context of a batched call counts into the call's tracker, with the
+  // other problems: its plan fits beside its own matrix copy
+  if (c->own_M.track != &c->track) return c->own_M.bytes;
+  size_t sweep = 0;
+  for (DevBuf* d : c->sweep_bufs()) sweep += d->bytes;
+  return c->track.live - sweep;
+}
+
+// Under a cap, the sweep's workspace is freed between groups, so that its
+// buffers never hold more than the plan of the group being run.
+void release_sweep(mbinv_ctx* c) {
+  if (!c->opt.device_cap_bytes) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (DevBuf* d : c->sweep_bufs()) d->release();
+}
+
+// The merged plan of a group of requests, with its Schur-temporary chunk and
+// inverse chunk chosen to fit the cap beside what the context already holds.
+mbinv_status get_plan(mbinv_ctx* c, const std::vector<std::pair<int, int>>& reqs, const Schedule** out) {
+  auto it = c->plans.find(reqs);
+  if (it != c->plans.end() &&
+      (!c->opt.device_cap_bytes || base_bytes(c) + it->second.second.planned <= c->opt.device_cap_bytes)) {
     *out = &it->second.second;
     return MBINV_OK;
   }
-  if (it == c->plans.end() || it->second.second.inv_chunk == 0 || G > 1) {
-    Plan P = (it == c->plans.end()) ? build_plan((int)c->k, (int)i, (int)j, c->l > 0) : it->second.first;
-    const size_t cap = c->opt.device_cap_bytes;
-    const size_t base = c->own_M.bytes;
-    Schedule best;
+  const size_t cap = c->opt.device_cap_bytes;
+  const size_t base = base_bytes(c);
+  if (c->k == 1) {
+    // the recursion degenerates to one inversion of M per request
+    Schedule S;
+    Step st;
+    st.kind = Step::INV;
+    for (size_t r = 0; r < reqs.size(); ++r) {
+      InvOp io;
+      io.src.kind = Ref::MBLK;
+      io.dst.kind = Ref::OUT;
+      io.dst.slot = (int)r;
+      st.inv.push_back(io);
+    }
+    S.steps.push_back(st);
+    S.nouts = (int)reqs.size();
+    S.inv_units = 2.0 * reqs.size();
+    S.inversions = reqs.size();
+    S.max_inv_batch = (int)reqs.size();
+    S.frames = S.request_frames = 0;
+    const int full = std::min<int>((int)reqs.size(), max_inv_chunk((int)c->b, c->opt.precision));
     bool ok = false;
-    for (int z : {0, 64, 16, 4, 1}) {
-      Schedule T = build_schedule(P, z);
-      const int full = std::min(std::max(1, T.max_inv_batch) * G, max_inv_chunk((int)c->b, c->opt.precision));
-      for (int ic : {full, 256, 64, 16, 4, 1}) {
-        if (ic > full) continue;
-        if (cap == 0 || base + run_bytes(c, T, G, ic) <= cap) {
-          T.inv_chunk = ic;
-          best = std::move(T);
-          ok = true;
-          break;
-        }
+    for (int ic : {full, 256, 64, 16, 4, 1}) {
+      if (ic > full) continue;
+      if (cap == 0 || base + run_bytes(c, S, ic) <= cap) {
+        S.inv_chunk = ic;
+        S.planned = run_bytes(c, S, ic);
+        ok = true;
+        break;
       }
-      if (ok) break;
     }
     if (!ok) return MBINV_ENOMEM_CAP;
-    if (c->plans.size() > 4096) c->plans.clear();
-    it = c->plans.insert_or_assign(key, std::make_pair(std::move(P), std::move(best))).first;
+    if (c->plans.size() > 256) c->plans.clear();
+    it = c->plans.insert_or_assign(reqs, std::make_pair(Plan{}, std::move(S))).first;
+    *out = &it->second.second;
+    return MBINV_OK;
   }
+  Plan P = build_plan((int)c->k, reqs, c->l > 0);
+  Schedule best;
+  bool ok = false;
+  for (int z : {0, 256, 64, 16, 4, 1}) {
+    Schedule T = build_schedule(P, z);
+    const int full = std::min(std::max(1, T.max_inv_batch), max_inv_chunk((int)c->b, c->opt.precision));
+    for (int ic : {full, 256, 64, 16, 4, 1}) {
+      if (ic > full) continue;
+      if (cap == 0 || base + run_bytes(c, T, ic) <= cap) {
+        T.inv_chunk = ic;
+        T.planned = run_bytes(c, T, ic);
+        best = std::move(T);
+        ok = true;
+        break;
+      }
+    }
+    if (ok) break;
+  }
+  if (!ok) return MBINV_ENOMEM_CAP;
+  if (c->plans.size() > 256) c->plans.clear();
+  it = c->plans.insert_or_assign(reqs, std::make_pair(std::move(P), std::move(best))).first;
   *out = &it->second.second;
   return MBINV_OK;
-}
-
-// Largest number of requests (<= want) that fit the cap together.
-int fit_group(mbinv_ctx* c, int64_t i, int64_t j, int want) {
-  for (int G = want; G > 1; G = G / 2) {
-    const Schedule* S;
-    if (get_plan(c, i, j, G, &S) == MBINV_OK) return G;
-  }
-  return 1;
 }
 
 struct Req {
@@ -252,82 +291,83 @@ void add_env_report(mbinv_report* r, const Env& env) {
   r->gemm_device_seconds += env.gemm_dev_s;
   r->inv_device_seconds += env.inv_dev_s;
   r->pack_device_seconds += env.pack_dev_s;
+  r->pack_bytes += env.pack_bytes;
   r->inv_panel_device_seconds += env.inv_panel_dev_s;
   r->inv_panel_flops += env.inv_panel_flops;
   r->inv_update_flops += env.inv_update_flops;
   r->inv_panel_launches += env.inv_panel_launches;
 }
 
-void add_report(mbinv_report* r, const mbinv_ctx* c, const Schedule& S, size_t nreq) {
+void add_report(mbinv_report* r, const mbinv_ctx* c, const Schedule& S) {
   if (!r) return;
   const double b3 = (double)c->b * (double)c->b * (double)c->b;
-  r->gemm_flops += nreq * S.gemm_flops_units * b3;
-  r->inv_flops += nreq * S.inv_units * b3;
-  r->frames += nreq * S.frames;
-  r->inversions += nreq * S.inversions;
+  r->gemm_flops += S.gemm_flops_units * b3;
+  r->inv_flops += S.inv_units * b3;
+  r->frames += S.frames;
+  r->request_frames += S.request_frames;
+  r->inversions += S.inversions;
 }
 
-// Runs requests with the same border together.
+std::vector<std::pair<int, int>> group_key(const std::vector<Req>& reqs, size_t n) {
+  std::vector<std::pair<int, int>> key;
+  for (size_t q = 0; q < n && q < reqs.size(); ++q) key.emplace_back((int)reqs[q].i, (int)reqs[q].j);
+  return key;
+}
+
+// Runs a group of requests with the same border as one merged schedule:
+// frames that compute the same thing are evaluated once for all of them.
 mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report* rep) {
   if (reqs.empty()) return MBINV_OK;
   mbinv_status s = set_border(c, border_of(c, reqs[0].i, reqs[0].j));
   if (s != MBINV_OK) return s;
-  const int G = (int)reqs.size();
-  std::vector<const Schedule*> sch(G);
-  for (int q = 0; q < G; ++q) {
-    s = get_plan(c, reqs[q].i, reqs[q].j, G, &sch[q]);
-    if (s != MBINV_OK) return s;
-  }
+  const Schedule* S;
+  s = get_plan(c, group_key(reqs, reqs.size()), &S);
+  if (s != MBINV_OK) return s;
+  release_sweep(c);
+  const size_t planned = c->track.live + S->planned;
   const int prec = c->opt.precision;
   const size_t sb = slot_bytes_for((int)c->b, prec);
-  size_t per = 0;
-  int ic = INT_MAX;
-  for (const Schedule* S : sch) {
-    per = std::max(per, (size_t)S->nslots * sb);
-    ic = std::min(ic, S->inv_chunk);
-  }
-  CU(c->slots.ensure(per * G));
-  std::vector<Job> jobs(G);
-  for (int q = 0; q < G; ++q) {
-    Job& J = jobs[q];
-    J.dM = c->dM;
-    J.ldm = c->ldm;
-    J.mdt = c->mdt;
-    J.b = (int)c->b;
-    J.slots = (char*)c->slots.p + per * q;
-    J.slot_bytes = sb;
-    J.slot_dt = env_slot_type(prec);
-    J.out = reqs[q].dst;
-    J.ldo = reqs[q].ldd;
-    J.out_dt = c->dtype;
-    J.S = sch[q];
+  CU(c->slots.ensure((size_t)S->nslots * sb + 256));
+  Job J;
+  J.dM = c->dM;
+  J.ldm = c->ldm;
+  J.mdt = c->mdt;
+  J.b = (int)c->b;
+  J.slots = (char*)c->slots.p;
+  J.slot_bytes = sb;
+  J.slot_dt = env_slot_type(prec);
+  J.out_dt = c->dtype;
+  J.S = S;
+  for (const Req& r : reqs) {
+    J.outs.push_back(r.dst);
+    J.ldos.push_back(r.ldd);
   }
   c->env.stream = c->stream;
   c->env.precision = prec;
   c->env.slices = c->opt.bf16_slices;
   c->env.profile = c->opt.profile != 0;
-  c->env.inv_chunk = std::max(1, ic);
-  s = run_jobs(c->env, jobs);
+  c->env.inv_chunk = std::max(1, S->inv_chunk);
+  s = run_jobs(c->env, {J});
   if (s == MBINV_ECUDA) last_cuda_error() = c->env.last_error;
-  size_t held = c->slots.bytes + c->own_M.bytes + c->outtmp.bytes;
-  for (DevBuf* d : {&c->env.inv_work, &c->env.inv_wrow, &c->env.inv_perm, &c->env.inv_amax, &c->env.inv_tc, &c->env.desc,
-                    &c->env.apk, &c->env.bpk, &c->env.b2pk, &c->env.oexp})
-    held += d->bytes;
-  c->peak = std::max(c->peak, held);
   if (rep) {
-    for (int q = 0; q < G; ++q) add_report(rep, c, *sch[q], 1);
+    add_report(rep, c, *S);
     rep->launches += (size_t)c->env.launches;
     rep->gemm_launches += (size_t)c->env.gemm_launches;
     add_env_report(rep, c->env);
-    rep->peak_device_bytes = std::max(rep->peak_device_bytes, c->peak);
-    if (s == MBINV_ESINGULAR && rep->failed_pivot < 0)
-      for (int q = 0; q < G; ++q)
-        if (c->env.job_singular[q]) {
-          rep->failed_pivot = q;
-          break;
-        }
+    rep->planned_device_bytes = std::max(rep->planned_device_bytes, planned);
+    if (s == MBINV_ESINGULAR && rep->failed_pivot < 0) rep->failed_pivot = c->env.failed_inverse;
   }
   return s;
+}
+
+// Largest number of the first requests of v (at most want) whose merged
+// schedule fits the cap.
+int fit_group(mbinv_ctx* c, const std::vector<Req>& v, int want) {
+  for (int G = want; G > 1; G = G / 2) {
+    const Schedule* S;
+    if (get_plan(c, group_key(v, (size_t)G), &S) == MBINV_OK) return G;
+  }
+  return 1;
 }
 
 // Runs any list of requests: groups of at most `width` with one border each.
@@ -336,7 +376,7 @@ mbinv_status run_requests(mbinv_ctx* c, const std::vector<Req>& reqs, int width,
   for (const Req& r : reqs) by_border[border_of(c, r.i, r.j)].push_back(r);
   for (auto& kv : by_border) {
     const std::vector<Req>& v = kv.second;
-    const int G = std::max(1, std::min<int>(width, fit_group(c, v[0].i, v[0].j, std::min<int>(width, (int)v.size()))));
+    const int G = std::max(1, fit_group(c, v, std::min<int>(std::max(1, width), (int)v.size())));
     for (size_t q0 = 0; q0 < v.size(); q0 += G) {
       std::vector<Req> grp(v.begin() + q0, v.begin() + std::min(v.size(), q0 + G));
       mbinv_status s = run_group(c, grp, rep);
@@ -592,7 +632,6 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
   const size_t rsz = (size_t)b * n, csz = (size_t)n * b;
   CU(c->rowbuf.ensure(rows.size() * rsz * xs + 256));
   CU(c->colbuf.ensure(cols.size() * csz * xs + 256));
-  CU(c->resid.ensure(rows.size() * rsz * 8 + v.size() * (size_t)b * b * 8 + 512));
   char* X = (char*)c->rowbuf.p;  // X_i at X + (rows[i] * rsz) * xs, leading dimension n
   char* Y = (char*)c->colbuf.p;  // Y_j at Y + (cols[j] * csz) * xs, leading dimension b
   // every block of the needed rows and columns, each computed once
@@ -625,7 +664,10 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
                          X + (rows[p.first] * rsz + p.second * b) * xs, (size_t)n * xs, (size_t)bj * xs, (size_t)bi,
                          cudaMemcpyDeviceToDevice, c->stream));
   }
-  // R_i = -X_i M + E_i^T (FP64_TC: as digit products on the tensor cores)
+  // R_i = -X_i M + E_i^T (FP64_TC: as digit products on the tensor cores);
+  // under a cap the sweep's workspace goes first
+  release_sweep(c);
+  CU(c->resid.ensure(rows.size() * rsz * 8 + v.size() * (size_t)b * b * 8 + 512));
   double* R = (double*)c->resid.p;
   double* Nb = R + rows.size() * rsz;
   const bool tcr = c->opt.precision == MBINV_FP64_TC && c->mdt == F64;
@@ -701,8 +743,7 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
     for (auto& p : v) rep->gemm_flops += 2.0 * block_extent(c, p.first) * block_extent(c, p.second) * n;
     rep->launches += 2 + 2 * rows.size() + v.size();
     rep->rel_residual = std::max(rep->rel_residual, rmax);
-    rep->peak_device_bytes =
-        std::max(rep->peak_device_bytes, c->peak + c->rowbuf.bytes + c->colbuf.bytes + c->resid.bytes);
+
   }
   if (!(rmax < 1.0)) return MBINV_ENOTCONV;
   return MBINV_OK;
@@ -721,6 +762,29 @@ mbinv_status guarded(F&& f) {
   } catch (...) {
     return MBINV_EINVAL;
   }
+}
+
+// One call on a context: under a cap the context first lets go of the
+// workspace an earlier call left (buffers only grow within a call), and the
+// report carries the measured high-water mark of the call.  The nested calls
+// some entry points make (mbinv_all_blocks runs mbinv_blocks) keep the
+// outermost call's mark.
+template <typename F>
+mbinv_status on_context(mbinv_ctx* c, mbinv_report* rep, F&& f) {
+  if (!c) return MBINV_EINVAL;
+  const bool outer = c->depth++ == 0;
+  if (outer) {
+    if (c->opt.device_cap_bytes) {
+      if (c->stream) cudaStreamSynchronize(c->stream);
+      for (DevBuf* d : c->bufs())
+        if (d != &c->own_M) d->release();
+    }
+    c->track.hwm = c->track.live;
+  }
+  mbinv_status s = guarded(f);
+  --c->depth;
+  if (rep) rep->peak_device_bytes = std::max(rep->peak_device_bytes, c->track.hwm);
+  return s;
 }
 
 // ====================================================================== ABI
@@ -757,8 +821,10 @@ const char* mbinv_version(void) { return "mbinv 0.2 (sm_103a)"; }
 
 const char* mbinv_last_cuda_error(void) { return cudaGetErrorString(last_cuda_error()); }
 
+// shared: the tracker of a batched call, whose contexts count their bytes
+// together (no cap of their own); null for an ordinary context.
 static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,
-                          const mbinv_options* opt) {
+                                      const mbinv_options* opt, MemTrack* shared = nullptr) {
   if (!out || !M || n <= 0 || k <= 0 || k > 63 || k > n || ld < n || (dtype != F64 && dtype != F32))
     return MBINV_EINVAL;
   *out = nullptr;
@@ -780,6 +846,9 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   c->l = c->npad - n;
   c->dtype = dtype;
   c->opt = o;
+  c->track.cap = shared ? 0 : o.device_cap_bytes;
+  MemTrack* tr = shared ? shared : &c->track;
+  for (DevBuf* d : c->bufs()) d->track = tr;
   c->stream = (cudaStream_t)o.cuda_stream;
   // the plain paths read M in their own precision; the mixed path reads the
   // caller's M as given (its residual is taken against it)
@@ -802,6 +871,7 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
     } else {
       // stage the caller's matrix on the device, then convert it
       DevBuf stage;
+      stage.track = tr;
       CU(stage.ensure((size_t)n * n * es));
       CU(cudaMemcpy2DAsync(stage.p, (size_t)n * es, M, (size_t)ld * es, (size_t)n * es, (size_t)n,
                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -891,47 +961,62 @@ static mbinv_status mbinv_blocks_impl(mbinv_ctx* c, int64_t count, const int64_t
   return s;
 }
 
-static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, const uint8_t* done, mbinv_block_done_cb cb,
-                              void* user, mbinv_report* rep) {
+static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, const uint8_t* done,
+                                          mbinv_block_done_cb cb, void* user, mbinv_report* rep) {
   if (!c || !out || ldo < c->n) return MBINV_EINVAL;
   start_report(rep);
+  auto t0 = std::chrono::steady_clock::now();
   const size_t es = dtype_size(c->dtype);
-  // one block row at a time: its k blocks run together, then the callback
-  for (int64_t i = 0; i < c->k; ++i) {
+  // the blocks still to do, in row-major order
+  std::vector<std::pair<int64_t, int64_t>> todo;
+  for (int64_t i = 0; i < c->k; ++i)
+    for (int64_t j = 0; j < c->k; ++j)
+      if (!(done && done[i * c->k + j])) todo.emplace_back(i, j);
+  // Without a cap all runs go in one call, their shared frames evaluated once;
+  // under a cap one block row at a time (mbinv_blocks splits further if the
+  // cap asks).  The callback follows each finished chunk.
+  const size_t chunk = c->opt.device_cap_bytes ? (size_t)c->k : todo.size();
+  for (size_t q0 = 0; q0 < todo.size(); q0 += chunk) {
+    const size_t q1 = std::min(todo.size(), q0 + chunk);
     std::vector<int64_t> ij;
     std::vector<void*> outs;
     std::vector<int64_t> ldos;
-    for (int64_t j = 0; j < c->k; ++j) {
-      if (done && done[i * c->k + j]) continue;
+    for (size_t q = q0; q < q1; ++q) {
+      const int64_t i = todo[q].first, j = todo[q].second;
       ij.push_back(i);
       ij.push_back(j);
       outs.push_back((char*)out + ((size_t)i * c->b * ldo + (size_t)j * c->b) * es);
       ldos.push_back(ldo);
     }
-    if (outs.empty()) continue;
     mbinv_report r;
-    mbinv_status s = mbinv_blocks(c, (int64_t)outs.size(), ij.data(), outs.data(), ldos.data(), kDefaultWidth, &r);
+    mbinv_status s =
+        mbinv_blocks(c, (int64_t)outs.size(), ij.data(), outs.data(), ldos.data(), (int)outs.size(), &r);
     if (rep) {
       rep->gemm_flops += r.gemm_flops;
       rep->inv_flops += r.inv_flops;
-      rep->seconds += r.seconds;
       rep->frames += r.frames;
+      rep->request_frames += r.request_frames;
       rep->inversions += r.inversions;
       rep->launches += r.launches;
       rep->gemm_launches += r.gemm_launches;
       rep->gemm_device_seconds += r.gemm_device_seconds;
       rep->inv_device_seconds += r.inv_device_seconds;
       rep->pack_device_seconds += r.pack_device_seconds;
+      rep->pack_bytes += r.pack_bytes;
       rep->inv_panel_device_seconds += r.inv_panel_device_seconds;
       rep->inv_panel_flops += r.inv_panel_flops;
       rep->inv_update_flops += r.inv_update_flops;
       rep->inv_panel_launches += r.inv_panel_launches;
+      rep->rel_residual = std::max(rep->rel_residual, r.rel_residual);
       rep->peak_device_bytes = std::max(rep->peak_device_bytes, r.peak_device_bytes);
+      rep->planned_device_bytes = std::max(rep->planned_device_bytes, r.planned_device_bytes);
+      if (s == MBINV_ESINGULAR) rep->failed_pivot = r.failed_pivot;
     }
     if (s != MBINV_OK) return s;
     if (cb)
-      for (size_t t = 0; t < outs.size(); ++t) cb(i, ij[2 * t + 1], user);
+      for (size_t q = q0; q < q1; ++q) cb(todo[q].first, todo[q].second, user);
   }
+  if (rep) rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return MBINV_OK;
 }
 
@@ -994,7 +1079,7 @@ static mbinv_status mbinv_backward_impl(mbinv_ctx* c, int64_t i, int64_t j, cons
   if (rep) {
     rep->gemm_flops += 2.0 * bi * bj * n + 2.0 * n * n * bi;
     rep->launches += 2;
-    rep->peak_device_bytes += c->rowbuf.bytes + c->colbuf.bytes + c->wbuf.bytes;
+
   }
   return MBINV_OK;
 }
@@ -1013,7 +1098,9 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     o = *opt;
   }
   if (o.refine_steps > 0) return MBINV_ENOTSUP;
-  // one context per problem (its device matrix and plan), all run together
+  // one context per problem (its device matrix and plan), all run together;
+  // their device bytes and the shared executor's are counted together
+  MemTrack shared;
   std::vector<mbinv_ctx*> ctxs((size_t)count, nullptr);
   mbinv_status first = MBINV_OK;
   auto cleanup = [&]() {
@@ -1023,10 +1110,11 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     mbinv_problem& p = probs[t];
     p.status = MBINV_EINVAL;
     if (p.i < 0 || p.j < 0 || p.i >= p.k || p.j >= p.k || !p.out) continue;
-    p.status = mbinv_create(&ctxs[t], p.n, p.k, dtype, p.M, p.ld, &o);
+    p.status = guarded([&] { return mbinv_create_impl(&ctxs[t], p.n, p.k, dtype, p.M, p.ld, &o, &shared); });
   }
   // run in waves whose summed workspace fits the cap
   Env env;
+  for (DevBuf* d : env.bufs()) d->track = &shared;
   env.stream = (cudaStream_t)o.cuda_stream;
   env.precision = o.precision;
   env.slices = o.bf16_slices;
@@ -1046,11 +1134,11 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
       mbinv_ctx* c = ctxs[order[q]];
       mbinv_problem& p = probs[order[q]];
       const Schedule* S;
-      if (get_plan(c, p.i, p.j, 1, &S) != MBINV_OK) {
+      if (get_plan(c, {{(int)p.i, (int)p.j}}, &S) != MBINV_OK) {
         p.status = MBINV_ENOMEM_CAP;
         continue;
       }
-      const size_t need = run_bytes(c, *S, 1, S->inv_chunk) + c->own_M.bytes;
+      const size_t need = run_bytes(c, *S, S->inv_chunk) + c->own_M.bytes;
       if (!jobs.empty() && ((o.device_cap_bytes && used + need > o.device_cap_bytes) || jobs.size() >= 1024)) break;
       if (set_border(c, border_of(c, p.i, p.j)) != MBINV_OK ||
           c->slots.ensure((size_t)S->nslots * slot_bytes_for((int)c->b, o.precision)) != cudaSuccess ||
@@ -1077,7 +1165,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
       J.S = S;
       jobs.push_back(J);
       members.push_back(order[q]);
-      if (rep) add_report(rep, c, *S, 1);
+      if (rep) add_report(rep, c, *S);
     }
     q0 = q;
     if (members.empty()) continue;
@@ -1126,7 +1214,8 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
   for (int64_t t = 0; t < count; ++t)
     if (probs[t].status != MBINV_OK && first == MBINV_OK) first = (mbinv_status)probs[t].status;
   if (rep) {
-    rep->peak_device_bytes = peak;
+    rep->peak_device_bytes = shared.hwm;
+    rep->planned_device_bytes = peak;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return first;
@@ -1137,25 +1226,25 @@ mbinv_status mbinv_create(mbinv_ctx** out, int64_t n, int64_t k, int dtype, cons
   return guarded([&] { return mbinv_create_impl(out, n, k, dtype, M, ld, opt); });
 }
 mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
-  return guarded([&] { return mbinv_block_impl(c, i, j, out, ldo, rep); });
+  return on_context(c, rep, [&] { return mbinv_block_impl(c, i, j, out, ldo, rep); });
 }
 mbinv_status mbinv_blocks(mbinv_ctx* c, int64_t count, const int64_t* ij, void* const* outs, const int64_t* ldos,
                           int width, mbinv_report* rep) {
-  return guarded([&] { return mbinv_blocks_impl(c, count, ij, outs, ldos, width, rep); });
+  return on_context(c, rep, [&] { return mbinv_blocks_impl(c, count, ij, outs, ldos, width, rep); });
 }
 mbinv_status mbinv_all_blocks(mbinv_ctx* c, void* out, int64_t ldo, const uint8_t* done, mbinv_block_done_cb cb,
                               void* user, mbinv_report* rep) {
-  return guarded([&] { return mbinv_all_blocks_impl(c, out, ldo, done, cb, user, rep); });
+  return on_context(c, rep, [&] { return mbinv_all_blocks_impl(c, out, ldo, done, cb, user, rep); });
 }
 mbinv_status mbinv_block_row(mbinv_ctx* c, int64_t i, void* out, int64_t ldo, mbinv_report* rep) {
-  return guarded([&] { return mbinv_block_row_impl(c, i, out, ldo, rep); });
+  return on_context(c, rep, [&] { return mbinv_block_row_impl(c, i, out, ldo, rep); });
 }
 mbinv_status mbinv_block_col(mbinv_ctx* c, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
-  return guarded([&] { return mbinv_block_col_impl(c, j, out, ldo, rep); });
+  return on_context(c, rep, [&] { return mbinv_block_col_impl(c, j, out, ldo, rep); });
 }
 mbinv_status mbinv_backward(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM, int64_t ldd,
                             mbinv_report* rep) {
-  return guarded([&] { return mbinv_backward_impl(c, i, j, G, ldg, dM, ldd, rep); });
+  return on_context(c, rep, [&] { return mbinv_backward_impl(c, i, j, G, ldg, dM, ldd, rep); });
 }
 mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem* probs, int dtype, const mbinv_options* opt,
                                   mbinv_report* rep) {

@@ -178,3 +178,31 @@ extern "C" int mbinv_debug_plan(int k, int i, int j, int pad_last, double* out) 
   }
   return 0;
 }
+
+// Host-only hook of the merged planner (no CUDA call): the requests ij[2t],
+// ij[2t+1] (t < count) of a k x k grid planned together.  out[0] frames
+// evaluated, out[1] frames of the requests run one by one, out[2] inverses,
+// out[3] peak value slots, out[4] product work and out[5] inverse work in
+// units of b^3, out[6] leaves.  0, or -1 for invalid arguments.
+extern "C" int mbinv_debug_plan_group(int k, int count, const int* ij, int pad_last, double* out) {
+  if (k < 2 || count < 1 || !ij || !out) return -1;
+  try {
+    std::vector<std::pair<int, int>> reqs;
+    for (int t = 0; t < count; ++t) {
+      if (ij[2 * t] < 0 || ij[2 * t + 1] < 0 || ij[2 * t] >= k || ij[2 * t + 1] >= k) return -1;
+      reqs.emplace_back(ij[2 * t], ij[2 * t + 1]);
+    }
+    const Plan P = build_plan(k, reqs, pad_last != 0);
+    const Schedule S = build_schedule(P, 0);
+    out[0] = (double)S.frames;
+    out[1] = (double)S.request_frames;
+    out[2] = (double)S.inversions;
+    out[3] = (double)S.nslots;
+    out[4] = S.gemm_flops_units;
+    out[5] = S.inv_units;
+    out[6] = (double)P.leaves;
+  } catch (...) {
+    return -1;
+  }
+  return 0;
+}

@@ -63,8 +63,12 @@ const void* resolve(const Job& J, const Ref& r, int64_t* ld, int* dt) {
       *dt = J.slot_dt;
       return J.slots + (size_t)r.slot * J.slot_bytes;
     case Ref::OUT:
-      *ld = J.ldo;
       *dt = J.out_dt;
+      if (!J.outs.empty()) {
+        *ld = J.ldos[r.slot];
+        return J.outs[r.slot];
+      }
+      *ld = J.ldo;
       return J.out;
     default:
       *ld = 0;
@@ -110,13 +114,17 @@ struct Launch {
   double alpha = 1, beta = 0;           // OZ
 };
 
-#define CUE(x)                      \
-  do {                              \
-    cudaError_t e_ = (x);           \
-    if (e_ != cudaSuccess) {        \
-      E.last_error = e_;            \
-      return MBINV_ECUDA;           \
-    }                               \
+#define CUE(x)                                       \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) {                         \
+      E.last_error = e_;                             \
+      if (e_ == cudaErrorMemoryAllocation && cap_refused()) { \
+        cap_refused() = false;                       \
+        return MBINV_ENOMEM_CAP;                     \
+      }                                              \
+      return MBINV_ECUDA;                            \
+    }                                                \
   } while (0)
 
 }  // namespace
@@ -142,9 +150,11 @@ size_t digit_bytes(int bmax, size_t ops) {
 mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   E.launches = E.gemm_launches = 0;
   E.gemm_dev_s = E.inv_dev_s = E.pack_dev_s = 0;
+  E.pack_bytes = 0;
   E.inv_panel_dev_s = E.inv_panel_flops = E.inv_update_flops = 0;
   E.inv_panel_launches = 0;
   E.job_singular.assign(jobs.size(), 0);
+  E.failed_inverse = -1;
   if (jobs.empty()) return MBINV_OK;
   const bool mixed = E.precision == MBINV_MIXED_BF16;
   const bool ozk = E.precision == MBINV_FP64_TC;
@@ -232,6 +242,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   };
   std::vector<Launch> L;
   int* dflags = (int*)E.flags.p;
+  int ninv_seen = 0;  // inverses so far, in launch order: the status tag
 
   // ---- pass 2: descriptors
   std::map<std::pair<int, int>, int> zslab;  // (request, slot of a Z value) -> slab in its group
@@ -272,7 +283,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           d.perm = (int*)((char*)E.inv_perm.p + (u - c0) * st.perm);
           d.amax = (unsigned long long*)((char*)E.inv_amax.p + (u - c0) * 256);
           d.b = J.b;
-          d.tag = ops[u].first;
+          d.tag = ninv_seen++;
           d.flag = dflags + ops[u].first;
           bm = std::max(bm, J.b);
           double pf, uf;
@@ -331,6 +342,8 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
             const void* p = resolve(jobs[ops[first[a]].first], side == 0 ? g.A : g.B, &ld, &dt);
             if (dt != F64) return MBINV_ENOTSUP;
             pd[a] = oz::PackDesc{(const double*)p, ld, b, b, side, (int)a};
+            // each FP64 entry read once, 8 BF16 digits written; one exponent per row
+            E.pack_bytes += (double)b * b * (8 + 2 * oz::kDigits) + 4.0 * b;
           }
           Launch l{Launch::OZPACK, o, (int)first.size()};
           l.rows_pad = side == 0 ? rpa : rpb;
@@ -461,6 +474,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           int dt;
           const void* p = resolve(jobs[ops[afirst[a]].first], ops[afirst[a]].second->A, &ld, &dt);
           pd[a] = tc::PackDesc{p, ld, b, b, dt == F64 ? 1 : 0, 0, (int)a};
+          E.pack_bytes += (double)b * b * (dtype_size(dt) + 2 * NS);
         }
         Launch l{Launch::PACK, o, (int)afirst.size()};
         l.rows_pad = rpad;
@@ -476,6 +490,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           int dt;
           const void* p = resolve(jobs[ops[us[v]].first], ops[us[v]].second->B, &ld, &dt);
           pd[v] = tc::PackDesc{p, ld, b, b, dt == F64 ? 1 : 0, 1, (int)v};
+          E.pack_bytes += (double)b * b * (dtype_size(dt) + 2 * NS);
         }
         Launch l{Launch::PACK, o, (int)us.size()};
         l.rows_pad = rpad;
@@ -626,6 +641,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   CUE(cudaMemcpy(fl.data(), E.flags.p, jobs.size() * sizeof(int), cudaMemcpyDeviceToHost));
   if (mixed || ozk) CUE(cudaMemcpy(&herr, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
   for (size_t q = 0; q < jobs.size(); ++q) E.job_singular[q] = fl[q];
+  if (hst[1].singular) E.failed_inverse = hst[1].tag;
   if (E.profile) {
     for (size_t q = 0; q < L.size(); ++q) {
       float ms = 0;

@@ -11,20 +11,50 @@
 
 namespace mbinv {
 
+// Device bytes a context holds, counted at every allocation and free, and
+// the bound they must stay under (0 = none).
+struct MemTrack {
+  size_t live = 0, hwm = 0, cap = 0;
+};
+
+// Set when an allocation was refused because it would have crossed the cap
+// (the caller then reports MBINV_ENOMEM_CAP rather than a CUDA error).
+inline bool& cap_refused() {
+  static thread_local bool f = false;
+  return f;
+}
+
+// A device buffer that grows on demand.  With a tracker attached, every byte
+// it holds is counted there, and growth that would take the tracker past its
+// cap is refused before cudaMalloc is called.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  MemTrack* track = nullptr;
   cudaError_t ensure(size_t need) {
     if (need <= bytes) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
+    release();
+    if (track && track->cap && track->live + need > track->cap) {
+      cap_refused() = true;
+      return cudaErrorMemoryAllocation;
+    }
     cudaError_t e = cudaMalloc(&p, need);
-    if (e == cudaSuccess) bytes = need;
-    return e;
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = need;
+    if (track) {
+      track->live += need;
+      track->hwm = track->live > track->hwm ? track->live : track->hwm;
+    }
+    return cudaSuccess;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      if (track) track->live -= bytes;
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -49,7 +79,8 @@ struct HostBuf {
   }
 };
 
-// One request: the matrix it reads, its value slots, its output, its schedule.
+// One job: the matrix it reads, its value slots, its outputs (one per request
+// of its plan), its schedule.
 struct Job {
   const void* dM = nullptr;  // (bordered) matrix, row-major
   int64_t ldm = 0;
@@ -58,8 +89,10 @@ struct Job {
   char* slots = nullptr;     // this request's slots, slot_bytes apart
   size_t slot_bytes = 0;
   int slot_dt = F64;
-  void* out = nullptr;       // device destination of N_ij (b x b)
+  void* out = nullptr;       // device destination of N_ij (b x b), one request
   int64_t ldo = 0;
+  std::vector<void*> outs;   // several requests: destination of request r
+  std::vector<int64_t> ldos;
   int out_dt = F64;
   const Schedule* S = nullptr;
 };
@@ -77,10 +110,16 @@ struct Env {
   // results of the last run
   int launches = 0, gemm_launches = 0;
   double gemm_dev_s = 0, inv_dev_s = 0, pack_dev_s = 0;
+  double pack_bytes = 0;  // algorithmic bytes of the operand packs of the last run
   double inv_panel_dev_s = 0, inv_panel_flops = 0, inv_update_flops = 0;
   size_t inv_panel_launches = 0;
   std::vector<cudaEvent_t> pevents;  // panel timing (profile)
-  std::vector<int> job_singular;  // per request
+  // buffers of the sweep (everything but the descriptor staging on the host)
+  std::vector<DevBuf*> bufs() {
+    return {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &inv_tc, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr, &oexp};
+  }
+  std::vector<int> job_singular;  // per job
+  int64_t failed_inverse = -1;    // first singular inverse, in launch order
   cudaError_t last_error = cudaSuccess;
 
   void release();

@@ -15,32 +15,43 @@ enum DType : int { F64 = 0, F32 = 1, BF16 = 2 };
 inline size_t dtype_size(int t) { return t == F64 ? 8 : (t == F32 ? 4 : 2); }
 
 // --------------------------------------------------------------- planner
-// A frame of the recursion (Sec. 3.1): kept block row/column, role and, for
-// order >= 3, the ids of its four children; order-2 frames are leaves whose
-// value is M[a,c] - M[a,pc] (P^-1 M[pr,c]) with P = M[pr,pc] (Eqs. FA2-FD2).
+// A frame of the recursion (Sec. 3.1) after hash-consing: its value is
+//   order 2 (leaf):  M[krow, kcol] - M[krow, pcol] (P^-1 M[prow, kcol]),
+//                    P = M[prow, pcol] the pivot block of the request that
+//                    reached it (Eqs. FA2-FD2);
+//   order >= 3:      kept - left * (piv^-1 * right), the four operands being
+//                    frames of the order below, chosen by the frame's role
+//                    (Eqs. SchurofA-SchurofD).
+// Two frames are one when they compute the same thing: leaves with the same
+// (krow, kcol, prow, pcol), other frames with the same four operand frames.
+// Such frames round identically, so sharing them across requests changes no
+// bit of any result.
 struct PFrame {
-  int order = 0, role = 0;
-  int krow = -1, kcol = -1;
-  int child[4] = {-1, -1, -1, -1};
-  int kept = -1, left = -1, piv = -1, right = -1;
+  int order = 0;
+  int krow = -1, kcol = -1, prow = -1, pcol = -1;  // leaves
+  int kept = -1, left = -1, piv = -1, right = -1;  // order >= 3
 };
 
 struct Plan {
-  int k = 0, i = 0, j = 0;
-  std::vector<int> rows, cols;  // root lists (0-based block indices)
-  int prow = -1, pcol = -1;     // pivot block (the paper's M_22 after permutation)
-  std::vector<PFrame> f;        // f[0] is the root
-  std::vector<std::vector<int>> level;  // level[p] = ids of frames of order p
+  int k = 0;
+  std::vector<std::pair<int, int>> reqs;  // requested blocks (i, j), 0-based
+  std::vector<int> roots;                 // frame id of each request's root
+  std::vector<PFrame> f;
+  std::vector<std::vector<int>> level;    // level[p] = ids of frames of order p
   size_t nonleaf = 0, leaves = 0;
+  size_t request_frames = 0;              // sum over requests of their own distinct frames
 };
 
-Plan build_plan(int k, int i, int j, bool pad_last);
+// The frame DAG of several requests on one k x k grid, built request by
+// request as the paper's forward procedure prescribes and merged by value.
+Plan build_plan(int k, const std::vector<std::pair<int, int>>& reqs, bool pad_last);
+inline Plan build_plan(int k, int i, int j, bool pad_last) { return build_plan(k, {{i, j}}, pad_last); }
 
 // Operand reference of a scheduled operation.
 struct Ref {
   enum Kind : int { NONE = 0, MBLK = 1, SLOT = 2, OUT = 3 } kind = NONE;
   int r = 0, c = 0;  // block coordinates for MBLK
-  int slot = -1;     // slot id for SLOT
+  int slot = -1;     // slot id for SLOT; request index for OUT
 };
 
 struct GemmOp {  // C = alpha * A * B + beta * Cin, all b x b
@@ -59,16 +70,20 @@ struct Step {
 
 struct Schedule {
   std::vector<Step> steps;
+  int nouts = 1;       // requests: Ref::OUT's slot field indexes them
   int nslots = 0;      // peak number of b x b value slots alive at once
   int max_inv_batch = 0;
   double gemm_flops_units = 0;  // in units of b^3 (2 per product)
   double inv_units = 0;         // in units of b^3 (2 per inverse)
   size_t frames = 0, inversions = 0;
+  size_t request_frames = 0;    // frames the requests would evaluate one by one
   int inv_chunk = 0;            // matrices per inverse launch chosen to fit the cap
+  size_t planned = 0;           // device bytes of its workspace with that chunk
 };
 
-// Builds the level-by-level schedule of one request.  zchunk bounds the
-// number of Schur temporaries alive at once (0 = a whole level).
+// Builds the level-by-level schedule of a plan (one or several requests).
+// zchunk bounds the number of Schur temporaries alive at once (0 = a whole
+// level).
 Schedule build_schedule(const Plan& p, int zchunk);
 
 // --------------------------------------------------------------- kernels

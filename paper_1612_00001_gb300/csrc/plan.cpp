@@ -10,13 +10,18 @@
 // 2x2-assembled frame by the Schur complement its role names: A -> (./D),
 // B -> (./C), C -> (./B), D -> (./A) (Eqs. SchurofA-SchurofD, Phi_A-Phi_D).
 //
-// A frame's value depends only on its identity: the kept block row and
-// column and the sets of eliminated block rows and columns.  The planner
-// builds the recursion once, shares every frame that appears under several
-// parents (the reuse across branches that Sec. 8 proposes), and orders the
-// distinct frames by order (level), so that each level runs as a few grouped
-// launches.
+// Within one request a frame's value depends only on its identity: the kept
+// block row and column and the sets of eliminated block rows and columns, so
+// the planner visits each identity once (the reuse across branches that
+// Sec. 8 proposes).  Across requests - the k^2 runs of Sec. 5, or any group
+// of blocks - frames are merged by what they compute: the same four operand
+// frames (or, for a leaf, the same kept block and pivot block), so a merged
+// frame rounds exactly as it would in each request alone.  The distinct
+// frames are then ordered by order (level), so that each level runs as a few
+// grouped launches, and the products piv^-1 * right that several frames
+// share are formed once.
 #include <algorithm>
+#include <array>
 #include <cstdint>
 #include <map>
 #include <stdexcept>
@@ -44,7 +49,18 @@ struct KeyHash {
 
 struct Builder {
   Plan* P;
-  std::unordered_map<Key, int, KeyHash> memo;
+  int prow = -1, pcol = -1;                    // pivot block of the current request
+  std::unordered_map<Key, int, KeyHash> memo;  // identity -> frame, per request
+  std::map<std::array<int, 5>, int> cons;      // computation -> frame, all requests
+
+  int make(const std::array<int, 5>& ck, const PFrame& fr) {
+    auto it = cons.find(ck);
+    if (it != cons.end()) return it->second;
+    const int id = (int)P->f.size();
+    P->f.push_back(fr);
+    cons.emplace(ck, id);
+    return id;
+  }
 
   int visit(const std::vector<int>& rows, const std::vector<int>& cols, int role) {
     const int p = (int)rows.size();
@@ -57,15 +73,11 @@ struct Builder {
     }
     auto it = memo.find(key);
     if (it != memo.end()) return it->second;
-    const int id = (int)P->f.size();
-    P->f.emplace_back();
-    memo.emplace(key, id);
     PFrame fr;
     fr.order = p;
-    fr.role = role;
-    fr.krow = kr;
-    fr.kcol = kc;
+    int id;
     if (p >= 3) {
+      int child[4];
       for (int ch = 0; ch < 4; ++ch) {
         // A: drop last row and last col; B: drop last row, first col;
         // C: drop first row, last col;  D: drop first row, first col.
@@ -74,72 +86,91 @@ struct Builder {
         std::vector<int> cr(rows.begin() + r0, rows.begin() + r0 + p - 1);
         std::vector<int> cc(cols.begin() + c0, cols.begin() + c0 + p - 1);
         if (p - 1 >= 3) {
-          if (cr[0] == P->prow) std::swap(cr[0], cr[1]);
-          if (cc[0] == P->pcol) std::swap(cc[0], cc[1]);
+          if (cr[0] == prow) std::swap(cr[0], cr[1]);
+          if (cc[0] == pcol) std::swap(cc[0], cc[1]);
         }
-        fr.child[ch] = visit(cr, cc, ch);
+        child[ch] = visit(cr, cc, ch);
       }
       // (kept, left, pivot, right) by role: value = kept - left * pivot^-1 * right
       static const int KLPR[4][4] = {{0, 1, 3, 2},   // A: a - b d^-1 c
                                      {1, 0, 2, 3},   // B: b - a c^-1 d
                                      {2, 3, 1, 0},   // C: c - d b^-1 a
                                      {3, 2, 0, 1}};  // D: d - c a^-1 b
-      fr.kept = fr.child[KLPR[role][0]];
-      fr.left = fr.child[KLPR[role][1]];
-      fr.piv = fr.child[KLPR[role][2]];
-      fr.right = fr.child[KLPR[role][3]];
+      fr.kept = child[KLPR[role][0]];
+      fr.left = child[KLPR[role][1]];
+      fr.piv = child[KLPR[role][2]];
+      fr.right = child[KLPR[role][3]];
+      id = make({1, fr.kept, fr.left, fr.piv, fr.right}, fr);
+    } else {
+      fr.krow = kr;
+      fr.kcol = kc;
+      fr.prow = prow;
+      fr.pcol = pcol;
+      id = make({0, kr, kc, prow, pcol}, fr);
     }
-    P->f[id] = fr;
+    memo.emplace(key, id);
     return id;
   }
 };
 
-}  // namespace
-
-Plan build_plan(int k, int i, int j, bool pad_last) {
-  if (k < 2 || k > 63 || i < 0 || j < 0 || i >= k || j >= k) throw std::invalid_argument("bad plan request");
-  Plan P;
-  P.k = k;
-  P.i = i;
-  P.j = j;
-  // Root lists for block (i, j): (P M Q)^-1 = Q^T M^-1 P^T, so rows start
-  // with j and columns with i; the other indices keep their order.  When the
-  // last block is padding (k does not divide n) and the request does not
-  // touch it, it is placed second in both lists: it is then the pivot index,
-  // eliminated in every frame, so no frame keeps padded rows or columns.
+// Root lists for block (i, j): (P M Q)^-1 = Q^T M^-1 P^T, so rows start with
+// j and columns with i; the other indices keep their order.  When the last
+// block is padding (k does not divide n) and the request does not touch it,
+// it is placed second in both lists: it is then the pivot index, eliminated
+// in every frame, so no frame keeps padded rows or columns.
+void root_lists(int k, int i, int j, bool pad_last, std::vector<int>* rows, std::vector<int>* cols) {
   const int last = k - 1;
+  rows->clear();
+  cols->clear();
   if (pad_last && k >= 3 && i != last && j != last) {
-    P.rows = {j, last};
-    P.cols = {i, last};
+    *rows = {j, last};
+    *cols = {i, last};
     for (int x = 0; x < last; ++x)
       if (x != i && x != j) {
-        P.rows.push_back(x);
-        P.cols.push_back(x);
+        rows->push_back(x);
+        cols->push_back(x);
       }
     if (i != j) {
-      P.rows.push_back(i);
-      P.cols.push_back(j);
+      rows->push_back(i);
+      cols->push_back(j);
     }
   } else if (i == j) {
-    P.rows.push_back(i);
+    rows->push_back(i);
     for (int x = 0; x < k; ++x)
-      if (x != i) P.rows.push_back(x);
-    P.cols = P.rows;
+      if (x != i) rows->push_back(x);
+    *cols = *rows;
   } else {
-    P.rows.push_back(j);
-    P.cols.push_back(i);
+    rows->push_back(j);
+    cols->push_back(i);
     for (int x = 0; x < k; ++x)
       if (x != i && x != j) {
-        P.rows.push_back(x);
-        P.cols.push_back(x);
+        rows->push_back(x);
+        cols->push_back(x);
       }
-    P.rows.push_back(i);
-    P.cols.push_back(j);
+    rows->push_back(i);
+    cols->push_back(j);
   }
-  P.prow = P.rows[1];
-  P.pcol = P.cols[1];
-  Builder B{&P, {}};
-  B.visit(P.rows, P.cols, 0);
+}
+
+}  // namespace
+
+Plan build_plan(int k, const std::vector<std::pair<int, int>>& reqs, bool pad_last) {
+  if (k < 2 || k > 63 || reqs.empty()) throw std::invalid_argument("bad plan request");
+  Plan P;
+  P.k = k;
+  P.reqs = reqs;
+  Builder B{&P};
+  for (const auto& ij : reqs) {
+    const int i = ij.first, j = ij.second;
+    if (i < 0 || j < 0 || i >= k || j >= k) throw std::invalid_argument("bad plan request");
+    std::vector<int> rows, cols;
+    root_lists(k, i, j, pad_last, &rows, &cols);
+    B.prow = rows[1];
+    B.pcol = cols[1];
+    B.memo.clear();
+    P.roots.push_back(B.visit(rows, cols, 0));
+    P.request_frames += B.memo.size();
+  }
   P.level.assign(k + 1, {});
   for (int id = 0; id < (int)P.f.size(); ++id) P.level[P.f[id].order].push_back(id);
   P.leaves = P.level[2].size();
@@ -185,9 +216,10 @@ Ref slot(int s) {
   x.slot = s;
   return x;
 }
-Ref outref() {
+Ref outref(int r) {
   Ref x;
   x.kind = Ref::OUT;
+  x.slot = r;
   return x;
 }
 
@@ -198,31 +230,40 @@ Schedule build_schedule(const Plan& P, int zchunk) {
   SlotPool pool;
   std::vector<int> val(P.f.size(), -1);  // slot of each frame's value
   const int k = P.k;
+  S.nouts = (int)P.roots.size();
 
-  // ---- level 2 (Backward Step 1): every leaf pivots on P = M[prow, pcol]
+  // ---- level 2 (Backward Step 1): a leaf pivots on its request's block
+  // P = M[prow, pcol]; every distinct pivot block is inverted once and every
+  // distinct T = P^-1 M[prow, c] formed once
   {
     const std::vector<int>& lv = P.level[2];
+    std::map<std::pair<int, int>, int> pinv;         // (prow, pcol) -> slot of P^-1
+    std::map<std::tuple<int, int, int>, int> tcol;   // (prow, pcol, c) -> slot of T
+    for (int id : lv) {
+      const PFrame& fr = P.f[id];
+      pinv[{fr.prow, fr.pcol}] = -1;
+      tcol[std::make_tuple(fr.prow, fr.pcol, fr.kcol)] = -1;
+    }
     Step inv;
     inv.kind = Step::INV;
-    const int pinv = pool.get();
-    InvOp io;
-    io.src = mblk(P.prow, P.pcol);
-    io.dst = slot(pinv);
-    inv.inv.push_back(io);
+    for (auto& kv : pinv) {
+      kv.second = pool.get();
+      InvOp io;
+      io.src = mblk(kv.first.first, kv.first.second);
+      io.dst = slot(kv.second);
+      inv.inv.push_back(io);
+    }
     S.steps.push_back(inv);
-    S.inv_units += 2;
-    S.inversions += 1;
-    S.max_inv_batch = std::max(S.max_inv_batch, 1);
-    // T_c = P^-1 M[prow, c] for every distinct leaf column c
-    std::map<int, int> tcol;
-    for (int id : lv) tcol[P.f[id].kcol] = -1;
+    S.inv_units += 2.0 * (double)pinv.size();
+    S.inversions += pinv.size();
+    S.max_inv_batch = std::max(S.max_inv_batch, (int)pinv.size());
     Step g1;
     g1.kind = Step::GEMM;
     for (auto& kv : tcol) {
       kv.second = pool.get();
       GemmOp g;
-      g.A = slot(pinv);
-      g.B = mblk(P.prow, kv.first);
+      g.A = slot(pinv[{std::get<0>(kv.first), std::get<1>(kv.first)}]);
+      g.B = mblk(std::get<0>(kv.first), std::get<2>(kv.first));
       g.C = slot(kv.second);
       g.alpha = 1.0;
       g.beta = 0.0;
@@ -235,8 +276,8 @@ Schedule build_schedule(const Plan& P, int zchunk) {
       const PFrame& fr = P.f[id];
       val[id] = pool.get();
       GemmOp g;  // leaf = M[a,c] - M[a,pc] T_c
-      g.A = mblk(fr.krow, P.pcol);
-      g.B = slot(tcol[fr.kcol]);
+      g.A = mblk(fr.krow, fr.pcol);
+      g.B = slot(tcol[std::make_tuple(fr.prow, fr.pcol, fr.kcol)]);
       g.Cin = mblk(fr.krow, fr.kcol);
       g.C = slot(val[id]);
       g.alpha = -1.0;
@@ -245,11 +286,12 @@ Schedule build_schedule(const Plan& P, int zchunk) {
     }
     S.steps.push_back(g2);
     S.gemm_flops_units += 2.0 * (double)(tcol.size() + lv.size());
-    pool.put(pinv);
+    for (auto& kv : pinv) pool.put(kv.second);
     for (auto& kv : tcol) pool.put(kv.second);
   }
 
-  // ---- levels 3..k (Backward Steps 2..k-1): X = kept - left * (piv^-1 * right)
+  // ---- levels 3..k (Backward Steps 2..k-1): X = kept - left * Z with
+  // Z = piv^-1 * right formed once per distinct (piv, right)
   for (int p = 3; p <= k; ++p) {
     const std::vector<int>& lv = P.level[p];
     std::map<int, int> pinv;  // pivot frame -> slot of its inverse
@@ -269,25 +311,43 @@ Schedule build_schedule(const Plan& P, int zchunk) {
     S.inversions += pinv.size();
     S.steps.push_back(inv);
     for (int id : lv) val[id] = pool.get();
-    const int nz = (zchunk > 0) ? std::min<int>(zchunk, (int)lv.size()) : (int)lv.size();
+    // distinct Z keys in order of first use; the level's frames grouped by
+    // their Z key so that a chunk of keys serves a contiguous run of frames
+    std::map<std::pair<int, int>, int> zidx;
+    std::vector<std::pair<int, int>> zkeys;
+    for (int id : lv) {
+      const std::pair<int, int> zk{P.f[id].piv, P.f[id].right};
+      if (zidx.emplace(zk, (int)zkeys.size()).second) zkeys.push_back(zk);
+    }
+    std::vector<int> order(lv.begin(), lv.end());
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return zidx[{P.f[a].piv, P.f[a].right}] < zidx[{P.f[b].piv, P.f[b].right}];
+    });
+    const int nzk = (int)zkeys.size();
+    const int nz = (zchunk > 0) ? std::min(zchunk, nzk) : nzk;
     std::vector<int> z(nz);
     for (int t = 0; t < nz; ++t) z[t] = pool.get();
-    for (size_t c0 = 0; c0 < lv.size(); c0 += nz) {
-      const size_t c1 = std::min(lv.size(), c0 + nz);
+    size_t f0 = 0;
+    for (int c0 = 0; c0 < nzk; c0 += nz) {
+      const int c1 = std::min(nzk, c0 + nz);
       Step g1, g2;
       g1.kind = g2.kind = Step::GEMM;
-      for (size_t t = c0; t < c1; ++t) {
-        const PFrame& fr = P.f[lv[t]];
+      for (int t = c0; t < c1; ++t) {
         GemmOp a;  // Z = piv^-1 * right
-        a.A = slot(pinv[fr.piv]);
-        a.B = slot(val[fr.right]);
+        a.A = slot(pinv[zkeys[t].first]);
+        a.B = slot(val[zkeys[t].second]);
         a.C = slot(z[t - c0]);
         g1.gemm.push_back(a);
+      }
+      for (; f0 < order.size(); ++f0) {
+        const PFrame& fr = P.f[order[f0]];
+        const int t = zidx[{fr.piv, fr.right}];
+        if (t >= c1) break;
         GemmOp b;  // X = kept - left * Z
         b.A = slot(val[fr.left]);
         b.B = slot(z[t - c0]);
         b.Cin = slot(val[fr.kept]);
-        b.C = slot(val[lv[t]]);
+        b.C = slot(val[order[f0]]);
         b.alpha = -1.0;
         b.beta = 1.0;
         g2.gemm.push_back(b);
@@ -295,7 +355,7 @@ Schedule build_schedule(const Plan& P, int zchunk) {
       S.steps.push_back(g1);
       S.steps.push_back(g2);
     }
-    S.gemm_flops_units += 4.0 * (double)lv.size();
+    S.gemm_flops_units += 2.0 * (double)(nzk + lv.size());
     for (int t = 0; t < nz; ++t) pool.put(z[t]);
     for (auto& kv : pinv) pool.put(kv.second);
     for (int id : P.level[p - 1]) {
@@ -304,21 +364,25 @@ Schedule build_schedule(const Plan& P, int zchunk) {
     }
   }
 
-  // ---- root (Eq. blockmatrix_NxN): N = (root value)^-1
+  // ---- roots (Eq. blockmatrix_NxN): N = (root value)^-1 for every request
   {
     Step inv;
     inv.kind = Step::INV;
-    InvOp io;
-    io.src = slot(val[0]);
-    io.dst = outref();
-    io.frame = 0;
-    inv.inv.push_back(io);
+    for (size_t r = 0; r < P.roots.size(); ++r) {
+      InvOp io;
+      io.src = slot(val[P.roots[r]]);
+      io.dst = outref((int)r);
+      io.frame = P.roots[r];
+      inv.inv.push_back(io);
+    }
+    S.max_inv_batch = std::max(S.max_inv_batch, (int)inv.inv.size());
     S.steps.push_back(inv);
-    S.inv_units += 2;
-    S.inversions += 1;
+    S.inv_units += 2.0 * (double)P.roots.size();
+    S.inversions += P.roots.size();
   }
   S.nslots = pool.peak;
   S.frames = P.f.size();
+  S.request_frames = P.request_frames;
   return S;
 }
 

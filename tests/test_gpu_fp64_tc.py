@@ -66,12 +66,16 @@ def test_haar_matrix_kappa_1e4(mb):
         assert err <= tol, (i, j, err, tol)
 
 
-def test_close_to_plain_fp64_path(mb):
+@pytest.mark.parametrize("prec", ["fp64_tc", "fp64"])
+def test_k8_block_against_oracle(mb, prec):
+    """n = 2048, k = 8 (b = 256): both FP64-valued paths against the oracle
+    at the FP64 bar, max(1e-11, 10 x floor)."""
     m = bi.uniform_shift(2048, 5)
-    a = to_np(mb.Context(dev(m), 8).block(3, 6))
-    c = to_np(mb.Context(dev(m), 8, precision=P).block(3, 6))
-    floor = oracle.sensitivity_floor(m, 8, 3, 6)
-    assert oracle.rel_fro(c, a) <= max(TOL_FP64, 10 * floor)
+    for i, j in [(3, 6), (0, 0)]:
+        got = to_np(mb.Context(dev(m), 8, precision=prec).block(i, j))
+        tol, floor = parity_tol(m, 8, i, j, TOL_FP64)
+        err = oracle.rel_fro(got, oracle_block(m, 8, i, j))
+        assert err <= tol, (prec, i, j, err, tol, floor)
 
 
 def test_padding_border(mb):
@@ -228,3 +232,45 @@ def test_full_size_bench_configuration(mb):
     e_oracle = oracle.rel_fro(ref, inv[i * b:(i + 1) * b, j * b:(j + 1) * b])
     got = outs[ij.index((i, j))]
     assert oracle.rel_fro(got, ref) <= e_oracle + 2e-10, (oracle.rel_fro(got, ref), e_oracle)
+
+
+def test_all_blocks_merged_and_resumable(mb):
+    """n = 1024, k = 8 (b = 128): the 64 runs merged in one call evaluate 6116
+    distinct frames instead of 64 x 270.  A call interrupted after its first
+    24 blocks (the others marked done) and resumed with those 24 marked done
+    writes exactly the uninterrupted result, each block reported once by the
+    callback; sampled blocks match the oracle at the FP64 bar."""
+    n, k = 1024, 8
+    b = n // k
+    m = bi.uniform_shift(n, 7)
+    with mb.Context(dev(m), k, precision=P) as ctx:
+        full = to_np(ctx.all_blocks())
+        rep = ctx.last_report
+        assert (rep["frames"], rep["request_frames"]) == (6116, 17280)
+        out = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+        seen = []
+        ctx.all_blocks(out=out, done=[0 if t < 24 else 1 for t in range(k * k)],
+                       callback=lambda i, j: seen.append((i, j)))
+        assert seen == [(t // k, t % k) for t in range(24)]
+        ctx.all_blocks(out=out, done=[1 if t < 24 else 0 for t in range(k * k)],
+                       callback=lambda i, j: seen.append((i, j)))
+        assert sorted(seen) == [(i, j) for i in range(k) for j in range(k)]
+        assert np.array_equal(to_np(out), full)
+    for i, j in [(0, 0), (3, 5), (7, 2)]:
+        tol, floor = parity_tol(m, k, i, j, TOL_FP64)
+        err = oracle.rel_fro(full[i * b:(i + 1) * b, j * b:(j + 1) * b], oracle_block(m, k, i, j))
+        assert err <= tol, (i, j, err, tol)
+
+
+def test_merged_runs_bitwise_equal_runs_alone_with_padding(mb):
+    """k does not divide n (the bordered matrix of Sec. 3): requests of every
+    border kind merged in one call equal their runs alone bit for bit."""
+    n, k = 250, 4
+    m = bi.uniform_shift(n, 9)
+    ij = [(i, j) for i in range(k) for j in range(k)]
+    with mb.Context(dev(m), k, precision=P, pad_seed=3) as ctx:
+        together = [to_np(x) for x in ctx.blocks(ij, width=len(ij))]
+        assert ctx.last_report["frames"] < ctx.last_report["request_frames"]
+    for (i, j), t in zip(ij, together):
+        with mb.Context(dev(m), k, precision=P, pad_seed=3) as c1:
+            assert np.array_equal(t, to_np(c1.block(i, j))), (i, j)

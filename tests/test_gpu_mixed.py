@@ -73,19 +73,37 @@ def test_mixed_refined_reaches_fp64_accuracy(mb):
         assert ctx.last_report["rel_residual"] < 1e-3
 
 
-def test_mixed_all_blocks_batched_levels(mb):
-    """n = 512, k = 8 (b = 64): 270 frames, grouped launches of up to 100
-    products."""
+def _mixed_k8(mb, i, j):
     m = bi.uniform_shift(512, 2)
     M = torch.tensor(m, dtype=torch.float32, device="cuda")
-    ctx = mb.Context(M, 8, precision="mixed")
+    got = to_np(mb.Context(M, 8, precision="mixed").block(i, j))
     ref32 = m.astype(np.float32).astype(np.float64)
-    for i, j in [(0, 0), (5, 2)]:
-        got = to_np(ctx.block(i, j))
-        ref = oracle_block(ref32, 8, i, j)
-        # FP32 frame values: the k = 8 recursion amplifies rounding ~1e4-1e6x
-        tol = max(1e-3, 1e9 * oracle.sensitivity_floor(ref32, 8, i, j))
-        assert oracle.rel_fro(got, ref) < tol
+    floor = oracle.sensitivity_floor(ref32, 8, i, j)
+    return got, oracle.rel_fro(got, oracle_block(ref32, 8, i, j)), floor
+
+
+def test_mixed_k8_block00_meets_the_fp32_bar(mb):
+    """n = 512, k = 8 (b = 64): 270 frames, grouped launches of up to 100
+    products.  Block (0,0) meets the parity rule max(1e-4, 10 x floor)."""
+    got, err, floor = _mixed_k8(mb, 0, 0)
+    assert err <= max(1e-4, 10.0 * floor), (err, floor)
+
+
+@pytest.mark.parametrize("i,j", [(5, 2), (7, 0)])
+def test_mixed_k8_offdiagonal_misses_the_fp32_bar(mb, i, j):
+    """The same matrix, off-diagonal blocks: the parity rule is NOT met and the
+    test states so.  FP32 frame values carry unit roundoff 2^-24 and the k = 8
+    recursion amplifies rounding by floor / 2^-53 (the oracle's own
+    sensitivity at FP64), so the expected error is near 2^29 x floor, far
+    above 10 x floor.  Asserted: the error is above the bar, and within
+    10 x the floor scaled to FP32 unit roundoff (a wrong result still fails).
+    One refinement step does not rescue such a sweep (its error squared
+    stays far above 1e-10)."""
+    got, err, floor = _mixed_k8(mb, i, j)
+    bar = max(1e-4, 10.0 * floor)
+    assert np.isfinite(got).all()
+    assert err > bar, ("the FP32-valued sweep met the FP32 bar", err, bar)
+    assert err <= 10.0 * 2.0 ** 29 * floor, (err, floor)
 
 
 def test_mixed_refined_many_blocks_share_rows_and_columns(mb):
