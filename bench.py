@@ -81,6 +81,11 @@ def parse():
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--batched", type=int, default=0,
                    help="batched workload: this many independent matrices of uneven n and k, one block each")
+    p.add_argument("--large", action="store_true",
+                   help="memory-bounded workload: n x n Householder matrix in FP32 host memory under a device cap, "
+                        "one block per step by the bounded schedule (use --n 65536 --k 16)")
+    p.add_argument("--cap-gb", type=float, default=24.0)
+    p.add_argument("--block", type=int, nargs=2, default=[0, 15])
     p.add_argument("--backward", action="store_true",
                    help="differentiation workload: one block forward and the adjoint backward per step")
     args = p.parse_args()
@@ -217,6 +222,60 @@ def fp64_path_arm(args, M, k, b, bps, rank, world, first_block, m_host):
     return {"value": bps / secs, "unit": "blocks/s", "ms_per_step": 1e3 * secs, "steps": 1,
             "max_rel_err_vs_dense_inverse": max(errs), "refine": args.refine,
             "rel_diff_of_headline_block": diff}
+
+
+def householder_svd_device(n, kappa, seed, reflectors=64):
+    """M = U diag(sigma) V^T (the Householder construction of bri_inputs, the
+    same reflector vectors) built on the GPU in FP64 for sizes the host
+    cannot handle; returns (M on the device, vu, vv, sigma)."""
+    import torch
+
+    import bri_inputs as bi
+    vu = torch.tensor(bi.gaussian(seed, bi.STREAM_HOUSE, reflectors * n).reshape(reflectors, n), device="cuda")
+    vv = torch.tensor(bi.gaussian(seed + 0x5151, bi.STREAM_HOUSE, reflectors * n).reshape(reflectors, n),
+                      device="cuda")
+    sig = torch.tensor(bi.log_spaced(n, kappa), device="cuda")
+    m = torch.diag(sig)
+    for v in reversed(vu):  # U X = H_1 (H_2 (... H_r X))
+        m.addr_(v, v @ m, alpha=-2.0 / float(v @ v))
+    for v in reversed(vv):  # X V^T = X H_r ... H_1
+        m.addr_(m @ v, v, alpha=-2.0 / float(v @ v))
+    return m, vu, vv, sig
+
+
+def householder_inverse_columns(vu, vv, sig, j0, j1):
+    """Columns j0..j1-1 of M^-1 = V diag(1/sigma) U^T in closed form (FP64)."""
+    import torch
+    n = sig.shape[0]
+    y = torch.zeros((n, j1 - j0), dtype=torch.float64, device="cuda")
+    y[j0:j1] = torch.eye(j1 - j0, dtype=torch.float64, device="cuda")
+    for v in vu:  # U^T Y = H_r (... (H_1 Y))
+        y.addr_(v, v @ y, alpha=-2.0 / float(v @ v))
+    y.div_(sig[:, None])
+    for v in reversed(vv):  # V Y = H_1 (... (H_r Y))
+        y.addr_(v, v @ y, alpha=-2.0 / float(v @ v))
+    return y
+
+
+def stored_inverse_columns(m_stored, vu, vv, sig, j0, j1, iters=2):
+    """Columns j0..j1-1 of the inverse of the stored matrix (FP32 entries
+    taken exactly): the closed form for the unrounded matrix, corrected by
+    iterative refinement against the stored one (FP64 products)."""
+    import torch
+    y = householder_inverse_columns(vu, vv, sig, j0, j1)
+    n = m_stored.shape[0]
+    for _ in range(iters):
+        r = -(m_stored @ y)
+        r[j0:j1] += torch.eye(j1 - j0, dtype=torch.float64, device="cuda")
+        # apply M^-1 in closed form to the residual columns
+        for v in vu:
+            r.addr_(v, v @ r, alpha=-2.0 / float(v @ v))
+        r.div_(sig[:, None])
+        for v in reversed(vv):
+            r.addr_(v, v @ r, alpha=-2.0 / float(v @ v))
+        y += r
+        del r
+    return y
 
 
 def make_matrix(args, n):
@@ -449,6 +508,83 @@ def run_inverses(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_large(args, rank, world, dist):
+    """The memory-bounded workload: n = 65536, k = 16 (b = 4096), M = U diag(sigma)
+    V^T with U, V each a product of 64 Householder reflectors, cond(M) = kappa,
+    stored in FP32 (17.2 GB) in pinned host memory; a device cap (24 GB); one
+    block N_ij per step through the C ABI with the bounded schedule (frames
+    depth first in the slots the cap leaves, values needed later in pinned host
+    memory, M read block by block), FP64_TC arithmetic, the block returned in
+    FP64.  Its error is taken against the inverse of the stored FP32 matrix:
+    the closed form V diag(1/sigma) U^T of the unrounded matrix, corrected by
+    two steps of iterative refinement with FP64 products."""
+    import numpy as np
+    import torch
+
+    import paper_1612_00001_gb300 as mb
+    n, k = args.n, args.k
+    b = n // k
+    cap = int(args.cap_gb * 1e9)
+    m64, vu, vv, sig = householder_svd_device(n, args.kappa, 0)
+    m32 = m64.to(torch.float32)
+    del m64
+    torch.cuda.empty_cache()
+    mh = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+    mh.copy_(m32)
+    i, j = args.block
+    stream = torch.cuda.current_stream()
+    out = torch.empty((b, b), dtype=torch.float64, device="cuda")
+    ctx = mb.Context(mh, k, precision=args.precision, cap=cap, out_dtype=torch.float64)
+    for _ in range(args.warmup):
+        ctx.block(i, j, out=out)
+    clocks = _clock_region(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = []
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        ctx.block(i, j, out=out)
+        ev[s][1].record(stream)
+        reps.append(ctx.last_report)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
+    rep = reps[-1]
+    ctx.close()
+    # the inverse of the stored matrix, block column j, rows of block i
+    ms = m32.to(torch.float64)
+    del m32
+    y = stored_inverse_columns(ms, vu, vv, sig, j * b, (j + 1) * b)
+    ref = y[i * b:(i + 1) * b].clone()
+    del y, ms
+    err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
+    closed = householder_inverse_columns(vu, vv, sig, j * b, (j + 1) * b)[i * b:(i + 1) * b]
+    err_unrounded = float(torch.linalg.norm(out - closed) / torch.linalg.norm(closed))
+    flops = rep["gemm_flops"] + rep["inv_flops"]
+    line = {"metric": METRIC, "value": args.steps / secs, "unit": "blocks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(args),
+            "data": "synthetic",
+            "config": {"workload": f"n={n} k={k} b={b} U diag(sigma) V^T (64 Householder reflectors each), "
+                                   f"cond {args.kappa:g}, FP32 storage in pinned host memory, device cap "
+                                   f"{args.cap_gb:g} GB, block ({i},{j}), bounded schedule ({args.precision})",
+                       "device_cap_bytes": cap, "peak_device_bytes": rep["peak_device_bytes"],
+                       "planned_device_bytes": rep["planned_device_bytes"],
+                       "host_in_bytes": rep["host_in_bytes"], "host_out_bytes": rep["host_out_bytes"],
+                       "host_spill_bytes": rep["host_spill_bytes"], "frames": rep["frames"],
+                       "inversions": rep["inversions"], "launches": rep["launches"],
+                       "fp64_equivalent_tflops": flops / secs / 1e12,
+                       "rel_err_vs_inverse_of_stored_matrix": err,
+                       "rel_err_vs_inverse_of_unrounded_matrix": err_unrounded,
+                       "wall_seconds": wall,
+                       "launches_per_block": rep["launches"]},
+            "gpu_launches": rep["launches"] * args.steps, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_backward(args, rank, world, dist):
     """Differentiation: L = sum(W * N_ij), W ~ N(0,1); a step is the forward
     block and dL/dM = -(X_i)^T W (Y_j)^T, the block row and column recomputed
@@ -533,6 +669,8 @@ def main():
         return run_inverses(args, rank, world, dist)
     if args.backward:
         return run_backward(args, rank, world, dist)
+    if args.large:
+        return run_large(args, rank, world, dist)
     n, k = args.n, args.k
     b = -(-n // k)
     bps = args.blocks_per_step

@@ -44,7 +44,8 @@ typedef enum {
     MBINV_ENOTCONV = 4,
     MBINV_ETIMEOUT = 5,
     MBINV_ECUDA = 6,
-    MBINV_ENOTSUP = 7
+    MBINV_ENOTSUP = 7,
+    MBINV_ECALLBACK = 8         /* a block producer (mbinv_block_fn) failed */
 } mbinv_status;
 
 /* Element type of M, of the outputs and of G / dM. */
@@ -71,6 +72,24 @@ typedef enum { MBINV_DTYPE_F64 = 0, MBINV_DTYPE_F32 = 1 } mbinv_dtype;
  *                     run its FP64 products on the tensor pipe). */
 typedef enum { MBINV_FP64 = 0, MBINV_FP32 = 1, MBINV_MIXED_BF16 = 2, MBINV_FP64_TC = 3 } mbinv_precision;
 
+/* Order of evaluation (Sec. 5-6: the method's point is a bounded memory
+ * footprint; its cost is recomputation or, here, traffic to host memory).
+ *   MBINV_SCHEDULE_AUTO     level by level when that fits device_cap_bytes,
+ *                           else MBINV_SCHEDULE_BOUNDED; M stays in host
+ *                           memory when it is there and its device copy
+ *                           alone would not fit the cap.
+ *   MBINV_SCHEDULE_LEVELS   level by level, every frame of an order in the
+ *                           same grouped launches; MBINV_ENOMEM_CAP when the
+ *                           smallest chunking does not fit.
+ *   MBINV_SCHEDULE_BOUNDED  depth first, one operation per launch sequence,
+ *                           in as many b x b device slots as the cap leaves;
+ *                           values needed again later wait in pinned host
+ *                           memory (the one needed last goes first), and a
+ *                           host M is read block by block as it is needed.
+ *                           Not with MBINV_MIXED_BF16 or k not dividing n
+ *                           (MBINV_ENOTSUP). */
+typedef enum { MBINV_SCHEDULE_AUTO = 0, MBINV_SCHEDULE_LEVELS = 1, MBINV_SCHEDULE_BOUNDED = 2 } mbinv_schedule;
+
 typedef struct {
     size_t struct_size;         /* sizeof(mbinv_options) */
     mbinv_precision precision;
@@ -87,7 +106,23 @@ typedef struct {
                                    does not divide n */
     int profile;                /* 1: time every launch with CUDA events and
                                    report device seconds per kernel family */
-    int reserved[7];
+    int schedule;               /* an mbinv_schedule: how the frames are
+                                   ordered and where M lives */
+    int out_dtype;              /* type of the returned blocks: 0 = M's
+                                   type, 1 = FP64, 2 = FP32 (an FP32 M whose
+                                   blocks are computed in FP64 can return
+                                   them in FP64) */
+    double sing_tol;            /* a pivot is singular when its largest
+                                   candidate is at most sing_tol times the
+                                   matrix's largest magnitude; 0 = b times
+                                   the unit roundoff of the working type */
+    int no_graphs;              /* 1: never replay a CUDA graph.  0: a call
+                                   whose launch sequence equals the previous
+                                   call's on this context (same blocks,
+                                   buffers and schedule; not profiled; no
+                                   host copies) is captured into a graph
+                                   the second time and replayed after */
+    int reserved[3];
 } mbinv_options;
 
 typedef struct {
@@ -134,9 +169,46 @@ typedef struct {
     double pack_bytes;          /* algorithmic bytes of operand packing:
                                    FP64_TC 8 B read and 16 B of digits
                                    written per operand entry, 4 B per row */
+    double host_in_bytes;       /* bounded schedule: bytes copied host ->
+                                   device (blocks of a host M, values
+                                   brought back) */
+    double host_out_bytes;      /* bounded schedule: bytes of values spilled
+                                   to host memory */
+    size_t host_spill_bytes;    /* bounded schedule: pinned host memory the
+                                   spilled values took at once */
+    size_t graph_replays;       /* launch sequences replayed from a CUDA
+                                   graph during the call */
+    double max_pivot_cond;      /* largest 1-norm condition estimate
+                                   ||P||_1 ||P^-1||_1 over the inverted
+                                   pivots (0 when not computed) */
 } mbinv_report;
 
 typedef struct mbinv_ctx mbinv_ctx;
+
+/* Producer of M for a context that does not store it (Sec. 5: a matrix that
+ * can be computed element by element need not be stored, as in LS-SVM
+ * training).  Writes M[r0 : r0 + rows, c0 : c0 + cols] (element offsets,
+ * 0-based) into dst - device memory, row-major, leading dimension ldd, of
+ * type dtype (an mbinv_dtype) - with its work ordered on the CUDA stream
+ * `stream`, which it must not synchronise with other streams' work on dst.
+ * Returns 0, or nonzero to fail the call with MBINV_ECALLBACK. */
+typedef int (*mbinv_block_fn)(int64_t r0, int64_t c0, int64_t rows, int64_t cols, void *dst, int64_t ldd,
+                              int dtype, void *stream, void *user);
+
+/* The LS-SVM matrix of Sec. 7, Eq. A, as a producer: with n points x_1..x_n
+ * of dimension dim,
+ *     A_gamma = [[0, 1^T], [1, K + I / gamma]],  K_pq = exp(-|x_p - x_q|^2 / (2 sigma^2)),
+ * of order n + 1 (row and column 0 are the border).  Pass mbinv_rbf_block as
+ * the producer and a mbinv_rbf* as user; x is device memory, n x dim
+ * row-major FP64, and must stay valid while the context is used.  Entries
+ * are computed in FP64 on the GPU (and rounded to dtype). */
+typedef struct {
+    const double *x;
+    int64_t n, dim;
+    double sigma, gamma;
+} mbinv_rbf;
+int mbinv_rbf_block(int64_t r0, int64_t c0, int64_t rows, int64_t cols, void *dst, int64_t ldd, int dtype,
+                    void *stream, void *user);
 
 /* Called after each finished block by mbinv_all_blocks. */
 typedef void (*mbinv_block_done_cb)(int64_t i, int64_t j, void *user);
@@ -160,11 +232,26 @@ void mbinv_default_options(mbinv_options *opt);
 /* Creates a context for an n x n matrix split into k x k blocks
  * (Sec. 2, Eq. blockmatricesnxn).  When k does not divide n the matrix is
  * bordered to order k * ceil(n/k) (Sec. 3, Eq. M_augmented; see mbinv_block
- * for the border used).  M is borrowed: if it is device memory it must stay
- * valid and unchanged until mbinv_destroy; host memory is copied to the
- * device during this call.  dtype is an mbinv_dtype.  opt may be NULL. */
+ * for the border used).  M is borrowed.  Device memory: it must stay valid
+ * and unchanged until mbinv_destroy.  Host memory: it is copied to the device
+ * during this call, unless the bounded schedule keeps it in host memory
+ * (schedule MBINV_SCHEDULE_BOUNDED, or MBINV_SCHEDULE_AUTO with a cap that
+ * the device copy plus 16 b x b value slots would exceed; k must divide n
+ * and k >= 2): then it is read block by block during the calls and must stay
+ * valid and unchanged until mbinv_destroy, pinned host memory being the
+ * fastest.  dtype is an mbinv_dtype.  opt may be NULL. */
 mbinv_status mbinv_create(mbinv_ctx **out, int64_t n, int64_t k, int dtype, const void *M, int64_t ld,
                           const mbinv_options *opt);
+
+/* A context whose M (n x n, type dtype) is produced on demand by fn and
+ * never stored: every block the recursion reads is written by fn into a
+ * device value slot just before its use, under the bounded schedule (depth
+ * first; with a cap, values needed later wait in pinned host memory).  k
+ * must divide n and be at least 2 (else MBINV_ENOTSUP), and MBINV_MIXED_BF16
+ * and refine_steps = 1 are not supported (the refinement residual reads all
+ * of M).  fn and user must stay valid until mbinv_destroy. */
+mbinv_status mbinv_create_from_fn(mbinv_ctx **out, int64_t n, int64_t k, int dtype, mbinv_block_fn fn, void *user,
+                                  const mbinv_options *opt);
 
 /* N_ij, the b x b block (i, j) of M^-1 (Sec. 3.1-3.2, Eq. blockmatrix_NxN;
  * any block through a permutation of block rows and columns, Sec. 3.2 last
@@ -222,8 +309,15 @@ mbinv_status mbinv_block_col(mbinv_ctx *ctx, int64_t j, void *out, int64_t ldo, 
  *   dM += -(X_i)^T G (Y_j)^T,  X_i = block row i, Y_j = block column j of M^-1,
  * both recomputed block by block with the recursion.  G is b_i x b_j
  * (leading dimension ldg), dM is n x n (leading dimension ldd) and is
- * accumulated into, both in M's dtype, host or device.  The paper has no
- * gradient; this is the derivative of its output. */
+ * accumulated into, both in M's dtype, host or device.  On MBINV_FP64 and
+ * MBINV_FP64_TC the rows, columns and products are FP64 (digit products on
+ * the tensor cores on FP64_TC), and with refine_steps = 1 every block of
+ * M^-1 is first computed (runs merged) and X_i, Y_j are each corrected by
+ * one Newton step against that whole approximate inverse N~:
+ * X_i + (E_i^T - X_i M) N~ and Y_j + N~ (E_j - M Y_j), which squares their
+ * error (n^2 doubles of device memory; M on the device, k dividing n, else
+ * MBINV_ENOTSUP).  The paper has no gradient; this is the derivative of its
+ * output. */
 mbinv_status mbinv_backward(mbinv_ctx *ctx, int64_t i, int64_t j, const void *G, int64_t ldg, void *dM, int64_t ldd,
                             mbinv_report *report);
 
@@ -259,9 +353,10 @@ void mbinv_destroy(mbinv_ctx *ctx);
  * library's load until the process exits; no cudaMalloc, cudaFree or other
  * allocating routine is called.  Every call on a device shares that array and
  * overwrites what it uses, so calls whose GPU work overlaps (two threads or
- * two streams) race: serialise them.  The first call on a device looks up the
- * array's device address with that device current; make it before any stream
- * capture. */
+ * two streams) race: serialise them.  Each call waits on the host for its
+ * own result (it reads its status word back before returning).  The first
+ * call on a device also looks up the array's device address with that device
+ * current; that first call should come before any stream capture. */
 mbinv_status mbinv_invert_noalloc(const void *A, int64_t lda, void *X, int64_t ldx, int64_t b, int dtype,
                                   void *stream);
 

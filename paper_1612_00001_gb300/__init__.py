@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmbinv.so")
 
 OK, EINVAL, ENOMEM_CAP, ESINGULAR, ENOTCONV, ETIMEOUT, ECUDA, ENOTSUP = range(8)
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_bf16": 2, "fp64_tc": 3}
+SCHEDULE = {"auto": 0, "levels": 1, "bounded": 2}
 DTYPE_F64, DTYPE_F32 = 0, 1
 
 _lock = threading.Lock()
@@ -39,7 +40,9 @@ class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int),
                 ("device_cap_bytes", ctypes.c_size_t), ("refine_steps", ctypes.c_int),
                 ("bf16_slices", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("pad_seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("pad_seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("out_dtype", ctypes.c_int), ("sing_tol", ctypes.c_double), ("no_graphs", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class Report(ctypes.Structure):
@@ -51,7 +54,10 @@ class Report(ctypes.Structure):
                 ("pack_device_seconds", ctypes.c_double), ("inv_panel_device_seconds", ctypes.c_double),
                 ("inv_panel_flops", ctypes.c_double), ("inv_update_flops", ctypes.c_double),
                 ("inv_panel_launches", ctypes.c_size_t), ("request_frames", ctypes.c_size_t),
-                ("planned_device_bytes", ctypes.c_size_t), ("pack_bytes", ctypes.c_double)]
+                ("planned_device_bytes", ctypes.c_size_t), ("pack_bytes", ctypes.c_double),
+                ("host_in_bytes", ctypes.c_double), ("host_out_bytes", ctypes.c_double),
+                ("host_spill_bytes", ctypes.c_size_t), ("graph_replays", ctypes.c_size_t),
+                ("max_pivot_cond", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -64,6 +70,13 @@ class Problem(ctypes.Structure):
 
 
 DONE_CB = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p)
+BLOCK_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Rbf(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("n", ctypes.c_int64), ("dim", ctypes.c_int64), ("sigma", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
 
 # name -> (restype, argtypes) of every entry point the header declares
 SIGNATURES = {
@@ -86,6 +99,12 @@ SIGNATURES = {
     "mbinv_batched_blocks": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Problem), ctypes.c_int,
                                             ctypes.POINTER(Options), ctypes.POINTER(Report)]),
     "mbinv_destroy": (None, [ctypes.c_void_p]),
+    "mbinv_create_from_fn": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(Options)]),
+    "mbinv_rbf_block": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "mbinv_invert_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
     "mbinv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -145,7 +164,8 @@ def _ptr(t) -> int:
 
 
 def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3, stream=None,
-                 pad_seed: int = 0, profile: bool = False) -> Options:
+                 pad_seed: int = 0, profile: bool = False, schedule="auto", sing_tol: float = 0.0,
+                 out_dtype=None, graphs: bool = True) -> Options:
     o = Options()
     lib().mbinv_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -155,6 +175,10 @@ def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 
     o.cuda_stream = stream
     o.pad_seed = int(pad_seed)
     o.profile = int(bool(profile))
+    o.schedule = SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule)
+    o.sing_tol = float(sing_tol)
+    o.no_graphs = 0 if graphs else 1
+    o.out_dtype = {None: 0, "float64": 1, "float32": 2}[None if out_dtype is None else str(out_dtype).split(".")[-1]]
     return o
 
 
@@ -165,7 +189,8 @@ class Context:
     not change while the context lives."""
 
     def __init__(self, M, k: int, precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3,
-                 pad_seed: int = 0, stream=None, profile: bool = False):
+                 pad_seed: int = 0, stream=None, profile: bool = False, schedule="auto", sing_tol: float = 0.0,
+                 out_dtype=None, graphs: bool = True):
         torch = _torch()
         if M.dim() != 2 or M.shape[0] != M.shape[1]:
             raise ValueError("M must be square")
@@ -175,17 +200,48 @@ class Context:
         self.n = M.shape[0]
         self.k = int(k)
         self.b = -(-self.n // self.k)
-        self.dtype = M.dtype
+        self.mdtype = M.dtype  # type of M, G and dM
+        self.dtype = M.dtype if out_dtype is None else out_dtype  # type of the returned blocks
         self.device = M.device if M.is_cuda else torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream(self.device).cuda_stream
         self.stream = stream
-        self.opts = make_options(precision, cap, refine, slices, stream, pad_seed, profile)
+        self.opts = make_options(precision, cap, refine, slices, stream, pad_seed, profile, schedule, sing_tol,
+                                 out_dtype, graphs)
         h = ctypes.c_void_p()
         _check(lib().mbinv_create(ctypes.byref(h), self.n, self.k, _dtype_code(M), _ptr(M), M.stride(0),
                                   ctypes.byref(self.opts)), "mbinv_create")
         self._h = h
         self.last_report = None
+
+    @classmethod
+    def from_rbf(cls, x, k: int, sigma: float, gamma: float, dtype=None, precision="fp64_tc", cap: int = 0,
+                 stream=None, out_dtype=None):
+        """The LS-SVM matrix A_gamma of the points x (n x dim, float64 on the
+        GPU) - order n + 1 - produced block by block on the GPU by the
+        library's RBF producer and never stored."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        self._keep = x = x.contiguous().to(torch.float64)
+        self.rbf = Rbf(_ptr(x), x.shape[0], x.shape[1], float(sigma), float(gamma))
+        self.n = x.shape[0] + 1
+        self.k = int(k)
+        self.b = -(-self.n // self.k)
+        self.mdtype = dtype or torch.float64
+        self.dtype = self.mdtype if out_dtype is None else out_dtype
+        self.device = x.device
+        self.stream = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        self.opts = make_options(precision, cap, 0, 3, self.stream, out_dtype=out_dtype)
+        L = lib()
+        h = ctypes.c_void_p()
+        fn = ctypes.cast(L.mbinv_rbf_block, ctypes.c_void_p)
+        _check(L.mbinv_create_from_fn(ctypes.byref(h), self.n, self.k,
+                                      DTYPE_F64 if self.mdtype == torch.float64 else DTYPE_F32, fn,
+                                      ctypes.cast(ctypes.pointer(self.rbf), ctypes.c_void_p),
+                                      ctypes.byref(self.opts)), "mbinv_create_from_fn")
+        self._h = h
+        self.last_report = None
+        return self
 
     def extent(self, t: int) -> int:
         return self.n - (self.k - 1) * self.b if t == self.k - 1 else self.b
@@ -268,9 +324,9 @@ class Context:
     def backward(self, i: int, j: int, G, dM=None):
         """dM += -(X_i)^T G (Y_j)^T, the gradient of sum(G * N_ij) w.r.t. M."""
         torch = _torch()
-        G = G.to(dtype=self.dtype).contiguous()
+        G = G.to(dtype=self.mdtype).contiguous()
         if dM is None:
-            dM = torch.zeros((self.n, self.n), dtype=self.dtype, device=G.device)
+            dM = torch.zeros((self.n, self.n), dtype=self.mdtype, device=G.device)
         rep = Report()
         _check(lib().mbinv_backward(self._h, i, j, _ptr(G), G.stride(0), _ptr(dM), dM.stride(0), ctypes.byref(rep)),
                "mbinv_backward")
@@ -316,8 +372,8 @@ class _BlockInverse:
 
             class BlockInverse(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, M, k, i, j, precision, cap):
-                    c = Context(M.detach(), k, precision=precision, cap=cap)
+                def forward(ctx, M, k, i, j, precision, cap, refine):
+                    c = Context(M.detach(), k, precision=precision, cap=cap, refine=refine)
                     out = c.block(i, j)
                     ctx.mb = c
                     ctx.ij = (i, j)
@@ -328,13 +384,15 @@ class _BlockInverse:
                     c = ctx.mb
                     dM = c.backward(ctx.ij[0], ctx.ij[1], G.contiguous())
                     c.close()
-                    return dM, None, None, None, None, None
+                    return dM, None, None, None, None, None, None
 
             cls.fn = BlockInverse
         return cls.fn
 
 
-def block(M, k: int, i: int, j: int, precision="fp64", cap: int = 0):
+def block(M, k: int, i: int, j: int, precision="fp64", cap: int = 0, refine: int = 0):
     """Differentiable N_ij of M^-1: the backward pass is the hand-written
-    adjoint dM = -(X_i)^T G (Y_j)^T, with X_i and Y_j recomputed block by block."""
-    return _BlockInverse.get().apply(M, k, i, j, precision, cap)
+    adjoint dM = -(X_i)^T G (Y_j)^T, with X_i and Y_j recomputed block by block
+    (refine = 1: the forward block refined, and X_i, Y_j corrected by one
+    Newton step against the whole approximate inverse before the adjoint)."""
+    return _BlockInverse.get().apply(M, k, i, j, precision, cap, refine)

@@ -115,12 +115,18 @@ __global__ void sumsq_kernel(const double* R, int64_t ldr, int64_t m, int64_t n,
 
 struct mbinv_ctx {
   int64_t n = 0, k = 0, b = 0, npad = 0, l = 0;
-  int dtype = F64;  // the caller's element type (M, outputs, G, dM)
+  int dtype = F64;  // the caller's element type (M, G, dM)
+  int odt = F64;    // element type of the returned blocks
   int mdt = F64;    // element type of the device matrix the sweep reads
   mbinv_options opt{};
   cudaStream_t stream = nullptr;
   const void* dM = nullptr;  // borrowed caller pointer, or own_M
   int64_t ldm = 0;
+  const void* hM = nullptr;  // host-resident M (bounded schedule): borrowed, caller's dtype
+  int64_t hld = 0;
+  mbinv_block_fn gen = nullptr;  // produced M (bounded schedule): never stored
+  void* gen_user = nullptr;
+  HostBuf spill;             // pinned host slots of the values a bounded run spills
   DevBuf own_M;
   int border_mode = -1;
   DevBuf slots, outtmp, rowbuf, colbuf, resid, gbuf, wbuf, dmbuf, gemmdesc;
@@ -178,15 +184,12 @@ int max_inv_chunk(int b, int prec) {
 // Memory of running one (merged) schedule, beyond M.
 size_t run_bytes(const mbinv_ctx* c, const Schedule& S, int inv_chunk) {
   const int prec = c->opt.precision;
-  size_t bytes = (size_t)S.nslots * slot_bytes_for((int)c->b, prec);
+  size_t bytes = (size_t)S.nslots * slot_bytes_for((int)c->b, prec) + 256;
   bytes += inv_scratch_bytes((int)c->b, prec, inv_chunk);
-  size_t ops = 0;
-  for (const Step& st : S.steps) ops = std::max(ops, st.gemm.size());
-  if (prec == MBINV_MIXED_BF16) bytes += pack_bytes((int)c->b, c->opt.bf16_slices, ops);
-  if (prec == MBINV_FP64_TC) bytes += digit_bytes((int)c->b, ops);
-  size_t all = 0;
-  for (const Step& st : S.steps) all += st.inv.size() + st.gemm.size();
-  bytes += all * 2 * sizeof(GemmDesc) + S.steps.size() * 1024 + (64u << 10);  // descriptors
+  // descriptors, operand slabs, staging: as the executor reckons them, plus
+  // its status words
+  bytes += arena_bytes(S, (int)c->b, prec, c->opt.bf16_slices, inv_chunk, c->dtype, env_slot_type(prec)) +
+           (64u << 10);
   return bytes;
 }
 
@@ -258,7 +261,9 @@ mbinv_status get_plan(mbinv_ctx* c, const std::vector<std::pair<int, int>>& reqs
   Plan P = build_plan((int)c->k, reqs, c->l > 0);
   Schedule best;
   bool ok = false;
+  const bool want_bounded = c->hM || c->gen || c->opt.schedule == MBINV_SCHEDULE_BOUNDED;
   for (int z : {0, 256, 64, 16, 4, 1}) {
+    if (want_bounded) break;
     Schedule T = build_schedule(P, z);
     const int full = std::min(std::max(1, T.max_inv_batch), max_inv_chunk((int)c->b, c->opt.precision));
     for (int ic : {full, 256, 64, 16, 4, 1}) {
@@ -273,7 +278,29 @@ mbinv_status get_plan(mbinv_ctx* c, const std::vector<std::pair<int, int>>& reqs
     }
     if (ok) break;
   }
-  if (!ok) return MBINV_ENOMEM_CAP;
+  if (!ok && c->opt.schedule == MBINV_SCHEDULE_LEVELS) return MBINV_ENOMEM_CAP;
+  if (!ok) {
+    // depth first in the slots the cap leaves, values spilled to the host
+    if (c->opt.precision == MBINV_MIXED_BF16 || c->l > 0) return MBINV_ENOTSUP;
+    const size_t sb = slot_bytes_for((int)c->b, c->opt.precision);
+    Schedule T;
+    const bool host_m = c->hM != nullptr || c->gen != nullptr;
+    if (!build_bounded_schedule(P, (int)std::min<size_t>(1u << 20, 4 * P.f.size() + 64), host_m, &T))
+      return MBINV_ENOTSUP;
+    int slots = T.nslots;  // no spill at all
+    for (int iter = 0; cap && iter < 8; ++iter) {
+      const size_t need = base + run_bytes(c, T, 1);
+      if (need <= cap && T.nslots <= slots) break;
+      const size_t over = need > cap ? (need - cap + sb - 1) / sb + 1 : 0;
+      slots = std::min(slots, T.nslots) - (int)over;
+      if (slots < 6) return MBINV_ENOMEM_CAP;
+      if (!build_bounded_schedule(P, slots, host_m, &T)) return MBINV_ENOMEM_CAP;
+    }
+    if (cap && base + run_bytes(c, T, 1) > cap) return MBINV_ENOMEM_CAP;
+    T.inv_chunk = 1;
+    T.planned = run_bytes(c, T, 1);
+    best = std::move(T);
+  }
   if (c->plans.size() > 256) c->plans.clear();
   it = c->plans.insert_or_assign(reqs, std::make_pair(std::move(P), std::move(best))).first;
   *out = &it->second.second;
@@ -336,8 +363,19 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
   J.slots = (char*)c->slots.p;
   J.slot_bytes = sb;
   J.slot_dt = env_slot_type(prec);
-  J.out_dt = c->dtype;
+  J.out_dt = c->odt;
   J.S = S;
+  if (S->bounded) {
+    J.hM = c->hM;
+    J.hldm = c->hld;
+    J.hmdt = c->dtype;
+    J.gen = c->gen;
+    J.gen_user = c->gen_user;
+    if (S->nspill > 0) {
+      CU(c->spill.ensure((size_t)S->nspill * sb));
+      J.spill = (char*)c->spill.p;
+    }
+  }
   for (const Req& r : reqs) {
     J.outs.push_back(r.dst);
     J.ldos.push_back(r.ldd);
@@ -347,6 +385,9 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
   c->env.slices = c->opt.bf16_slices;
   c->env.profile = c->opt.profile != 0;
   c->env.inv_chunk = std::max(1, S->inv_chunk);
+  c->env.sing_tol = c->opt.sing_tol;
+  c->env.use_graphs = c->opt.no_graphs == 0;
+  const size_t replays0 = c->env.graph_replays;
   s = run_jobs(c->env, {J});
   if (s == MBINV_ECUDA) last_cuda_error() = c->env.last_error;
   if (rep) {
@@ -355,6 +396,11 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
     rep->gemm_launches += (size_t)c->env.gemm_launches;
     add_env_report(rep, c->env);
     rep->planned_device_bytes = std::max(rep->planned_device_bytes, planned);
+    rep->max_pivot_cond = std::max(rep->max_pivot_cond, c->env.max_cond);
+    rep->graph_replays += c->env.graph_replays - replays0;
+    rep->host_in_bytes += c->env.host_in_bytes;
+    rep->host_out_bytes += c->env.host_out_bytes;
+    rep->host_spill_bytes = std::max(rep->host_spill_bytes, (size_t)S->nspill * sb);
     if (s == MBINV_ESINGULAR && rep->failed_pivot < 0) rep->failed_pivot = c->env.failed_inverse;
   }
   return s;
@@ -398,7 +444,7 @@ void start_report(mbinv_report* rep) {
 mbinv_status blocks_to(mbinv_ctx* c, const std::vector<std::pair<int64_t, int64_t>>& ij,
                        const std::vector<void*>& outs, const std::vector<int64_t>& ldos, int width,
                        mbinv_report* rep) {
-  const size_t es = dtype_size(c->dtype);
+  const size_t es = dtype_size(c->odt);
   std::vector<Req> direct;
   std::vector<size_t> staged;
   for (size_t t = 0; t < ij.size(); ++t) {
@@ -470,7 +516,7 @@ mbinv_status row_or_col(mbinv_ctx* c, int64_t t, bool row, void* out, int64_t ld
   std::vector<std::pair<int64_t, int64_t>> ij;
   std::vector<void*> outs;
   std::vector<int64_t> ldos;
-  const size_t es = dtype_size(c->dtype);
+  const size_t es = dtype_size(c->odt);
   for (int64_t q = 0; q < c->k; ++q) {
     ij.emplace_back(row ? t : q, row ? q : t);
     outs.push_back(row ? (char*)out + (size_t)q * c->b * es : (char*)out + (size_t)q * c->b * ldo * es);
@@ -518,6 +564,7 @@ struct OzOp {
   double* C;
   int64_t ldc;
   int m, n;
+  int ta = 0, tb = 0;  // A given as its transpose (k x m), B as its transpose (n x k)
 };
 
 mbinv_status oz_list(mbinv_ctx* c, const std::vector<OzOp>& ops, int k, double alpha, double beta) {
@@ -529,8 +576,13 @@ mbinv_status oz_list(mbinv_ctx* c, const std::vector<OzOp>& ops, int k, double a
   for (const OzOp& o : ops) {
     mmax = std::max(mmax, o.m);
     nmax = std::max(nmax, o.n);
-    if (aslab.emplace(o.A, (int)pa.size()).second) pa.push_back(oz::PackDesc{o.A, o.lda, o.m, k, 0, (int)pa.size()});
-    if (bslab.emplace(o.B, (int)pb.size()).second) pb.push_back(oz::PackDesc{o.B, o.ldb, k, o.n, 1, (int)pb.size()});
+    // slab rows are the rows of A and the columns of B
+    if (aslab.emplace(o.A, (int)pa.size()).second)
+      pa.push_back(o.ta ? oz::PackDesc{o.A, o.lda, k, o.m, 1, (int)pa.size()}
+                        : oz::PackDesc{o.A, o.lda, o.m, k, 0, (int)pa.size()});
+    if (bslab.emplace(o.B, (int)pb.size()).second)
+      pb.push_back(o.tb ? oz::PackDesc{o.B, o.ldb, o.n, k, 0, (int)pb.size()}
+                        : oz::PackDesc{o.B, o.ldb, k, o.n, 1, (int)pb.size()});
   }
   const int rpa = (int)up(mmax, oz::tile_m()), rpb = (int)up(nmax, oz::tile_n()), kpad = (int)up(k, oz::tile_k());
   const int nkb = kpad / oz::tile_k(), nchunk = (nkb + oz::kMaxKBlocks - 1) / oz::kMaxKBlocks;
@@ -621,6 +673,7 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
                             const std::vector<void*>& outs, const std::vector<int64_t>& ldos, int width,
                             mbinv_report* rep) {
   const int64_t n = c->n, b = c->b, k = c->k;
+  if (c->hM || c->gen) return MBINV_ENOTSUP;  // the residual reads all of M on the device
   std::map<int64_t, int> rows, cols;
   for (auto& p : v) {
     rows.emplace(p.first, (int)rows.size());
@@ -653,10 +706,10 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
       dst.push_back(Y + (cc.second * csz + q * b * b) * xs);
       ld.push_back(b);
     }
-  const int saved_dtype = c->dtype;
-  c->dtype = xt;  // the sweeps write blocks in the working type
+  const int saved_dtype = c->odt;
+  c->odt = xt;  // the sweeps write blocks in the working type
   mbinv_status s = blocks_to(c, ij, dst, ld, width, rep);
-  c->dtype = saved_dtype;
+  c->odt = saved_dtype;
   if (s != MBINV_OK) return s;
   for (auto& p : copies) {
     const int64_t bi = block_extent(c, p.first), bj = block_extent(c, p.second);
@@ -719,12 +772,12 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
   }
   s = tcr ? oz_list(c, zs, (int)n, 1.0, 1.0) : gemm_list(c, xt == F64 ? G_F64 : G_F64F32_F64, ds);
   if (s != MBINV_OK) return s;
-  const size_t es = dtype_size(c->dtype);
+  const size_t es = dtype_size(c->odt);
   for (size_t t = 0; t < v.size(); ++t) {
     const int64_t bi = block_extent(c, v[t].first), bj = block_extent(c, v[t].second);
     double* Nt = Nb + t * (size_t)b * b;
     const bool dev = is_device_ptr(outs[t]);
-    if (c->dtype == F64) {
+    if (c->odt == F64) {
       CU(cudaMemcpy2DAsync(outs[t], (size_t)ldos[t] * es, Nt, (size_t)bj * 8, (size_t)bj * 8, (size_t)bi,
                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     } else {
@@ -813,6 +866,7 @@ const char* mbinv_status_string(mbinv_status s) {
     case MBINV_ETIMEOUT: return "a device wait timed out";
     case MBINV_ECUDA: return "CUDA error";
     case MBINV_ENOTSUP: return "unsupported combination";
+    case MBINV_ECALLBACK: return "the matrix producer failed";
   }
   return "unknown status";
 }
@@ -837,6 +891,8 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   if (o.precision < MBINV_FP64 || o.precision > MBINV_FP64_TC) return MBINV_EINVAL;
   if (o.precision == MBINV_MIXED_BF16 && (o.bf16_slices < 1 || o.bf16_slices > 3)) return MBINV_EINVAL;
   if (o.refine_steps < 0 || o.refine_steps > 1) return MBINV_EINVAL;
+  if (o.out_dtype < 0 || o.out_dtype > 2 || o.schedule < 0 || o.schedule > 2 || !(o.sing_tol >= 0.0))
+    return MBINV_EINVAL;
   std::unique_ptr<mbinv_ctx> c(new (std::nothrow) mbinv_ctx);
   if (!c) return MBINV_EINVAL;
   c->n = n;
@@ -845,6 +901,7 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   c->npad = c->b * k;
   c->l = c->npad - n;
   c->dtype = dtype;
+  c->odt = o.out_dtype == 1 ? F64 : (o.out_dtype == 2 ? F32 : dtype);
   c->opt = o;
   c->track.cap = shared ? 0 : o.device_cap_bytes;
   MemTrack* tr = shared ? shared : &c->track;
@@ -856,6 +913,17 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
                                                                           : (o.precision == MBINV_FP32 ? F32 : dtype);
   const size_t es = dtype_size(dtype), mes = dtype_size(c->mdt);
   const bool dev = is_device_ptr(M);
+  const size_t mbytes_dev = (size_t)c->npad * c->npad * mes;
+  const size_t slot16 = 16 * slot_bytes_for((int)c->b, o.precision);
+  if (!dev && !shared && c->l == 0 && k >= 2 && o.precision != MBINV_MIXED_BF16 &&
+      o.schedule != MBINV_SCHEDULE_LEVELS &&
+      (o.schedule == MBINV_SCHEDULE_BOUNDED || (o.device_cap_bytes && mbytes_dev + slot16 > o.device_cap_bytes))) {
+    // M stays in host memory, read block by block by the bounded schedule
+    c->hM = M;
+    c->hld = ld;
+    *out = c.release();
+    return MBINV_OK;
+  }
   if (c->l == 0 && dev && c->mdt == dtype) {
     c->dM = M;
     c->ldm = ld;
@@ -906,6 +974,41 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   return MBINV_OK;
 }
 
+static mbinv_status mbinv_create_from_fn_impl(mbinv_ctx** out, int64_t n, int64_t k, int dtype, mbinv_block_fn fn,
+                                              void* user, const mbinv_options* opt) {
+  if (!out || !fn || n <= 0 || k < 2 || k > 63 || k > n || (dtype != F64 && dtype != F32)) return MBINV_EINVAL;
+  *out = nullptr;
+  mbinv_options o;
+  mbinv_default_options(&o);
+  if (opt) {
+    if (opt->struct_size != sizeof(mbinv_options)) return MBINV_EINVAL;
+    o = *opt;
+  }
+  if (o.precision < MBINV_FP64 || o.precision > MBINV_FP64_TC || o.refine_steps < 0 || o.refine_steps > 1 ||
+      o.out_dtype < 0 || o.out_dtype > 2 || o.schedule < 0 || o.schedule > 2 || !(o.sing_tol >= 0.0))
+    return MBINV_EINVAL;
+  if (n % k || o.precision == MBINV_MIXED_BF16 || o.refine_steps || o.schedule == MBINV_SCHEDULE_LEVELS)
+    return MBINV_ENOTSUP;
+  std::unique_ptr<mbinv_ctx> c(new (std::nothrow) mbinv_ctx);
+  if (!c) return MBINV_EINVAL;
+  c->n = n;
+  c->k = k;
+  c->b = n / k;
+  c->npad = n;
+  c->l = 0;
+  c->dtype = dtype;
+  c->odt = o.out_dtype == 1 ? F64 : (o.out_dtype == 2 ? F32 : dtype);
+  c->opt = o;
+  c->track.cap = o.device_cap_bytes;
+  for (DevBuf* d : c->bufs()) d->track = &c->track;
+  c->stream = (cudaStream_t)o.cuda_stream;
+  c->mdt = (o.precision == MBINV_FP64 || o.precision == MBINV_FP64_TC) ? F64 : F32;
+  c->gen = fn;
+  c->gen_user = user;
+  *out = c.release();
+  return MBINV_OK;
+}
+
 void mbinv_destroy(mbinv_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -914,6 +1017,7 @@ void mbinv_destroy(mbinv_ctx* c) {
                     &c->dmbuf, &c->gemmdesc})
     d->release();
   c->env.release();
+  c->spill.release();
   delete c;
 }
 
@@ -966,7 +1070,7 @@ static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, 
   if (!c || !out || ldo < c->n) return MBINV_EINVAL;
   start_report(rep);
   auto t0 = std::chrono::steady_clock::now();
-  const size_t es = dtype_size(c->dtype);
+  const size_t es = dtype_size(c->odt);
   // the blocks still to do, in row-major order
   std::vector<std::pair<int64_t, int64_t>> todo;
   for (int64_t i = 0; i < c->k; ++i)
@@ -1008,6 +1112,11 @@ static mbinv_status mbinv_all_blocks_impl(mbinv_ctx* c, void* out, int64_t ldo, 
       rep->inv_update_flops += r.inv_update_flops;
       rep->inv_panel_launches += r.inv_panel_launches;
       rep->rel_residual = std::max(rep->rel_residual, r.rel_residual);
+      rep->max_pivot_cond = std::max(rep->max_pivot_cond, r.max_pivot_cond);
+      rep->graph_replays += r.graph_replays;
+      rep->host_in_bytes += r.host_in_bytes;
+      rep->host_out_bytes += r.host_out_bytes;
+      rep->host_spill_bytes = std::max(rep->host_spill_bytes, r.host_spill_bytes);
       rep->peak_device_bytes = std::max(rep->peak_device_bytes, r.peak_device_bytes);
       rep->planned_device_bytes = std::max(rep->planned_device_bytes, r.planned_device_bytes);
       if (s == MBINV_ESINGULAR) rep->failed_pivot = r.failed_pivot;
@@ -1032,20 +1141,173 @@ static mbinv_status mbinv_block_col_impl(mbinv_ctx* c, int64_t j, void* out, int
   return row_or_col(c, j, false, out, ldo, rep);
 }
 
-static mbinv_status mbinv_backward_impl(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM, int64_t ldd,
+// One FP64 product C = beta Cin + alpha op(A) op(B) (op = transpose when ta /
+// tb), as a digit product on the tensor cores on FP64_TC, else on the FP64
+// CUDA-core GEMM.
+mbinv_status prod64(mbinv_ctx* c, const double* A, int64_t lda, int ta, const double* B, int64_t ldb, int tb,
+                    const double* Cin, int64_t ldcin, double* C, int64_t ldc, int m, int n, int k, double alpha,
+                    double beta) {
+  if (c->opt.precision == MBINV_FP64_TC) {
+    OzOp o{A, lda, B, ldb, Cin, ldcin, C, ldc, m, n};
+    o.ta = ta;
+    o.tb = tb;
+    return oz_list(c, {o}, k, alpha, Cin ? beta : 0.0);
+  }
+  return gemm1(c, G_F64, A, lda, ta, B, ldb, tb, Cin, ldcin, C, ldc, m, n, k, alpha, Cin ? beta : 0.0);
+}
+
+// The adjoint of L = sum(G .* N_ij): dM += -(X_i)^T G (Y_j)^T.  On the
+// FP64-valued paths with refine_steps = 1 the block row X_i and column Y_j
+// are first corrected by one Newton step each against the whole approximate
+// inverse N~ (every block by the merged sweep):
+//   X_i <- X_i + (E_i^T - X_i M) N~,   Y_j <- Y_j + N~ (E_j - M Y_j),
+// which squares their error (the correction of X_i leaves -dX M dN~...).
+static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM,
+                                  int64_t ldd, mbinv_report* rep) {
+  const int64_t bi = block_extent(c, i), bj = block_extent(c, j), n = c->n, b = c->b;
+  const bool refine = c->opt.refine_steps > 0;
+  if (refine && (c->hM || c->gen || c->mdt != F64 || c->l > 0)) return MBINV_ENOTSUP;
+  const size_t es = dtype_size(c->dtype);
+  double *X, *Y;
+  int64_t ldx, ldy;
+  const int saved_odt = c->odt;
+  c->odt = F64;  // rows, columns and the whole inverse come out in FP64
+  mbinv_status s = MBINV_OK;
+  if (refine) {
+    // N~: all k^2 blocks, their runs merged (the all-blocks sweep of Sec. 5)
+    CU(c->dmbuf.ensure((size_t)n * n * 8 + 256));
+    std::vector<std::pair<int64_t, int64_t>> ij;
+    std::vector<void*> outs;
+    std::vector<int64_t> lds;
+    for (int64_t r = 0; r < c->k; ++r)
+      for (int64_t q = 0; q < c->k; ++q) {
+        ij.emplace_back(r, q);
+        outs.push_back((double*)c->dmbuf.p + (size_t)r * b * n + (size_t)q * b);
+        lds.push_back(n);
+      }
+    s = blocks_to(c, ij, outs, lds, (int)ij.size(), rep);
+    c->odt = saved_odt;
+    if (s != MBINV_OK) return s;
+    release_sweep(c);
+    const double* Nt = (const double*)c->dmbuf.p;
+    // X_i' = X_i + (E_i^T - X_i M) N~   (rowbuf: R, then X_i')
+    CU(c->resid.ensure(((size_t)bi * n + (size_t)n * bj) * 8 * 2 + 512));
+    double* R = (double*)c->resid.p;
+    double* Xr = R + (size_t)bi * n;
+    double* S = Xr + (size_t)bi * n;
+    double* Yr = S + (size_t)n * bj;
+    const double* Xi = Nt + (size_t)i * b * n;
+    const double* Yj = Nt + (size_t)j * b;
+    s = prod64(c, Xi, n, 0, (const double*)c->dM, c->ldm, 0, nullptr, 0, R, n, (int)bi, (int)n, (int)n, -1.0, 0.0);
+    if (s != MBINV_OK) return s;
+    add_eye_kernel<<<(unsigned)((bi + 255) / 256), 256, 0, c->stream>>>(R, n, i * b, bi);
+    CU(cudaGetLastError());
+    s = prod64(c, R, n, 0, Nt, n, 0, Xi, n, Xr, n, (int)bi, (int)n, (int)n, 1.0, 1.0);
+    if (s != MBINV_OK) return s;
+    // Y_j' = Y_j + N~ (E_j - M Y_j)
+    s = prod64(c, (const double*)c->dM, c->ldm, 0, Yj, n, 0, nullptr, 0, S, bj, (int)n, (int)bj, (int)n, -1.0, 0.0);
+    if (s != MBINV_OK) return s;
+    add_eye_kernel<<<(unsigned)((bj + 255) / 256), 256, 0, c->stream>>>(S + (size_t)j * b * bj, bj, 0, bj);
+    CU(cudaGetLastError());
+    s = prod64(c, Nt, n, 0, S, bj, 0, Yj, n, Yr, bj, (int)n, (int)bj, (int)n, 1.0, 1.0);
+    if (s != MBINV_OK) return s;
+    X = Xr;
+    ldx = n;
+    Y = Yr;
+    ldy = bj;
+    if (rep) rep->gemm_flops += 2.0 * 2.0 * bi * n * n + 2.0 * 2.0 * n * n * bj;
+  } else {
+    CU(c->rowbuf.ensure((size_t)b * n * 8 + 256));
+    CU(c->colbuf.ensure((size_t)n * b * 8 + 256));
+    s = row_or_col(c, i, true, c->rowbuf.p, n, rep);
+    if (s == MBINV_OK) s = row_or_col(c, j, false, c->colbuf.p, bj, rep);
+    c->odt = saved_odt;
+    if (s != MBINV_OK) return s;
+    X = (double*)c->rowbuf.p;
+    ldx = n;
+    Y = (double*)c->colbuf.p;
+    ldy = bj;
+  }
+  // G and dM in FP64 on the device
+  CU(c->gbuf.ensure((size_t)bi * bj * 8 + 256));
+  double* Gd = (double*)c->gbuf.p;
+  const bool gdev = is_device_ptr(G);
+  if (c->dtype == F64) {
+    CU(cudaMemcpy2DAsync(Gd, (size_t)bj * 8, G, (size_t)ldg * 8, (size_t)bj * 8, (size_t)bi,
+                         gdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  } else {
+    CU(c->outtmp.ensure((size_t)bi * bj * 4 + 256));
+    CU(cudaMemcpy2DAsync(c->outtmp.p, (size_t)bj * 4, G, (size_t)ldg * 4, (size_t)bj * 4, (size_t)bi,
+                         gdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    convert_kernel<float, double><<<(unsigned)((bi * bj + 255) / 256), 256, 0, c->stream>>>(
+        (const float*)c->outtmp.p, bj, Gd, bj, bi, bj);
+    CU(cudaGetLastError());
+  }
+  const bool dm_dev = is_device_ptr(dM);
+  double* Dd;
+  int64_t lddd;
+  if (c->dtype == F64 && dm_dev) {
+    Dd = (double*)dM;
+    lddd = ldd;
+  } else {
+    CU(c->wbuf.ensure((size_t)n * n * 8 + (size_t)bi * n * 8 + 256));
+    Dd = (double*)c->wbuf.p + (size_t)bi * n;
+    lddd = n;
+    if (c->dtype == F64) {
+      CU(cudaMemcpy2DAsync(Dd, (size_t)n * 8, dM, (size_t)ldd * 8, (size_t)n * 8, (size_t)n, cudaMemcpyHostToDevice,
+                           c->stream));
+    } else {
+      // FP32 dM: stage it (host or device), widen, accumulate in FP64, narrow back
+      CU(c->outtmp.ensure((size_t)n * n * 4 + 256));
+      CU(cudaMemcpy2DAsync(c->outtmp.p, (size_t)n * 4, dM, (size_t)ldd * 4, (size_t)n * 4, (size_t)n,
+                           dm_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+      convert_kernel<float, double><<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(
+          (const float*)c->outtmp.p, n, Dd, n, n, n);
+      CU(cudaGetLastError());
+    }
+  }
+  CU(c->wbuf.ensure(std::max(c->wbuf.bytes, (size_t)bi * n * 8 + 256)));
+  double* W = (double*)c->wbuf.p;
+  // W = G Y_j^T (bi x n), then dM += -X_i^T W
+  s = prod64(c, Gd, bj, 0, Y, ldy, 1, nullptr, 0, W, n, (int)bi, (int)n, (int)bj, 1.0, 0.0);
+  if (s != MBINV_OK) return s;
+  s = prod64(c, X, ldx, 1, W, n, 0, Dd, lddd, Dd, lddd, (int)n, (int)n, (int)bi, -1.0, 1.0);
+  if (s != MBINV_OK) return s;
+  if (!(c->dtype == F64 && dm_dev)) {
+    if (c->dtype == F64) {
+      CU(cudaMemcpy2DAsync(dM, (size_t)ldd * 8, Dd, (size_t)n * 8, (size_t)n * 8, (size_t)n, cudaMemcpyDeviceToHost,
+                           c->stream));
+    } else {
+      convert_kernel<double, float><<<(unsigned)((n * n + 255) / 256), 256, 0, c->stream>>>(
+          Dd, n, (float*)c->outtmp.p, n, n, n);
+      CU(cudaGetLastError());
+      CU(cudaMemcpy2DAsync(dM, (size_t)ldd * 4, c->outtmp.p, (size_t)n * 4, (size_t)n * 4, (size_t)n,
+                           dm_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  if (rep) {
+    rep->gemm_flops += 2.0 * bi * bj * n + 2.0 * n * n * bi;
+    rep->launches += 2;
+  }
+  (void)es;
+  return MBINV_OK;
+}
+
+static mbinv_status backward_same_type(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM, int64_t ldd,
                             mbinv_report* rep) {
-  if (!c || !G || !dM || i < 0 || j < 0 || i >= c->k || j >= c->k || ldd < c->n) return MBINV_EINVAL;
   const int64_t bi = block_extent(c, i), bj = block_extent(c, j), n = c->n;
-  if (ldg < bj) return MBINV_EINVAL;
-  start_report(rep);
   const size_t es = dtype_size(c->dtype);
   const int combo = c->dtype == F64 ? G_F64 : G_F32;
   // X_i (bi x n) and Y_j (n x bj) of M^-1, their blocks run together
   CU(c->rowbuf.ensure((size_t)c->b * n * es + 256));
   CU(c->colbuf.ensure((size_t)n * c->b * es + 256));
+  // the rows and columns come out in M's type, the type of G and dM
+  const int saved_odt = c->odt;
+  c->odt = c->dtype;
   mbinv_status s = row_or_col(c, i, true, c->rowbuf.p, n, rep);
-  if (s != MBINV_OK) return s;
-  s = row_or_col(c, j, false, c->colbuf.p, bj, rep);
+  if (s == MBINV_OK) s = row_or_col(c, j, false, c->colbuf.p, bj, rep);
+  c->odt = saved_odt;
   if (s != MBINV_OK) return s;
   const void* Gd = G;
   if (!is_device_ptr(G)) {
@@ -1084,6 +1346,18 @@ static mbinv_status mbinv_backward_impl(mbinv_ctx* c, int64_t i, int64_t j, cons
   return MBINV_OK;
 }
 
+static mbinv_status mbinv_backward_impl(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM,
+                                        int64_t ldd, mbinv_report* rep) {
+  if (!c || !G || !dM || i < 0 || j < 0 || i >= c->k || j >= c->k || ldd < c->n) return MBINV_EINVAL;
+  if (ldg < block_extent(c, j)) return MBINV_EINVAL;
+  start_report(rep);
+  // the FP64-valued paths: rows, columns and products in FP64 (digit products
+  // on FP64_TC), optionally refined; the FP32-valued paths in M's type
+  if (c->opt.precision == MBINV_FP64 || c->opt.precision == MBINV_FP64_TC)
+    return backward_fp64(c, i, j, G, ldg, dM, ldd, rep);
+  return backward_same_type(c, i, j, G, ldg, dM, ldd, rep);
+}
+
 static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* probs, int dtype, const mbinv_options* opt,
                                   mbinv_report* rep) {
   if (count < 0 || (count > 0 && !probs)) return MBINV_EINVAL;
@@ -1119,6 +1393,8 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
   env.precision = o.precision;
   env.slices = o.bf16_slices;
   env.profile = o.profile != 0;
+  env.sing_tol = o.sing_tol;
+  env.use_graphs = false;  // every wave is a different launch sequence
   std::vector<int64_t> order;
   for (int64_t t = 0; t < count; ++t)
     if (ctxs[t] && probs[t].status == MBINV_OK) order.push_back(t);
@@ -1200,6 +1476,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     if (rep) {
       rep->launches += env.launches;
       rep->gemm_launches += env.gemm_launches;
+      rep->max_pivot_cond = std::max(rep->max_pivot_cond, env.max_cond);
       add_env_report(rep, env);
     }
     peak = std::max(peak, used);
@@ -1224,6 +1501,10 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
 mbinv_status mbinv_create(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,
                           const mbinv_options* opt) {
   return guarded([&] { return mbinv_create_impl(out, n, k, dtype, M, ld, opt); });
+}
+mbinv_status mbinv_create_from_fn(mbinv_ctx** out, int64_t n, int64_t k, int dtype, mbinv_block_fn fn, void* user,
+                                  const mbinv_options* opt) {
+  return guarded([&] { return mbinv_create_from_fn_impl(out, n, k, dtype, fn, user, opt); });
 }
 mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
   return on_context(c, rep, [&] { return mbinv_block_impl(c, i, j, out, ldo, rep); });

@@ -4,8 +4,10 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <limits>
 #include <vector>
 
+#include "exec.h"
 #include "mbinv_internal.h"
 #include "ozaki.h"
 #include "tc_gemm.h"
@@ -206,3 +208,77 @@ extern "C" int mbinv_debug_plan_group(int k, int count, const int* ij, int pad_l
   }
   return 0;
 }
+
+// Host-only hook (no CUDA call): builds the schedule of the requests ij (count
+// pairs) on a k x k grid and runs it on scalars, b = 1: M is k x k row-major,
+// an inverse is 1/x, a product alpha A B + beta Cin, a copy moves a value.
+// mode 0: level by level; mode 1: bounded, in `slots` slots, M blocks read
+// from "host memory" when host_m.  outs[t] receives request t's result;
+// stats: steps, peak slots, host spill slots, loads, spills, inversions,
+// product units (b^3).  0; -1 for invalid arguments; -2 when the schedule
+// cannot be built in that many slots; -3 when a value is read before it is
+// written.
+extern "C" int mbinv_debug_run_schedule_scalar(int k, int count, const int* ij, int mode, int slots, int host_m,
+                                               const double* M, double* outs, double* stats) {
+  if (k < 2 || count < 1 || !ij || !M || !outs || !stats) return -1;
+  try {
+    std::vector<std::pair<int, int>> reqs;
+    for (int t = 0; t < count; ++t) {
+      if (ij[2 * t] < 0 || ij[2 * t + 1] < 0 || ij[2 * t] >= k || ij[2 * t + 1] >= k) return -1;
+      reqs.emplace_back(ij[2 * t], ij[2 * t + 1]);
+    }
+    const Plan P = build_plan(k, reqs, false);
+    Schedule S;
+    if (mode == 0) S = build_schedule(P, 0);
+    else if (!build_bounded_schedule(P, slots, host_m != 0, &S)) return -2;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    std::vector<double> sl((size_t)std::max(1, S.nslots), nan), sp((size_t)std::max(1, S.nspill), nan);
+    std::vector<char> wsl(sl.size(), 0), wsp(sp.size(), 0);
+    for (int t = 0; t < count; ++t) outs[t] = nan;
+    bool bad = false;
+    auto rd = [&](const Ref& r) -> double {
+      switch (r.kind) {
+        case Ref::MBLK:
+        case Ref::HOSTM: return M[r.r * k + r.c];
+        case Ref::SLOT: if (!wsl.at(r.slot)) bad = true; return sl.at(r.slot);
+        case Ref::SPILL: if (!wsp.at(r.slot)) bad = true; return sp.at(r.slot);
+        default: bad = true; return nan;
+      }
+    };
+    auto wr = [&](const Ref& r, double v) {
+      if (r.kind == Ref::SLOT) { sl.at(r.slot) = v; wsl.at(r.slot) = 1; }
+      else if (r.kind == Ref::SPILL) { sp.at(r.slot) = v; wsp.at(r.slot) = 1; }
+      else if (r.kind == Ref::OUT) outs[r.slot] = v;
+      else bad = true;
+    };
+    for (const Step& st : S.steps) {
+      for (const CopyOp& c : st.copy) wr(c.dst, rd(c.src));
+      for (const InvOp& io : st.inv) wr(io.dst, 1.0 / rd(io.src));
+      for (const GemmOp& g : st.gemm) {
+        const double p = rd(g.A) * rd(g.B);
+        double v = g.alpha < 0 ? -p : p;
+        if (g.Cin.kind != Ref::NONE && g.beta != 0.0) v = g.alpha < 0 ? rd(g.Cin) - p : rd(g.Cin) + p;
+        wr(g.C, v);
+      }
+    }
+    if (bad) return -3;
+    stats[0] = (double)S.steps.size();
+    stats[1] = (double)S.nslots;
+    stats[2] = (double)S.nspill;
+    stats[3] = (double)S.loads;
+    stats[4] = (double)S.spills;
+    stats[5] = (double)S.inversions;
+    stats[6] = S.gemm_flops_units;
+  } catch (...) {
+    return -1;
+  }
+  return 0;
+}
+
+// Test hooks of the failure paths (no fault is made on the GPU):
+// every later digit-product launch first waits `ns` nanoseconds on a barrier
+// nothing arrives at and returns having raised its error word (0 = off); the
+// next `n` device allocations of the library fail as if the GPU were out of
+// memory.
+extern "C" void mbinv_debug_set_stall_ns(unsigned long long ns) { oz::set_debug_stall(ns); }
+extern "C" void mbinv_debug_fail_allocations(int n) { injected_alloc_failures() = n > 0 ? n : 0; }

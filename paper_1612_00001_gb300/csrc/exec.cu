@@ -11,7 +11,10 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <map>
+#include <mutex>
+#include <set>
 #include <tuple>
 
 #include "exec.h"
@@ -20,10 +23,34 @@
 
 namespace mbinv {
 
+cudaError_t once_per_device(const void* key, const std::function<cudaError_t()>& setup) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({key, dev})) return cudaSuccess;
+  e = setup();
+  if (e == cudaSuccess) done.insert({key, dev});
+  return e;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
 void Env::release() {
-  for (DevBuf* d :
-       {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &inv_tc, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr, &oexp})
-    d->release();
+  if (gexec) cudaGraphExecDestroy(gexec);
+  gexec = nullptr;
+  gkey.clear();
+  garena.clear();
+  if (cstream) cudaStreamDestroy(cstream);
+  cstream = nullptr;
+  for (DevBuf* d : bufs()) d->release();
   hdesc.release();
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   events.clear();
@@ -39,6 +66,10 @@ size_t slot_bytes_for(int b, int precision) {
 namespace {
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+// descriptor arrays in the arena: 64-byte aligned (a bounded schedule has
+// one small array per step, tens of thousands of them)
+constexpr size_t kDescAlign = 64;
+size_t al_desc(size_t x) { return (x + kDescAlign - 1) & ~(kDescAlign - 1); }
 size_t up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 struct Strides {
@@ -62,6 +93,14 @@ const void* resolve(const Job& J, const Ref& r, int64_t* ld, int* dt) {
       *ld = J.b;
       *dt = J.slot_dt;
       return J.slots + (size_t)r.slot * J.slot_bytes;
+    case Ref::HOSTM:
+      *ld = J.hldm;
+      *dt = J.hmdt;
+      return (const char*)J.hM + ((size_t)r.r * J.b * J.hldm + (size_t)r.c * J.b) * dtype_size(J.hmdt);
+    case Ref::SPILL:
+      *ld = J.b;
+      *dt = J.slot_dt;
+      return J.spill + (size_t)r.slot * J.slot_bytes;
     case Ref::OUT:
       *dt = J.out_dt;
       if (!J.outs.empty()) {
@@ -98,7 +137,7 @@ cudaError_t ensure_events(Env& E, size_t n) {
 
 // One launch (or launch sequence) of a run, in order.
 struct Launch {
-  enum Kind : int { INV = 0, GEMM = 1, PACK = 2, TC = 3, OZPACK = 4, OZ = 5 } kind;
+  enum Kind : int { INV = 0, GEMM = 1, PACK = 2, TC = 3, OZPACK = 4, OZ = 5, COPY = 6, CONVERT = 7, GEN = 8 } kind;
   size_t off;  // descriptors in the arena
   int count;
   int in_dt = 0, out_dt = 0, bmax = 0;  // INV
@@ -112,7 +151,26 @@ struct Launch {
   int* exps_b = nullptr;                // OZ exponents of B
   int b_rows_pad = 0, kb0 = 0, nkb = 0; // OZ
   double alpha = 1, beta = 0;           // OZ
+  // COPY: a b x b block between host and device (pitches in bytes);
+  // CONVERT: cdst (b x b, type out_dt, ld cld) from the staging block (in_dt)
+  const void* csrc = nullptr;
+  void* cdst = nullptr;
+  size_t spitch = 0, dpitch = 0, width = 0, height = 0;
+  cudaMemcpyKind ckind = cudaMemcpyHostToDevice;
+  int64_t cld = 0;
+  // GEN: gen writes block (r0, c0) of the produced matrix into cdst
+  mbinv_block_fn gen = nullptr;
+  void* gen_user = nullptr;
+  int64_t r0 = 0, c0 = 0;
 };
+
+// dst[r][c] = (TD) src[r][c] for an n x n block, src contiguous
+template <typename TS, typename TD>
+__global__ void convert_block_kernel(const TS* __restrict__ src, TD* __restrict__ dst, int64_t ldd, int n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  dst[(e / n) * ldd + e % n] = (TD)src[e];
+}
 
 #define CUE(x)                                       \
   do {                                               \
@@ -127,6 +185,84 @@ struct Launch {
     }                                                \
   } while (0)
 
+// Pass 1 of run_jobs: bytes of the descriptor arena and of the packed slabs
+// and staging the jobs' schedules need (single source for run_jobs and for
+// the planner's reckoning).
+struct ArenaSizes {
+  size_t need, maxA, maxB, maxZ, maxE, stage_bytes;
+};
+ArenaSizes arena_sizes(const std::vector<Job>& jobs, int precision, int slices, int inv_chunk) {
+  const bool mixed = precision == MBINV_MIXED_BF16;
+  const bool ozk = precision == MBINV_FP64_TC;
+  const int T = tc::tile_rows(), KT = tc::tile_k();
+  const int NS = slices;
+  size_t nsteps = 0;
+  for (const Job& J : jobs) nsteps = std::max(nsteps, J.S->steps.size());
+  struct {
+    int inv_chunk;
+  } E{inv_chunk};
+  size_t need = 512, maxA = 1, maxB = 1, maxZ = 1, maxE = 1;  // maxA/B/Z/E in bytes
+  size_t stage_bytes = 0;
+  for (size_t t = 0; t < nsteps; ++t) {
+    size_t ninv = 0, ngemm = 0;
+    std::map<int, std::pair<size_t, size_t>> per_b;  // b -> (distinct A, products)
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      const Schedule& S = *jobs[q].S;
+      if (t >= S.steps.size()) continue;
+      const Step& s = S.steps[t];
+      if (s.kind == Step::COPY) {
+        for (const CopyOp& cp : s.copy)
+          if (cp.src.kind == Ref::HOSTM && jobs[q].hmdt != jobs[q].slot_dt)
+            stage_bytes = std::max(stage_bytes, (size_t)jobs[q].b * jobs[q].b * dtype_size(jobs[q].hmdt));
+      } else if (s.kind == Step::INV) {
+        ninv += s.inv.size();
+      } else {
+        ngemm += s.gemm.size();
+        per_b[jobs[q].b].second += s.gemm.size();
+        per_b[jobs[q].b].first += s.gemm.size();
+      }
+    }
+    need += ninv * sizeof(InvDesc) + kDescAlign * ((ninv + E.inv_chunk - 1) / E.inv_chunk + 1);
+    need += ngemm * sizeof(GemmDesc) + kDescAlign;
+    if (mixed) {
+      size_t zsum = 0;
+      for (auto& kv : per_b) {
+        need += kv.second.first * sizeof(tc::PackDesc) * 2 + kv.second.second * sizeof(tc::TcProblem) + 1024;
+        const size_t slab = (size_t)NS * ((kv.first + T - 1) / T * T) * ((kv.first + KT - 1) / KT * KT) * 2;
+        maxA = std::max(maxA, kv.second.first * slab);
+        maxB = std::max(maxB, kv.second.second * slab);
+        zsum += al(kv.second.second * slab);
+      }
+      maxZ = std::max(maxZ, zsum);
+    }
+    if (ozk) {
+      for (auto& kv : per_b) {
+        const size_t b = kv.first, nops = kv.second.second;
+        const size_t rpa = up(b, oz::tile_m()), rpb = up(b, oz::tile_n()), kpad = up(b, oz::tile_k());
+        const size_t chunks = up(kpad / oz::tile_k(), oz::kMaxKBlocks) / oz::kMaxKBlocks;
+        need += nops * (2 * sizeof(oz::PackDesc) + chunks * sizeof(oz::Problem)) + kDescAlign * (3 + chunks);
+        maxA = std::max(maxA, nops * oz::kDigits * rpa * kpad * 2);
+        maxB = std::max(maxB, nops * oz::kDigits * rpb * kpad * 2);
+        maxE = std::max(maxE, nops * (rpa + rpb) * 4);
+      }
+    }
+  }
+  return ArenaSizes{need, maxA, maxB, maxZ, maxE, stage_bytes};
+}
+
+}  // namespace
+
+size_t arena_bytes(const Schedule& S, int b, int precision, int slices, int inv_chunk, int host_dt, int slot_dt) {
+  Job J;
+  J.b = b;
+  J.S = &S;
+  J.hmdt = host_dt;
+  J.slot_dt = slot_dt;
+  const ArenaSizes a = arena_sizes({J}, precision, slices, inv_chunk);
+  return a.need + a.maxA + a.maxB + a.maxZ + a.maxE + a.stage_bytes;
+}
+
+namespace {
 }  // namespace
 
 size_t inv_scratch_bytes(int bmax, int precision, int count) {
@@ -149,6 +285,7 @@ size_t digit_bytes(int bmax, size_t ops) {
 
 mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   E.launches = E.gemm_launches = 0;
+  E.host_in_bytes = E.host_out_bytes = 0;
   E.gemm_dev_s = E.inv_dev_s = E.pack_dev_s = 0;
   E.pack_bytes = 0;
   E.inv_panel_dev_s = E.inv_panel_flops = E.inv_update_flops = 0;
@@ -170,55 +307,19 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   const int NS = E.slices;
 
   // ---- pass 1: sizes of the descriptor arena and of the packed slabs
-  size_t need = 512, maxA = 1, maxB = 1, maxZ = 1, maxE = 1;  // maxA/B/Z/E in bytes
-  for (size_t t = 0; t < nsteps; ++t) {
-    size_t ninv = 0, ngemm = 0;
-    std::map<int, std::pair<size_t, size_t>> per_b;  // b -> (distinct A, products)
-    for (size_t q = 0; q < jobs.size(); ++q) {
-      const Schedule& S = *jobs[q].S;
-      if (t >= S.steps.size()) continue;
-      const Step& s = S.steps[t];
-      if (s.kind == Step::INV) {
-        ninv += s.inv.size();
-      } else {
-        ngemm += s.gemm.size();
-        per_b[jobs[q].b].second += s.gemm.size();
-        per_b[jobs[q].b].first += s.gemm.size();
-      }
-    }
-    need += ninv * sizeof(InvDesc) + 256 * ((ninv + E.inv_chunk - 1) / E.inv_chunk + 1);
-    need += ngemm * sizeof(GemmDesc) + 256;
-    if (mixed) {
-      size_t zsum = 0;
-      for (auto& kv : per_b) {
-        need += kv.second.first * sizeof(tc::PackDesc) * 2 + kv.second.second * sizeof(tc::TcProblem) + 1024;
-        const size_t slab = (size_t)NS * ((kv.first + T - 1) / T * T) * ((kv.first + KT - 1) / KT * KT) * 2;
-        maxA = std::max(maxA, kv.second.first * slab);
-        maxB = std::max(maxB, kv.second.second * slab);
-        zsum += al(kv.second.second * slab);
-      }
-      maxZ = std::max(maxZ, zsum);
-    }
-    if (ozk) {
-      for (auto& kv : per_b) {
-        const size_t b = kv.first, nops = kv.second.second;
-        const size_t rpa = up(b, oz::tile_m()), rpb = up(b, oz::tile_n()), kpad = up(b, oz::tile_k());
-        const size_t chunks = up(kpad / oz::tile_k(), oz::kMaxKBlocks) / oz::kMaxKBlocks;
-        need += nops * (2 * sizeof(oz::PackDesc) + chunks * sizeof(oz::Problem)) + 256 * (3 + chunks);
-        maxA = std::max(maxA, nops * oz::kDigits * rpa * kpad * 2);
-        maxB = std::max(maxB, nops * oz::kDigits * rpb * kpad * 2);
-        maxE = std::max(maxE, nops * (rpa + rpb) * 4);
-      }
-    }
-  }
+  const ArenaSizes az = arena_sizes(jobs, E.precision, E.slices, E.inv_chunk);
+  const size_t need = az.need, maxA = az.maxA, maxB = az.maxB, maxZ = az.maxZ, maxE = az.maxE,
+               stage_bytes = az.stage_bytes;
   CUE(E.desc.ensure(need));
   CUE(E.hdesc.ensure(need));
   CUE(E.status.ensure(256));
+  CUE(E.condw.ensure(256));
   CUE(E.flags.ensure(al(jobs.size() * sizeof(int))));
   CUE(E.inv_work.ensure((size_t)E.inv_chunk * st.work));
   CUE(E.inv_wrow.ensure((size_t)E.inv_chunk * st.wrow));
   CUE(E.inv_perm.ensure((size_t)E.inv_chunk * st.perm));
   CUE(E.inv_amax.ensure((size_t)E.inv_chunk * 256));
+  if (stage_bytes) CUE(E.stage.ensure(stage_bytes));
   if (ozk) CUE(E.inv_tc.ensure(inv_tc_bytes(bmax, E.inv_chunk)));
   if (mixed) {
     CUE(E.apk.ensure(maxA));
@@ -237,7 +338,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
-    off += al(bytes);
+    off += al_desc(bytes);
     return o;
   };
   std::vector<Launch> L;
@@ -256,6 +357,78 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
         if (kind >= 0 && k2 != kind) return MBINV_ENOTSUP;  // schedules must align
         kind = k2;
       }
+    if (kind == Step::COPY) {
+      // host <-> device copies of b x b values, in order
+      for (size_t q = 0; q < jobs.size(); ++q) {
+        if (t >= jobs[q].S->steps.size()) continue;
+        const Job& J = jobs[q];
+        for (const CopyOp& cp : J.S->steps[t].copy) {
+          int64_t lds, ldd;
+          int sdt, ddt;
+          if (cp.src.kind == Ref::HOSTM && J.gen) {
+            // a block of a produced matrix: written by the producer, in the
+            // producer's type, then converted to the slot's type if needed
+            void* dst = (void*)resolve(J, cp.dst, &ldd, &ddt);
+            if (!dst || cp.dst.kind != Ref::SLOT) return MBINV_ENOTSUP;
+            Launch g{Launch::GEN, 0, 1};
+            g.gen = J.gen;
+            g.gen_user = J.gen_user;
+            g.r0 = (int64_t)cp.src.r * J.b;
+            g.c0 = (int64_t)cp.src.c * J.b;
+            g.b = J.b;
+            g.in_dt = J.hmdt;
+            if (J.hmdt == ddt) {
+              g.cdst = dst;
+              g.cld = ldd;
+              L.push_back(g);
+            } else {
+              g.cdst = E.stage.p;
+              g.cld = J.b;
+              L.push_back(g);
+              Launch cv{Launch::CONVERT, 0, 1};
+              cv.cdst = dst;
+              cv.cld = ldd;
+              cv.in_dt = J.hmdt;
+              cv.out_dt = ddt;
+              cv.b = J.b;
+              L.push_back(cv);
+            }
+            continue;
+          }
+          const void* src = resolve(J, cp.src, &lds, &sdt);
+          void* dst = (void*)resolve(J, cp.dst, &ldd, &ddt);
+          if (!src || !dst) return MBINV_ENOTSUP;
+          const bool h2d = cp.src.kind == Ref::HOSTM || cp.src.kind == Ref::SPILL;
+          Launch l{Launch::COPY, 0, 1};
+          l.csrc = src;
+          l.ckind = h2d ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+          l.height = (size_t)J.b;
+          l.spitch = (size_t)lds * dtype_size(sdt);
+          l.dpitch = (size_t)ldd * dtype_size(ddt);
+          l.width = (size_t)J.b * dtype_size(sdt);
+          if (sdt == ddt) {
+            l.cdst = dst;
+            L.push_back(l);
+          } else {
+            // a block of the host matrix in another type: staged, then converted
+            if (cp.src.kind != Ref::HOSTM || cp.dst.kind != Ref::SLOT) return MBINV_ENOTSUP;
+            l.cdst = E.stage.p;
+            l.dpitch = l.width;
+            L.push_back(l);
+            Launch cv{Launch::CONVERT, 0, 1};
+            cv.cdst = dst;
+            cv.cld = ldd;
+            cv.in_dt = sdt;
+            cv.out_dt = ddt;
+            cv.b = J.b;
+            L.push_back(cv);
+          }
+          if (h2d) E.host_in_bytes += (double)J.b * J.b * dtype_size(sdt);
+          else E.host_out_bytes += (double)J.b * J.b * dtype_size(sdt);
+        }
+      }
+      continue;
+    }
     if (kind == Step::INV) {
       std::vector<std::pair<int, const InvOp*>> ops;
       for (size_t q = 0; q < jobs.size(); ++q)
@@ -284,6 +457,8 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           d.amax = (unsigned long long*)((char*)E.inv_amax.p + (u - c0) * 256);
           d.b = J.b;
           d.tag = ninv_seen++;
+          d.tol_rel = E.sing_tol;
+          d.cond = (unsigned long long*)E.condw.p;
           d.flag = dflags + ops[u].first;
           bm = std::max(bm, J.b);
           double pf, uf;
@@ -544,95 +719,184 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   }
   if (off + 64 > need) return MBINV_ENOTSUP;
 
-  // ---- launches
-  CUE(cudaMemcpyAsync(dbase, hbase, off, cudaMemcpyHostToDevice, E.stream));
+  // ---- launches.  The whole sequence is issued by `issue` onto E.stream.
+  // A call whose launch sequence equals the previous call's - the same
+  // schedule, buffers and descriptors, no profiling, no host copies - is
+  // captured into a CUDA graph the second time and replayed from then on.
   DevStatus* hst = (DevStatus*)(hbase + need - 64);
   hst[0] = DevStatus{0, INT_MAX};
-  CUE(cudaMemcpyAsync(E.status.p, &hst[0], sizeof(DevStatus), cudaMemcpyHostToDevice, E.stream));
-  CUE(cudaMemsetAsync(E.flags.p, 0, jobs.size() * sizeof(int), E.stream));
-  if (mixed || ozk) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
-  if (E.profile) CUE(ensure_events(E, 2 * L.size()));
   size_t pused = 0;  // panel timing events taken
-  const InvTc itc{E.inv_tc.p, (int*)E.tcerr.p};
-  tc::TcParams P{};
-  if (mixed) {
-    P.S = NS;
-    tc::pair_table(NS, &P.npairs, P.pa, P.pb);
-    P.err = (int*)E.tcerr.p;
-  }
-  for (size_t q = 0; q < L.size(); ++q) {
-    const Launch& l = L[q];
-    if (E.profile) CUE(cudaEventRecord(E.events[2 * q], E.stream));
-    switch (l.kind) {
-      case Launch::INV:
-      {
-        InvTiming tm{nullptr, 0, 0};
-        if (E.profile) {
-          const size_t need = pused + 2 * ((size_t)l.bmax / 32 + 2);
-          while (E.pevents.size() < need) {
-            cudaEvent_t ev;
-            CUE(cudaEventCreate(&ev));
-            E.pevents.push_back(ev);
-          }
-          tm = InvTiming{E.pevents.data() + pused, (int)(need - pused), 0};
-        }
-        CUE(run_inverse_batch(l.in_dt, l.out_dt, wt, (const InvDesc*)(dbase + l.off), l.count, l.bmax,
-                              (DevStatus*)E.status.p, E.stream, &E.launches, ozk ? &itc : nullptr,
-                              E.profile ? &tm : nullptr));
-        pused += tm.n;
-      }
-        break;
-      case Launch::GEMM:
-        CUE(launch_gemm_grouped(l.combo, (const GemmDesc*)(dbase + l.off), l.count, l.tiles, E.stream));
-        ++E.launches;
-        ++E.gemm_launches;
-        break;
-      case Launch::PACK:
-        CUE(tc::launch_pack((const tc::PackDesc*)(dbase + l.off), l.count, NS, l.rows_pad, l.kpad, l.dst, E.stream));
-        ++E.launches;
-        break;
-      case Launch::TC:
-        P.m = P.n = l.b;
-        P.kpad = l.kpad;
-        P.tiles_m = P.tiles_n = l.rows_pad / T;
-        P.orows = l.rows_pad;
-        P.okpad = l.kpad;
-        P.mode = l.mode;
-        P.alpha = l.mode == 0 ? -1.f : 1.f;
-        P.beta = 1.f;
-        P.opk = l.zout;
-        CUE(tc::launch_gemm(l.dst, l.nA, l.rows_pad, l.bsrc, l.nB, l.rows_pad, P,
-                            (const tc::TcProblem*)(dbase + l.off), l.count, E.stream));
-        ++E.launches;
-        ++E.gemm_launches;
-        break;
-      case Launch::OZPACK:
-        CUE(oz::launch_pack((const oz::PackDesc*)(dbase + l.off), l.count, l.rows_pad, l.kpad, l.dst, l.exps,
-                            E.stream));
-        ++E.launches;
-        break;
-      case Launch::OZ: {
-        oz::Params Q{};
-        Q.kpad = l.kpad;
-        Q.kb0 = l.kb0;
-        Q.nkb = l.nkb;
-        Q.tiles_m = l.rows_pad / oz::tile_m();
-        Q.tiles_n = l.b_rows_pad / oz::tile_n();
-        Q.alpha = l.alpha;
-        Q.beta = l.beta;
-        Q.ea = l.exps;
-        Q.eb = l.exps_b;
-        Q.ea_rows = l.rows_pad;
-        Q.eb_rows = l.b_rows_pad;
-        Q.err = (int*)E.tcerr.p;
-        CUE(oz::launch_gemm(l.dst, l.nA, l.rows_pad, l.bsrc, l.nB, l.b_rows_pad, Q,
-                            (const oz::Problem*)(dbase + l.off), l.count, E.stream));
-        ++E.launches;
-        ++E.gemm_launches;
-        break;
-      }
+  if (E.profile) CUE(ensure_events(E, 2 * L.size()));
+  auto issue = [&]() -> mbinv_status {
+    CUE(cudaMemcpyAsync(dbase, hbase, off, cudaMemcpyHostToDevice, E.stream));
+    CUE(cudaMemcpyAsync(E.status.p, &hst[0], sizeof(DevStatus), cudaMemcpyHostToDevice, E.stream));
+    CUE(cudaMemsetAsync(E.flags.p, 0, jobs.size() * sizeof(int), E.stream));
+    CUE(cudaMemsetAsync(E.condw.p, 0, sizeof(unsigned long long), E.stream));
+    if (mixed || ozk) CUE(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), E.stream));
+    const InvTc itc{E.inv_tc.p, (int*)E.tcerr.p};
+    tc::TcParams P{};
+    if (mixed) {
+      P.S = NS;
+      tc::pair_table(NS, &P.npairs, P.pa, P.pb);
+      P.err = (int*)E.tcerr.p;
     }
-    if (E.profile) CUE(cudaEventRecord(E.events[2 * q + 1], E.stream));
+    for (size_t q = 0; q < L.size(); ++q) {
+      const Launch& l = L[q];
+      if (E.profile) CUE(cudaEventRecord(E.events[2 * q], E.stream));
+      switch (l.kind) {
+        case Launch::COPY:
+          CUE(cudaMemcpy2DAsync(l.cdst, l.dpitch, l.csrc, l.spitch, l.width, l.height, l.ckind, E.stream));
+          break;
+        case Launch::GEN:
+          if (l.gen(l.r0, l.c0, l.b, l.b, l.cdst, l.cld, l.in_dt, (void*)E.stream, l.gen_user) != 0)
+            return MBINV_ECALLBACK;
+          CUE(cudaGetLastError());
+          break;
+        case Launch::CONVERT: {
+          const int64_t nel = (int64_t)l.b * l.b;
+          const unsigned blocks = (unsigned)((nel + 255) / 256);
+          if (l.in_dt == F32 && l.out_dt == F64)
+            convert_block_kernel<float, double><<<blocks, 256, 0, E.stream>>>((const float*)E.stage.p, (double*)l.cdst,
+                                                                              l.cld, l.b);
+          else if (l.in_dt == F64 && l.out_dt == F32)
+            convert_block_kernel<double, float><<<blocks, 256, 0, E.stream>>>((const double*)E.stage.p, (float*)l.cdst,
+                                                                              l.cld, l.b);
+          else
+            return MBINV_ENOTSUP;
+          CUE(cudaGetLastError());
+          ++E.launches;
+          break;
+        }
+        case Launch::INV:
+        {
+          InvTiming tm{nullptr, 0, 0};
+          if (E.profile) {
+            const size_t need = pused + 2 * ((size_t)l.bmax / 32 + 2);
+            while (E.pevents.size() < need) {
+              cudaEvent_t ev;
+              CUE(cudaEventCreate(&ev));
+              E.pevents.push_back(ev);
+            }
+            tm = InvTiming{E.pevents.data() + pused, (int)(need - pused), 0};
+          }
+          CUE(run_inverse_batch(l.in_dt, l.out_dt, wt, (const InvDesc*)(dbase + l.off), l.count, l.bmax,
+                                (DevStatus*)E.status.p, E.stream, &E.launches, ozk ? &itc : nullptr,
+                                E.profile ? &tm : nullptr));
+          CUE(launch_cond1((const InvDesc*)(dbase + l.off), l.count, l.in_dt, l.out_dt, E.stream));
+          ++E.launches;
+          pused += tm.n;
+        }
+          break;
+        case Launch::GEMM:
+          CUE(launch_gemm_grouped(l.combo, (const GemmDesc*)(dbase + l.off), l.count, l.tiles, E.stream));
+          ++E.launches;
+          ++E.gemm_launches;
+          break;
+        case Launch::PACK:
+          CUE(tc::launch_pack((const tc::PackDesc*)(dbase + l.off), l.count, NS, l.rows_pad, l.kpad, l.dst, E.stream));
+          ++E.launches;
+          break;
+        case Launch::TC:
+          P.m = P.n = l.b;
+          P.kpad = l.kpad;
+          P.tiles_m = P.tiles_n = l.rows_pad / T;
+          P.orows = l.rows_pad;
+          P.okpad = l.kpad;
+          P.mode = l.mode;
+          P.alpha = l.mode == 0 ? -1.f : 1.f;
+          P.beta = 1.f;
+          P.opk = l.zout;
+          CUE(tc::launch_gemm(l.dst, l.nA, l.rows_pad, l.bsrc, l.nB, l.rows_pad, P,
+                              (const tc::TcProblem*)(dbase + l.off), l.count, E.stream));
+          ++E.launches;
+          ++E.gemm_launches;
+          break;
+        case Launch::OZPACK:
+          CUE(oz::launch_pack((const oz::PackDesc*)(dbase + l.off), l.count, l.rows_pad, l.kpad, l.dst, l.exps,
+                              E.stream));
+          ++E.launches;
+          break;
+        case Launch::OZ: {
+          oz::Params Q{};
+          Q.kpad = l.kpad;
+          Q.kb0 = l.kb0;
+          Q.nkb = l.nkb;
+          Q.tiles_m = l.rows_pad / oz::tile_m();
+          Q.tiles_n = l.b_rows_pad / oz::tile_n();
+          Q.alpha = l.alpha;
+          Q.beta = l.beta;
+          Q.ea = l.exps;
+          Q.eb = l.exps_b;
+          Q.ea_rows = l.rows_pad;
+          Q.eb_rows = l.b_rows_pad;
+          Q.err = (int*)E.tcerr.p;
+          CUE(oz::launch_gemm(l.dst, l.nA, l.rows_pad, l.bsrc, l.nB, l.b_rows_pad, Q,
+                              (const oz::Problem*)(dbase + l.off), l.count, E.stream));
+          ++E.launches;
+          ++E.gemm_launches;
+          break;
+        }
+      }
+      if (E.profile) CUE(cudaEventRecord(E.events[2 * q + 1], E.stream));
+    }
+    return MBINV_OK;
+  };
+  bool graphable = E.use_graphs;
+  for (const Launch& l : L)
+    if (l.kind == Launch::COPY || l.kind == Launch::GEN || l.kind == Launch::CONVERT) graphable = false;
+  std::vector<uintptr_t> key;
+  if (graphable) {
+    key = {(uintptr_t)E.precision, (uintptr_t)E.slices, (uintptr_t)E.inv_chunk, off, L.size(), (uintptr_t)E.profile,
+           (uintptr_t)E.events.data(), E.events.size(), (uintptr_t)E.pevents.data(), E.pevents.size()};
+    for (DevBuf* d : E.bufs()) key.push_back((uintptr_t)d->p);
+    for (const Job& J : jobs) {
+      key.push_back((uintptr_t)J.S);
+      key.push_back((uintptr_t)J.slots);
+      key.push_back((uintptr_t)J.dM);
+    }
+  }
+  const bool same = graphable && key == E.gkey && E.garena.size() == off &&
+                    std::memcmp(E.garena.data(), hbase, off) == 0;
+  if (same && E.gexec) {
+    CUE(cudaGraphLaunch(E.gexec, E.stream));
+    E.launches = E.glaunches;
+    E.gemm_launches = E.ggemm_launches;
+    pused = E.gpused;
+    ++E.graph_replays;
+  } else if (same) {
+    // second identical call: capture on the library's own stream, replay on E.stream
+    if (!E.cstream) CUE(cudaStreamCreateWithFlags(&E.cstream, cudaStreamNonBlocking));
+    cudaStream_t user = E.stream;
+    E.stream = E.cstream;
+    cudaError_t ce = cudaStreamBeginCapture(E.cstream, cudaStreamCaptureModeThreadLocal);
+    mbinv_status st = ce == cudaSuccess ? issue() : MBINV_ECUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(E.cstream, &g) : ce;
+    E.stream = user;
+    if (st != MBINV_OK || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      E.last_error = ee != cudaSuccess ? ee : E.last_error;
+      return st != MBINV_OK ? st : MBINV_ECUDA;
+    }
+    if (E.gexec) cudaGraphExecDestroy(E.gexec);
+    E.gexec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&E.gexec, g, 0);
+    cudaGraphDestroy(g);
+    CUE(ie);
+    CUE(cudaGraphLaunch(E.gexec, E.stream));
+    E.glaunches = E.launches;
+    E.ggemm_launches = E.gemm_launches;
+    E.gpused = pused;
+  } else {
+    const mbinv_status st = issue();
+    if (st != MBINV_OK) return st;
+    if (graphable) {
+      E.gkey = key;
+      E.garena.assign(hbase, hbase + off);
+      if (E.gexec) cudaGraphExecDestroy(E.gexec);
+      E.gexec = nullptr;
+    }
   }
   CUE(cudaMemcpyAsync(&hst[1], E.status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, E.stream));
   int herr = 0;
@@ -642,10 +906,19 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
   if (mixed || ozk) CUE(cudaMemcpy(&herr, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
   for (size_t q = 0; q < jobs.size(); ++q) E.job_singular[q] = fl[q];
   if (hst[1].singular) E.failed_inverse = hst[1].tag;
+  {
+    unsigned long long cb = 0;
+    CUE(cudaMemcpy(&cb, E.condw.p, sizeof cb, cudaMemcpyDeviceToHost));
+    double cv;
+    std::memcpy(&cv, &cb, sizeof cv);
+    E.max_cond = cv;
+  }
   if (E.profile) {
     for (size_t q = 0; q < L.size(); ++q) {
       float ms = 0;
       CUE(cudaEventElapsedTime(&ms, E.events[2 * q], E.events[2 * q + 1]));
+      if (L[q].kind == Launch::COPY || L[q].kind == Launch::CONVERT || L[q].kind == Launch::GEN)
+        continue;  // host traffic and the producer, not the sweep's kernels
       if (L[q].kind == Launch::INV) E.inv_dev_s += ms * 1e-3;
       else if (L[q].kind == Launch::PACK || L[q].kind == Launch::OZPACK) E.pack_dev_s += ms * 1e-3;
       else E.gemm_dev_s += ms * 1e-3;

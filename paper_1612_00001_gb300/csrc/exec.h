@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/mbinv.h"
@@ -24,6 +25,13 @@ inline bool& cap_refused() {
   return f;
 }
 
+// Test hook: the next n device allocations of the library fail as if the
+// device were out of memory (cudaErrorMemoryAllocation), before cudaMalloc.
+inline std::atomic<int>& injected_alloc_failures() {
+  static std::atomic<int> n{0};
+  return n;
+}
+
 // A device buffer that grows on demand.  With a tracker attached, every byte
 // it holds is counted there, and growth that would take the tracker past its
 // cap is refused before cudaMalloc is called.
@@ -38,6 +46,8 @@ struct DevBuf {
       cap_refused() = true;
       return cudaErrorMemoryAllocation;
     }
+    if (injected_alloc_failures().load() > 0 && injected_alloc_failures().fetch_sub(1) > 0)
+      return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&p, need);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -93,6 +103,15 @@ struct Job {
   int64_t ldo = 0;
   std::vector<void*> outs;   // several requests: destination of request r
   std::vector<int64_t> ldos;
+  // bounded schedules: the matrix in host memory (HOSTM copies) and the host
+  // spill area (SPILL slots, slot_bytes apart)
+  const void* hM = nullptr;
+  int64_t hldm = 0;
+  int hmdt = F64;
+  char* spill = nullptr;
+  // a produced matrix: HOSTM blocks are written by gen instead of copied
+  mbinv_block_fn gen = nullptr;
+  void* gen_user = nullptr;
   int out_dt = F64;
   const Schedule* S = nullptr;
 };
@@ -105,10 +124,24 @@ struct Env {
   bool profile = false;
   int inv_chunk = 1;  // matrices per inverse launch
   DevBuf inv_work, inv_wrow, inv_perm, inv_amax, inv_tc, desc, status, flags, apk, bpk, b2pk, tcerr, oexp;
+  DevBuf stage;        // a block of a host matrix on its way to a slot of another type
+  DevBuf condw;        // largest condition estimate of the run's inverses (bits of a double)
+  double sing_tol = 0; // relative singularity threshold of the pivots (0 = b eps)
+  // CUDA graph of the last repeated launch sequence (see run_jobs)
+  bool use_graphs = true;
+  cudaStream_t cstream = nullptr;  // capture stream
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uintptr_t> gkey;
+  std::vector<char> garena;
+  int glaunches = 0, ggemm_launches = 0;
+  size_t gpused = 0;
+  size_t graph_replays = 0;
+  double max_cond = 0; // of the last run
   HostBuf hdesc;
   std::vector<cudaEvent_t> events;
   // results of the last run
   int launches = 0, gemm_launches = 0;
+  double host_in_bytes = 0, host_out_bytes = 0;  // copies of the last run
   double gemm_dev_s = 0, inv_dev_s = 0, pack_dev_s = 0;
   double pack_bytes = 0;  // algorithmic bytes of the operand packs of the last run
   double inv_panel_dev_s = 0, inv_panel_flops = 0, inv_update_flops = 0;
@@ -116,7 +149,8 @@ struct Env {
   std::vector<cudaEvent_t> pevents;  // panel timing (profile)
   // buffers of the sweep (everything but the descriptor staging on the host)
   std::vector<DevBuf*> bufs() {
-    return {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &inv_tc, &desc, &status, &flags, &apk, &bpk, &b2pk, &tcerr, &oexp};
+    return {&inv_work, &inv_wrow, &inv_perm, &inv_amax, &inv_tc, &desc,  &status, &flags,
+            &apk,      &bpk,      &b2pk,     &tcerr,    &oexp,   &stage, &condw};
   }
   std::vector<int> job_singular;  // per job
   int64_t failed_inverse = -1;    // first singular inverse, in launch order
@@ -138,6 +172,10 @@ size_t pack_bytes(int bmax, int slices, size_t ops);
 // Device bytes of the digit slabs and row exponents of the FP64_TC path for a
 // run whose widest GEMM step has `ops` products of order bmax.
 size_t digit_bytes(int bmax, size_t ops);
+// Device bytes of the executor's descriptor arena, operand slabs and staging
+// for one job running schedule S at order b (what run_jobs allocates beside
+// the value slots and the inverse scratch).
+size_t arena_bytes(const Schedule& S, int b, int precision, int slices, int inv_chunk, int host_dt, int slot_dt);
 
 // Runs the schedules of `jobs` together: step t of every schedule goes out in
 // the same grouped launches.  Returns MBINV_ESINGULAR if any request met a

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kPanelThreads) gj_panel_kernel(const InvDesc* 
     P[i * ldp + t] = X[(int64_t)(r0 + i) * b + p + t];
   }
   const double amax = __longlong_as_double((long long)*d.amax);
-  const TW tol = (TW)((double)b * (double)eps_of<TW>() * amax);
+  const TW tol = (TW)((d.tol_rel > 0.0 ? d.tol_rel : (double)b * (double)eps_of<TW>()) * amax);
   __syncthreads();
 
   for (int t = 0; t < nb; ++t) {
@@ -495,11 +495,11 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     const int CL = cluster_for(b);
     if (((size_t)((b + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) return cudaErrorInvalidValue;
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+  {
+    cudaError_t e = once_per_device((const void*)gj_panel_kernel<TW>, [] {
+      return cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    });
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   for (int p = 0; p < b; p += nb) {
     const int w = std::min(nb, b - p);  // widest panel of this step (b is the largest order)
@@ -627,6 +627,56 @@ cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvD
   if (wtype == F64) return run_batch_t<double>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, tc, timing);
   if (tc) return cudaErrorInvalidValue;
   return run_batch_t<float>(in_dtype, out_dtype, d_desc, count, b, d_status, s, launches, nullptr, timing);
+}
+
+}  // namespace mbinv
+
+namespace mbinv {
+namespace {
+
+template <typename TS>
+__device__ double colsum_max(const TS* a, int64_t ld, int b) {
+  double m = 0.0;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < b; ++r) s += fabs((double)a[(int64_t)r * ld + c]);
+    m = s > m ? s : m;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  __syncthreads();
+  return m;  // valid in thread 0
+}
+
+// One CTA per matrix: ||src||_1 ||dst||_1 (largest column sums), folded
+// into d.cond as the bit pattern of a non-negative double (NaN stays out:
+// a singular inverse is reported through the status word instead).
+__global__ void __launch_bounds__(1024) cond1_kernel(const InvDesc* __restrict__ descs, int in_dtype,
+                                                     int out_dtype) {
+  const InvDesc d = descs[blockIdx.x];
+  if (!d.cond) return;
+  const double a = in_dtype == F64 ? colsum_max((const double*)d.src, d.lds, d.b)
+                                   : colsum_max((const float*)d.src, d.lds, d.b);
+  const double x = out_dtype == F64 ? colsum_max((const double*)d.dst, d.ldd, d.b)
+                                    : colsum_max((const float*)d.dst, d.ldd, d.b);
+  if (threadIdx.x == 0) {
+    const double k = a * x;
+    if (k >= 0.0 && k <= 1.7976931348623157e308) atomicMax(d.cond, (unsigned long long)__double_as_longlong(k));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cond1(const InvDesc* d_desc, int count, int in_dtype, int out_dtype, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cond1_kernel<<<count, 1024, 0, s>>>(d_desc, in_dtype, out_dtype);
+  return cudaGetLastError();
 }
 
 }  // namespace mbinv

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -13,6 +14,13 @@ namespace mbinv {
 enum DType : int { F64 = 0, F32 = 1, BF16 = 2 };
 
 inline size_t dtype_size(int t) { return t == F64 ? 8 : (t == F32 ? 4 : 2); }
+
+// Runs setup once per (key, current device) - a kernel's shared-memory
+// attribute, say - safely for several host threads and several devices;
+// retried on a later call if it failed.
+cudaError_t once_per_device(const void* key, const std::function<cudaError_t()>& setup);
+// Multiprocessors of the current device.
+int sm_count();
 
 // --------------------------------------------------------------- planner
 // A frame of the recursion (Sec. 3.1) after hash-consing: its value is
@@ -49,9 +57,12 @@ inline Plan build_plan(int k, int i, int j, bool pad_last) { return build_plan(k
 
 // Operand reference of a scheduled operation.
 struct Ref {
-  enum Kind : int { NONE = 0, MBLK = 1, SLOT = 2, OUT = 3 } kind = NONE;
-  int r = 0, c = 0;  // block coordinates for MBLK
-  int slot = -1;     // slot id for SLOT; request index for OUT
+  // MBLK: block (r, c) of the device matrix; SLOT: a device value slot; OUT:
+  // a request's output; HOSTM: block (r, c) of the matrix kept in host
+  // memory; SPILL: a slot of the host spill area
+  enum Kind : int { NONE = 0, MBLK = 1, SLOT = 2, OUT = 3, HOSTM = 4, SPILL = 5 } kind = NONE;
+  int r = 0, c = 0;  // block coordinates for MBLK / HOSTM
+  int slot = -1;     // slot id for SLOT / SPILL; request index for OUT
 };
 
 struct GemmOp {  // C = alpha * A * B + beta * Cin, all b x b
@@ -62,10 +73,16 @@ struct InvOp {  // dst = src^-1
   Ref src, dst;
   int frame = -1;
 };
+struct CopyOp {  // dst = src (host <-> device), b x b
+  Ref src, dst;
+};
 struct Step {
-  enum Kind : int { INV = 0, GEMM = 1 } kind = INV;
+  // COPY: values moved between host memory and device slots (a block of a
+  // host-resident M loaded, a value spilled to the host or brought back)
+  enum Kind : int { INV = 0, GEMM = 1, COPY = 2 } kind = INV;
   std::vector<InvOp> inv;
   std::vector<GemmOp> gemm;
+  std::vector<CopyOp> copy;
 };
 
 struct Schedule {
@@ -79,12 +96,25 @@ struct Schedule {
   size_t request_frames = 0;    // frames the requests would evaluate one by one
   int inv_chunk = 0;            // matrices per inverse launch chosen to fit the cap
   size_t planned = 0;           // device bytes of its workspace with that chunk
+  // bounded schedules (build_bounded_schedule)
+  bool bounded = false;
+  int nspill = 0;               // host spill slots needed at once
+  size_t loads = 0, spills = 0; // b x b copies host -> device and device -> host
 };
 
 // Builds the level-by-level schedule of a plan (one or several requests).
 // zchunk bounds the number of Schur temporaries alive at once (0 = a whole
 // level).
 Schedule build_schedule(const Plan& p, int zchunk);
+
+// The memory-bounded schedule of a plan: frames evaluated depth first, one
+// operation per step, in at most `slots` device value slots.  The blocks of M
+// come from host memory when host_m (HOSTM copies) and from the device
+// matrix otherwise; a value evicted while it is still needed is spilled to
+// a host slot and copied back before its next use, the victim being the value
+// needed again last (Belady's rule on the known sequence).  Returns false
+// when `slots` is too small for a single operation.
+bool build_bounded_schedule(const Plan& p, int slots, bool host_m, Schedule* out);
 
 // --------------------------------------------------------------- kernels
 struct GemmDesc {
@@ -125,7 +155,15 @@ struct InvDesc {
   int b;
   int tag;          // reported through the status word when singular
   int* flag;        // set to 1 when singular (may be null): per-problem status
+  double tol_rel;   // a pivot is singular at or below tol_rel * max|entry|;
+                    // 0 = b times the unit roundoff of the working type
+  unsigned long long* cond;  // if set: max with the bits of ||src||_1 ||dst||_1
 };
+
+// Largest 1-norm condition estimate ||src||_1 ||dst||_1 of count inverted
+// matrices, folded (as the bit pattern of a non-negative double) into each
+// descriptor's cond word.
+cudaError_t launch_cond1(const InvDesc* d_desc, int count, int in_dtype, int out_dtype, cudaStream_t s);
 // Status word written by the inverse kernels: flag != 0 when a pivot was
 // singular; tag holds the smallest failing InvDesc::tag.
 struct DevStatus {

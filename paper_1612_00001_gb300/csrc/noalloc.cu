@@ -17,9 +17,11 @@
 //     and kept between calls (each call rewrites every word it reads).  Calls
 //     whose work overlaps on the GPU - two host threads, or two streams -
 //     race on it; serialise them.
+//   - Each call waits on the host for its own result (it reads its status
+//     word back before returning).
 //   - The first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture.
+//     (cudaGetSymbolAddress) with that device current; that first call
+//     should come before any stream capture.
 //   - No cudaMalloc, cudaFree or other allocating routine is called.
 #include <cuda_runtime.h>
 

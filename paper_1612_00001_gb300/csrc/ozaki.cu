@@ -48,6 +48,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include "mbinv_internal.h"
 #include "ozaki.h"
 #include "tcgen05_ptx.cuh"
 
@@ -203,7 +204,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* emptyA = fullA + ASTAGES;
   uint64_t* tfull = emptyA + ASTAGES;   // accumulators of a tile complete (MMA -> epilogue)
   uint64_t* tempty = tfull + 1;         // accumulators read out (epilogue -> MMA)
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+  uint64_t* stall = tempty + 1;         // test of the timeout path: never arrived at
+  uint32_t* tmem_slot = (uint32_t*)(stall + 1);
   int* failed = (int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     mbar_init(tfull, 1);
     mbar_init(tempty, NEPI);
+    mbar_init(stall, 1);
     *failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -233,8 +236,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  if (P.stall_ns) {
+    // nothing arrives at `stall`: the wait runs out, the CTA raises the
+    // error word and every role below finds `failed` set before it issues
+    // anything
+    if (threadIdx.x == 0 && !mbar_wait_ns(stall, 0, P.stall_ns)) {
+      *failed = 1;
+      if (P.err) atomicExch(P.err, 1);
+    }
+    __syncthreads();
+  }
+  const bool stalled = *(volatile int*)failed != 0;
 
-  if (warp == 0) {
+  if (stalled) {
+    // skip every role
+  } else if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer: runs ahead into the next tile while the
       // epilogue of the current one drains the accumulators
@@ -518,6 +534,10 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
 
 }  // namespace
 
+unsigned long long g_stall_ns = 0;
+
+void set_debug_stall(unsigned long long ns) { g_stall_ns = ns; }
+
 int tile_m() { return BM; }
 int tile_n() { return BN; }
 int tile_k() { return BK; }
@@ -528,12 +548,12 @@ cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kp
                         cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (rows_pad % PR || kpad % BK || ((uintptr_t)dst & 3)) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
+  {
     // the largest stage: 64 rows x 129 or 16 rows x 513 entries, about 66 KB
-    cudaError_t e = cudaFuncSetAttribute(oz_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPackSmemMax);
+    cudaError_t e = once_per_device((const void*)oz_pack_kernel, [] {
+      return cudaFuncSetAttribute(oz_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPackSmemMax);
+    });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int kc = kpad < PKC ? kpad : PKC;
   // rows per CTA: about 66 KB of staged entries, 16..64 rows (rows_pad is a multiple of 64)
@@ -558,20 +578,16 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
   CUtensorMap ta, tb;
   if (!make_map(&ta, apk, P.kpad, a_rows_pad, a_slabs * ND, BM, BK, 1)) return cudaErrorInvalidValue;
   if (!make_map(&tb, bpk, P.kpad, b_rows_pad, b_slabs * ND, BN, BK, ND)) return cudaErrorInvalidValue;
-  static bool attr = false;
   const size_t sm = smem_bytes();
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    cudaError_t e = once_per_device((const void*)oz_gemm_kernel, [sm] {
+      return cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  Params Q = P;
+  Q.stall_ns = g_stall_ns;
+  const int sms = sm_count();
   const int total = count * P.tiles_m * P.tiles_n;
   int grid = total < sms ? total : sms;
   if (P.coprime_grid) {
@@ -585,7 +601,7 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
     };
     while (grid > 1 && gcd(grid, P.tiles_n) != 1) --grid;
   }
-  oz_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, P, d_probs, total);
+  oz_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, Q, d_probs, total);
   return cudaGetLastError();
 }
 

@@ -56,7 +56,14 @@ struct Params {
   // dead tiles recurring with the column period (skipped columns) fall on
   // every CTA alike instead of on the CTAs whose index shares the period
   int coprime_grid;
+  // Test of the timeout path: when nonzero, every CTA first waits this many
+  // nanoseconds on a barrier nothing arrives at, raises err and returns
+  // before issuing any copy or product (nothing is left in flight).
+  unsigned long long stall_ns;
 };
+
+// Sets the stall of every later launch_gemm (0 = none); a test hook.
+void set_debug_stall(unsigned long long ns);
 
 int tile_m();  // 128 output rows per CTA
 int tile_n();  // 64 output columns per CTA

@@ -387,3 +387,310 @@ Schedule build_schedule(const Plan& P, int zchunk) {
 }
 
 }  // namespace mbinv
+
+// ------------------------------------------------------- bounded schedule
+//
+// Values of a bounded run, each a b x b matrix: a block of M, the inverse of
+// a leaf pivot block, T = P^-1 M[prow, c], a frame's value, the inverse of a
+// frame used as a pivot, Z = piv^-1 right.  Each is computed once, in the
+// order a depth-first walk from the roots asks for it; the slot allocation
+// below then decides which of them wait on the host.
+
+namespace mbinv {
+
+namespace {
+
+struct BVal {
+  enum Kind : int { MB, PINV, T, F, FINV, Z } kind;
+  int a = -1, b = -1, c = -1;  // MB (r, c); PINV (prow, pcol); T (prow, pcol, col); F/FINV frame; Z (piv, right)
+};
+
+struct BOp {
+  int kind;         // 0 inverse, 1 product
+  int out;          // value id, or -1 - r for the output of request r
+  int in[3];        // inverse: in[0]; product: A, B, Cin (Cin may be -1)
+  double alpha, beta;
+};
+
+struct Bounded {
+  const Plan& P;
+  std::vector<BVal> vals;
+  std::map<std::array<int, 4>, int> ids;
+  std::vector<char> done;
+  std::vector<BOp> ops;
+
+  explicit Bounded(const Plan& p) : P(p) {}
+
+  int id(int kind, int a, int b = -1, int c = -1) {
+    auto key = std::array<int, 4>{kind, a, b, c};
+    auto it = ids.find(key);
+    if (it != ids.end()) return it->second;
+    BVal v;
+    v.kind = (BVal::Kind)kind;
+    v.a = a;
+    v.b = b;
+    v.c = c;
+    vals.push_back(v);
+    done.push_back(0);
+    ids.emplace(key, (int)vals.size() - 1);
+    return (int)vals.size() - 1;
+  }
+
+  void emit(int kind, int out, int i0, int i1, int i2, double alpha = 1.0, double beta = 0.0) {
+    BOp o;
+    o.kind = kind;
+    o.out = out;
+    o.in[0] = i0;
+    o.in[1] = i1;
+    o.in[2] = i2;
+    o.alpha = alpha;
+    o.beta = beta;
+    ops.push_back(o);
+  }
+
+  // Makes value v available: its inputs first (depth first), then its op.
+  void need(int v) {
+    if (done[v]) return;
+    done[v] = 1;
+    const BVal x = vals[v];
+    switch (x.kind) {
+      case BVal::MB:
+        return;  // read from M where it lives
+      case BVal::PINV: {
+        const int m = id(BVal::MB, x.a, x.b);
+        need(m);
+        emit(0, v, m, -1, -1);
+        return;
+      }
+      case BVal::T: {
+        const int pi = id(BVal::PINV, x.a, x.b), m = id(BVal::MB, x.a, x.c);
+        need(pi);
+        need(m);
+        emit(1, v, pi, m, -1, 1.0, 0.0);
+        return;
+      }
+      case BVal::FINV: {
+        const int f = id(BVal::F, x.a);
+        need(f);
+        emit(0, v, f, -1, -1);
+        return;
+      }
+      case BVal::Z: {
+        // the right operand first, then the pivot and its inverse: the order
+        // of the walk that keeps the fewest values alive at once
+        const int pi = id(BVal::FINV, x.a), r = id(BVal::F, x.b);
+        need(r);
+        need(pi);
+        emit(1, v, pi, r, -1, 1.0, 0.0);
+        return;
+      }
+      case BVal::F: {
+        const PFrame& fr = P.f[x.a];
+        if (fr.order == 2) {  // leaf = M[a,c] - M[a,pc] T_c
+          const int t = id(BVal::T, fr.prow, fr.pcol, fr.kcol);
+          const int ma = id(BVal::MB, fr.krow, fr.pcol), mk = id(BVal::MB, fr.krow, fr.kcol);
+          need(t);
+          need(ma);
+          need(mk);
+          emit(1, v, ma, t, mk, -1.0, 1.0);
+        } else {  // X = kept - left * Z
+          const int z = id(BVal::Z, fr.piv, fr.right);
+          const int kv = id(BVal::F, fr.kept), lv = id(BVal::F, fr.left);
+          need(kv);
+          need(lv);
+          need(z);
+          emit(1, v, lv, z, kv, -1.0, 1.0);
+        }
+        return;
+      }
+    }
+  }
+};
+
+}  // namespace
+
+bool build_bounded_schedule(const Plan& P, int slots, bool host_m, Schedule* out) {
+  Bounded B(P);
+  for (size_t r = 0; r < P.roots.size(); ++r) {
+    const int f = B.id(BVal::F, P.roots[r]);
+    B.need(f);
+    B.emit(0, -1 - (int)r, f, -1, -1);
+  }
+  const int nv = (int)B.vals.size();
+  // a value lives in a slot unless it is a block of a device-resident M
+  auto slotted = [&](int v) { return v >= 0 && (B.vals[v].kind != BVal::MB || host_m); };
+  // uses of every value, in op order
+  std::vector<std::vector<int>> uses(nv);
+  for (int t = 0; t < (int)B.ops.size(); ++t)
+    for (int q = 0; q < 3; ++q)
+      if (B.ops[t].in[q] >= 0) uses[B.ops[t].in[q]].push_back(t);
+  std::vector<size_t> up(nv, 0);  // uses[v][up[v]] is v's next use
+  auto next_use = [&](int v) { return up[v] < uses[v].size() ? uses[v][up[v]] : INT32_MAX; };
+
+  Schedule S;
+  S.bounded = true;
+  S.nouts = (int)P.roots.size();
+  std::vector<int> slot_of(nv, -1), host_of(nv, -1);
+  std::vector<int> free_slots, free_host;
+  for (int q = slots - 1; q >= 0; --q) free_slots.push_back(q);
+  int host_next = 0, host_live = 0;
+  std::vector<int> resident;  // values holding a slot
+  auto ref_slot = [](int s) {
+    Ref x;
+    x.kind = Ref::SLOT;
+    x.slot = s;
+    return x;
+  };
+  auto push_copy = [&](const Ref& src, const Ref& dst) {
+    if (S.steps.empty() || S.steps.back().kind != Step::COPY) {
+      Step st;
+      st.kind = Step::COPY;
+      S.steps.push_back(st);
+    }
+    S.steps.back().copy.push_back(CopyOp{src, dst});
+  };
+  // a free slot, evicting the resident value needed again last if there is
+  // none (held: values the current op uses, which stay)
+  auto take_slot = [&](const int* held, int nheld) -> int {
+    if (free_slots.empty()) {
+      int victim = -1, far = -1;
+      for (int v : resident) {
+        bool h = false;
+        for (int q = 0; q < nheld; ++q) h |= held[q] == v;
+        if (h) continue;
+        const int nu = next_use(v);
+        if (nu > far) {
+          far = nu;
+          victim = v;
+        }
+      }
+      if (victim < 0) return -1;
+      if (next_use(victim) != INT32_MAX && B.vals[victim].kind != BVal::MB && host_of[victim] < 0) {
+        int h;
+        if (!free_host.empty()) {
+          h = free_host.back();
+          free_host.pop_back();
+        } else {
+          h = host_next++;
+        }
+        host_of[victim] = h;
+        ++host_live;
+        S.nspill = std::max(S.nspill, host_live);
+        Ref d;
+        d.kind = Ref::SPILL;
+        d.slot = h;
+        push_copy(ref_slot(slot_of[victim]), d);
+        ++S.spills;
+      }
+      free_slots.push_back(slot_of[victim]);
+      slot_of[victim] = -1;
+      resident.erase(std::find(resident.begin(), resident.end(), victim));
+    }
+    const int s = free_slots.back();
+    free_slots.pop_back();
+    S.nslots = std::max(S.nslots, slots - (int)free_slots.size());
+    return s;
+  };
+  auto release = [&](int v) {  // v has no use left
+    if (slot_of[v] >= 0) {
+      free_slots.push_back(slot_of[v]);
+      slot_of[v] = -1;
+      resident.erase(std::find(resident.begin(), resident.end(), v));
+    }
+    if (host_of[v] >= 0) {
+      free_host.push_back(host_of[v]);
+      host_of[v] = -1;
+      --host_live;
+    }
+  };
+  for (int t = 0; t < (int)B.ops.size(); ++t) {
+    const BOp& o = B.ops[t];
+    int held[4] = {o.in[0], o.in[1], o.in[2], o.out};
+    // inputs into slots
+    for (int q = 0; q < 3; ++q) {
+      const int u = o.in[q];
+      if (!slotted(u) || slot_of[u] >= 0) continue;
+      const int s = take_slot(held, 4);
+      if (s < 0) return false;
+      Ref src;
+      if (B.vals[u].kind == BVal::MB) {
+        src.kind = Ref::HOSTM;
+        src.r = B.vals[u].a;
+        src.c = B.vals[u].b;
+      } else {
+        if (host_of[u] < 0) return false;  // a value is always computed before it is read
+        src.kind = Ref::SPILL;
+        src.slot = host_of[u];
+      }
+      push_copy(src, ref_slot(s));
+      ++S.loads;
+      slot_of[u] = s;
+      resident.push_back(u);
+    }
+    int so = -1;
+    if (o.out >= 0) {
+      so = take_slot(held, 4);
+      if (so < 0) return false;
+    }
+    auto ref_of = [&](int v) {
+      Ref x;
+      if (v < 0) return x;
+      if (slotted(v)) return ref_slot(slot_of[v]);
+      x.kind = Ref::MBLK;
+      x.r = B.vals[v].a;
+      x.c = B.vals[v].b;
+      return x;
+    };
+    Ref dst;
+    if (o.out >= 0) {
+      dst = ref_slot(so);
+    } else {
+      dst.kind = Ref::OUT;
+      dst.slot = -1 - o.out;
+    }
+    Step st;
+    if (o.kind == 0) {
+      st.kind = Step::INV;
+      InvOp io;
+      io.src = ref_of(o.in[0]);
+      io.dst = dst;
+      st.inv.push_back(io);
+      S.inv_units += 2;
+      S.inversions += 1;
+    } else {
+      st.kind = Step::GEMM;
+      GemmOp g;
+      g.A = ref_of(o.in[0]);
+      g.B = ref_of(o.in[1]);
+      g.Cin = ref_of(o.in[2]);
+      g.C = dst;
+      g.alpha = o.alpha;
+      g.beta = o.beta;
+      st.gemm.push_back(g);
+      S.gemm_flops_units += 2;
+    }
+    S.steps.push_back(st);
+    S.max_inv_batch = 1;
+    // uses consumed; values with none left let go of their slot and host copy
+    for (int q = 0; q < 3; ++q) {
+      const int u = o.in[q];
+      if (u < 0) continue;
+      while (up[u] < uses[u].size() && uses[u][up[u]] <= t) ++up[u];
+    }
+    for (int q = 0; q < 3; ++q) {
+      const int u = o.in[q];
+      if (u >= 0 && next_use(u) == INT32_MAX) release(u);
+    }
+    if (o.out >= 0) {
+      slot_of[o.out] = so;
+      resident.push_back(o.out);
+      if (next_use(o.out) == INT32_MAX) release(o.out);
+    }
+  }
+  S.frames = P.f.size();
+  S.request_frames = P.request_frames;
+  *out = std::move(S);
+  return true;
+}
+
+}  // namespace mbinv

@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "mbinv_internal.h"
 #include "tc_gemm.h"
 #include "tcgen05_ptx.cuh"
 
@@ -257,12 +258,12 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
   CUtensorMap ta, tb;
   if (!make_map(&ta, apk, P.kpad, a_rows_pad, a_slabs * P.S, BM)) return cudaErrorInvalidValue;
   if (!make_map(&tb, bpk, P.kpad, b_rows_pad, b_slabs * P.S, BN)) return cudaErrorInvalidValue;
-  static bool attr = false;
   const size_t sm = smem_bytes();
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    cudaError_t e = once_per_device((const void*)tc_gemm_kernel, [sm] {
+      return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int grid = count * P.tiles_m * P.tiles_n;
   tc_gemm_kernel<<<grid, THREADS, sm, s>>>(ta, tb, P, d_probs);

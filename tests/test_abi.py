@@ -96,7 +96,7 @@ def header_struct(name):
 
 
 @pytest.mark.parametrize("cname,pyname", [("mbinv_report", "Report"), ("mbinv_options", "Options"),
-                                          ("mbinv_problem", "Problem")])
+                                          ("mbinv_problem", "Problem"), ("mbinv_rbf", "Rbf")])
 def test_binding_structs_match_header(cname, pyname):
     """The ctypes mirrors declare the header's fields in the header's order
     with the same types (a drifted struct would shift every later field)."""
