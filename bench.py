@@ -81,10 +81,15 @@ def parse():
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--batched", type=int, default=0,
                    help="batched workload: this many independent matrices of uneven n and k, one block each")
+    p.add_argument("--peaks", action="store_true",
+                   help="measure the FP64 and FP32 (no TF32) library GEMM rates that the FP64/FP32 rooflines "
+                        "are read against: torch.matmul on 8192^3, best of 5, CUDA events")
     p.add_argument("--large", action="store_true",
                    help="memory-bounded workload: n x n Householder matrix in FP32 host memory under a device cap, "
                         "one block per step by the bounded schedule (use --n 65536 --k 16)")
     p.add_argument("--cap-gb", type=float, default=24.0)
+    p.add_argument("--sing-tol", type=float, default=0.0,
+                   help="relative singularity threshold of the pivots (0: b times the unit roundoff)")
     p.add_argument("--block", type=int, nargs=2, default=[0, 15])
     p.add_argument("--backward", action="store_true",
                    help="differentiation workload: one block forward and the adjoint backward per step")
@@ -508,6 +513,34 @@ def run_inverses(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_peaks(args, rank):
+    """FP64 and FP32 GEMM rates of the library (cuBLAS through torch.matmul,
+    TF32 off) on 8192^3: the measured ceilings beside the nominal FP64 1.25
+    TFLOP/s used for the CUDA-core kernels' rooflines."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    n = 8192
+    out = {}
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        a = torch.rand((n, n), dtype=dt, device="cuda")
+        b = torch.rand((n, n), dtype=dt, device="cuda")
+        for _ in range(2):
+            a @ b
+        best = 1e9
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    if rank == 0:
+        print(json.dumps({"metric": "library GEMM rate (torch.matmul, 8192^3, best of 5)", "unit": "TFLOP/s",
+                          "fp64_tflops": out["fp64"], "fp32_tflops": out["fp32"], "tf32": False}), flush=True)
+
+
 def run_large(args, rank, world, dist):
     """The memory-bounded workload: n = 65536, k = 16 (b = 4096), M = U diag(sigma)
     V^T with U, V each a product of 64 Householder reflectors, cond(M) = kappa,
@@ -534,7 +567,7 @@ def run_large(args, rank, world, dist):
     i, j = args.block
     stream = torch.cuda.current_stream()
     out = torch.empty((b, b), dtype=torch.float64, device="cuda")
-    ctx = mb.Context(mh, k, precision=args.precision, cap=cap, out_dtype=torch.float64)
+    ctx = mb.Context(mh, k, precision=args.precision, cap=cap, out_dtype=torch.float64, sing_tol=args.sing_tol)
     for _ in range(args.warmup):
         ctx.block(i, j, out=out)
     clocks = _clock_region(0)
@@ -575,6 +608,7 @@ def run_large(args, rank, world, dist):
                        "host_in_bytes": rep["host_in_bytes"], "host_out_bytes": rep["host_out_bytes"],
                        "host_spill_bytes": rep["host_spill_bytes"], "frames": rep["frames"],
                        "inversions": rep["inversions"], "launches": rep["launches"],
+                       "max_pivot_cond": rep["max_pivot_cond"], "sing_tol": args.sing_tol,
                        "fp64_equivalent_tflops": flops / secs / 1e12,
                        "rel_err_vs_inverse_of_stored_matrix": err,
                        "rel_err_vs_inverse_of_unrounded_matrix": err_unrounded,
@@ -601,7 +635,7 @@ def run_backward(args, rank, world, dist):
     M = torch.tensor(m, dtype=dt, device="cuda")
     W = torch.tensor(bi.gaussian_matrix(b, b, 0), dtype=dt, device="cuda")
     i, j = 1, k - 2
-    ctx = mb.Context(M, k, precision=args.precision, slices=args.slices)
+    ctx = mb.Context(M, k, precision=args.precision, slices=args.slices, refine=args.refine)
     dM = torch.zeros((n, n), dtype=dt, device="cuda")
 
     def step():
@@ -635,7 +669,7 @@ def run_backward(args, rank, world, dist):
             "dtype": dtype_name(args),
             "data": "synthetic",
             "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, L = sum(W * N_{i}{j}), "
-                                   f"forward + adjoint ({args.precision})",
+                                   f"forward + adjoint ({args.precision}, refine {args.refine})",
                        "rel_err_forward_vs_dense": ferr, "rel_err_grad_vs_fp64_reference": gerr},
             "clocks": clk}
     if rank == 0:
@@ -671,6 +705,8 @@ def main():
         return run_backward(args, rank, world, dist)
     if args.large:
         return run_large(args, rank, world, dist)
+    if args.peaks:
+        return run_peaks(args, rank)
     n, k = args.n, args.k
     b = -(-n // k)
     bps = args.blocks_per_step

@@ -312,12 +312,13 @@ mbinv_status mbinv_block_col(mbinv_ctx *ctx, int64_t j, void *out, int64_t ldo, 
  * accumulated into, both in M's dtype, host or device.  On MBINV_FP64 and
  * MBINV_FP64_TC the rows, columns and products are FP64 (digit products on
  * the tensor cores on FP64_TC), and with refine_steps = 1 every block of
- * M^-1 is first computed (runs merged) and X_i, Y_j are each corrected by
- * one Newton step against that whole approximate inverse N~:
- * X_i + (E_i^T - X_i M) N~ and Y_j + N~ (E_j - M Y_j), which squares their
- * error (n^2 doubles of device memory; M on the device, k dividing n, else
- * MBINV_ENOTSUP).  The paper has no gradient; this is the derivative of its
- * output. */
+ * M^-1 is first computed (runs merged) and that whole approximate inverse
+ * N~ is improved by Newton-Schulz steps N~ <- N~ + N~ (I - M N~), each of
+ * which squares ||I - M N~||, until that residual stops falling (at most 6;
+ * its last value in rel_residual), X_i and Y_j then being its block row and
+ * column (3 n^2 doubles of device memory; M on the device, k dividing n,
+ * else MBINV_ENOTSUP).  The paper has no gradient; this is the derivative of
+ * its output. */
 mbinv_status mbinv_backward(mbinv_ctx *ctx, int64_t i, int64_t j, const void *G, int64_t ldg, void *dM, int64_t ldd,
                             mbinv_report *report);
 

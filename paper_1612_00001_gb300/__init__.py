@@ -393,6 +393,6 @@ class _BlockInverse:
 def block(M, k: int, i: int, j: int, precision="fp64", cap: int = 0, refine: int = 0):
     """Differentiable N_ij of M^-1: the backward pass is the hand-written
     adjoint dM = -(X_i)^T G (Y_j)^T, with X_i and Y_j recomputed block by block
-    (refine = 1: the forward block refined, and X_i, Y_j corrected by one
-    Newton step against the whole approximate inverse before the adjoint)."""
+    (refine = 1: the forward block refined, and X_i, Y_j taken from the
+    whole approximate inverse after Newton-Schulz steps)."""
     return _BlockInverse.get().apply(M, k, i, j, precision, cap, refine)

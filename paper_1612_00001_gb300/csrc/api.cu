@@ -1157,11 +1157,10 @@ mbinv_status prod64(mbinv_ctx* c, const double* A, int64_t lda, int ta, const do
 }
 
 // The adjoint of L = sum(G .* N_ij): dM += -(X_i)^T G (Y_j)^T.  On the
-// FP64-valued paths with refine_steps = 1 the block row X_i and column Y_j
-// are first corrected by one Newton step each against the whole approximate
-// inverse N~ (every block by the merged sweep):
-//   X_i <- X_i + (E_i^T - X_i M) N~,   Y_j <- Y_j + N~ (E_j - M Y_j),
-// which squares their error (the correction of X_i leaves -dX M dN~...).
+// FP64-valued paths with refine_steps = 1 the whole approximate inverse N~
+// (every block by the merged sweep) is first improved by Newton-Schulz steps
+// N~ <- N~ + N~ (I - M N~) - each squares ||I - M N~|| - and X_i, Y_j are its
+// block row and column.
 static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void* G, int64_t ldg, void* dM,
                                   int64_t ldd, mbinv_report* rep) {
   const int64_t bi = block_extent(c, i), bj = block_extent(c, j), n = c->n, b = c->b;
@@ -1189,33 +1188,44 @@ static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void
     c->odt = saved_odt;
     if (s != MBINV_OK) return s;
     release_sweep(c);
-    const double* Nt = (const double*)c->dmbuf.p;
-    // X_i' = X_i + (E_i^T - X_i M) N~   (rowbuf: R, then X_i')
-    CU(c->resid.ensure(((size_t)bi * n + (size_t)n * bj) * 8 * 2 + 512));
-    double* R = (double*)c->resid.p;
-    double* Xr = R + (size_t)bi * n;
-    double* S = Xr + (size_t)bi * n;
-    double* Yr = S + (size_t)n * bj;
-    const double* Xi = Nt + (size_t)i * b * n;
-    const double* Yj = Nt + (size_t)j * b;
-    s = prod64(c, Xi, n, 0, (const double*)c->dM, c->ldm, 0, nullptr, 0, R, n, (int)bi, (int)n, (int)n, -1.0, 0.0);
-    if (s != MBINV_OK) return s;
-    add_eye_kernel<<<(unsigned)((bi + 255) / 256), 256, 0, c->stream>>>(R, n, i * b, bi);
-    CU(cudaGetLastError());
-    s = prod64(c, R, n, 0, Nt, n, 0, Xi, n, Xr, n, (int)bi, (int)n, (int)n, 1.0, 1.0);
-    if (s != MBINV_OK) return s;
-    // Y_j' = Y_j + N~ (E_j - M Y_j)
-    s = prod64(c, (const double*)c->dM, c->ldm, 0, Yj, n, 0, nullptr, 0, S, bj, (int)n, (int)bj, (int)n, -1.0, 0.0);
-    if (s != MBINV_OK) return s;
-    add_eye_kernel<<<(unsigned)((bj + 255) / 256), 256, 0, c->stream>>>(S + (size_t)j * b * bj, bj, 0, bj);
-    CU(cudaGetLastError());
-    s = prod64(c, Nt, n, 0, S, bj, 0, Yj, n, Yr, bj, (int)n, (int)bj, (int)n, 1.0, 1.0);
-    if (s != MBINV_OK) return s;
-    X = Xr;
+    // Newton-Schulz on the whole approximate inverse: E = I - M N~,
+    // N~ <- N~ + N~ E, which squares ||E|| each time; until ||E||_F / sqrt(n)
+    // stops falling or is at the rounding level (at most 6 steps)
+    CU(c->rowbuf.ensure((size_t)n * n * 8 + 256));
+    CU(c->colbuf.ensure((size_t)n * n * 8 + 256));
+    CU(c->resid.ensure(512));
+    double* Nt = (double*)c->dmbuf.p;
+    double* E = (double*)c->rowbuf.p;
+    double* Nn = (double*)c->colbuf.p;
+    double* acc = (double*)c->resid.p;
+    double last = 1e300;
+    for (int it = 0; it < 6; ++it) {
+      s = prod64(c, (const double*)c->dM, c->ldm, 0, Nt, n, 0, nullptr, 0, E, n, (int)n, (int)n, (int)n, -1.0, 0.0);
+      if (s != MBINV_OK) return s;
+      add_eye_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(E, n, 0, n);
+      CU(cudaGetLastError());
+      CU(cudaMemsetAsync(acc, 0, sizeof(double), c->stream));
+      sumsq_kernel<<<152, 256, 0, c->stream>>>(E, n, n, n, acc);
+      CU(cudaGetLastError());
+      double h = 0;
+      CU(cudaMemcpyAsync(&h, acc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      const double res = std::sqrt(h / (double)n);
+      if (rep) {
+        rep->rel_residual = res;
+        rep->gemm_flops += 2.0 * (double)n * n * n;
+      }
+      if (!(res < 0.5 * last) || res < 1e-14) break;  // converged, or no longer contracting
+      last = res;
+      s = prod64(c, Nt, n, 0, E, n, 0, Nt, n, Nn, n, (int)n, (int)n, (int)n, 1.0, 1.0);
+      if (s != MBINV_OK) return s;
+      if (rep) rep->gemm_flops += 2.0 * (double)n * n * n;
+      std::swap(Nt, Nn);
+    }
+    X = Nt + (size_t)i * b * n;
     ldx = n;
-    Y = Yr;
-    ldy = bj;
-    if (rep) rep->gemm_flops += 2.0 * 2.0 * bi * n * n + 2.0 * 2.0 * n * n * bj;
+    Y = Nt + (size_t)j * b;
+    ldy = n;
   } else {
     CU(c->rowbuf.ensure((size_t)b * n * 8 + 256));
     CU(c->colbuf.ensure((size_t)n * b * 8 + 256));

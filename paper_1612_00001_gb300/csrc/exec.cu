@@ -841,7 +841,9 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
     }
     return MBINV_OK;
   };
-  bool graphable = E.use_graphs;
+  // (profiled calls run eagerly: their per-launch events are read back
+  // with cudaEventElapsedTime, which graph-recorded events do not serve)
+  bool graphable = E.use_graphs && !E.profile;
   for (const Launch& l : L)
     if (l.kind == Launch::COPY || l.kind == Launch::GEN || l.kind == Launch::CONVERT) graphable = false;
   std::vector<uintptr_t> key;

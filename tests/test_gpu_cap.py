@@ -86,34 +86,22 @@ def test_host_matrix_copy_counts_toward_the_cap(mb):
 @pytest.mark.parametrize("prec,host_dtype", [("fp64_tc", torch.float64), ("fp64", torch.float64),
                                              ("fp64_tc", torch.float32)])
 def test_bounded_schedule_under_a_cap_below_the_matrix(mb, prec, host_dtype):
-    """n = 2048, k = 16 (b = 128), M in host memory and a cap of 60% of M's
-    own FP64 bytes: M stays on the host and is read block by block, frames
-    are evaluated depth first in the slots the cap leaves, values needed
-    later wait in host memory.  Bit for bit the level-by-level result with M
-    on the device, within the FP64 bar of the oracle, and under the cap as
-    measured."""
-    n, k = 2048, 16
+    """n = 2048, k = 8 (b = 256), M in host memory (FP64, or FP32 with the
+    blocks returned in FP64) and a cap of 60% of M's own FP64 bytes: M stays
+    on the host and is read block by block, frames are evaluated depth first
+    in the slots the cap leaves, values needed later wait in host memory.  Bit
+    for bit the level-by-level result with M on the device, within the FP64
+    bar of the oracle, and under the cap as measured."""
+    n, k = 2048, 8
     m = bi.uniform_shift(n, 21)
     if host_dtype == torch.float32:
         m = m.astype(np.float32).astype(np.float64)
-    # requests the level-by-level run finishes on this matrix: at k = 16 some
-    # requests meet a pivot frame singular to working precision (the paper's
-    # order is unstable and the method then stops), in the oracle as on the
-    # GPU, where FP64_TC's per-row scaling meets it on more of them
-    ij, ref = [], []
+    ij = [(0, 7), (5, 2)]
     with mb.Context(torch.tensor(m, device="cuda"), k, precision=prec) as ref_ctx:
-        for cand in [(0, 15), (15, 3), (7, 9), (0, 0), (5, 5), (15, 15), (7, 3)]:
-            try:
-                ref.append(to_np(ref_ctx.block(*cand)))
-                ij.append(cand)
-            except mb.MbinvError as e:
-                assert e.status == mb.ESINGULAR
-            if len(ij) == 2:
-                break
-    assert ij, "no request of the list finishes"
+        ref = [to_np(x) for x in ref_ctx.blocks(ij)]
     cap = int(0.6 * n * n * 8)
     hm = torch.tensor(m, dtype=host_dtype)
-    with mb.Context(hm, k, precision=prec, cap=cap) as ctx:
+    with mb.Context(hm, k, precision=prec, cap=cap, out_dtype=torch.float64) as ctx:
         got = [to_np(x) for x in ctx.blocks(ij)]
         rep = ctx.last_report
     assert rep["peak_device_bytes"] <= cap, (rep["peak_device_bytes"], cap)
@@ -124,6 +112,27 @@ def test_bounded_schedule_under_a_cap_below_the_matrix(mb, prec, host_dtype):
     for (i, j), g in zip(ij, got):
         tol, floor = parity_tol(m, k, i, j, 1e-11)
         assert oracle.rel_fro(g, oracle_block(m, k, i, j)) <= tol, (i, j)
+
+
+def test_bounded_schedule_deep_recursion(mb):
+    """k = 16 (3502 frames per request, 646 values alive at once in the
+    depth-first walk), n = 2048, two requests merged, M in host memory under
+    a cap of 60% of its bytes: bit for bit the level-by-level blocks.  (No
+    oracle comparison here: at this size the paper's order is so unstable that
+    the oracle's own sensitivity floor is about 1; k = 16 against the oracle
+    is covered at b = 32 in test_gpu_parity.py.)"""
+    n, k = 2048, 16
+    m = bi.uniform_shift(n, 21)
+    ij = [(15, 3), (7, 9)]
+    with mb.Context(torch.tensor(m, device="cuda"), k, precision="fp64_tc") as ref_ctx:
+        ref = [to_np(x) for x in ref_ctx.blocks(ij)]
+    cap = int(0.6 * n * n * 8)
+    with mb.Context(torch.tensor(m), k, precision="fp64_tc", cap=cap) as ctx:
+        got = [to_np(x) for x in ctx.blocks(ij)]
+        rep = ctx.last_report
+    assert rep["peak_device_bytes"] <= cap and rep["host_spill_bytes"] > 0
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
 
 
 def test_bounded_schedule_large_blocks(mb):
