@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--together", type=int, default=64,
                    help="run each step's blocks as independent runs, this many executed together level by level "
                         "in grouped launches (0: one run after the other)")
+    p.add_argument("--variant", default="paper", choices=["paper", "principal"],
+                   help="paper: the paper's recursion; principal: the reformulation around M/A (principal pivots)")
     p.add_argument("--matrix", default="uniform", choices=["uniform", "haar", "spd"])
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--batched", type=int, default=0,
@@ -208,7 +210,7 @@ def fp64_path_arm(args, M, k, b, bps, rank, world, first_block, m_host):
     outs = [torch.empty((b, b), dtype=torch.float64, device="cuda") for _ in range(bps)]
     last = args.warmup + args.steps - 1
     ij = rank_blocks(k, rank, world, last, bps)
-    with mb.Context(M, k, precision="fp64", refine=args.refine) as c64:
+    with mb.Context(M, k, precision="fp64", refine=args.refine, variant=args.variant) as c64:
         c64.blocks(ij, outs=outs, width=args.together or 1)  # untimed: plans and workspace
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -714,7 +716,8 @@ def main():
     dt = torch.float64 if (args.precision in ("fp64", "fp64_tc") or args.refine) else torch.float32
     M = torch.tensor(m_host, dtype=dt, device="cuda")
     stream = torch.cuda.current_stream()
-    ctx = mb.Context(M, k, precision=args.precision, profile=True, slices=args.slices, refine=args.refine)
+    ctx = mb.Context(M, k, precision=args.precision, profile=True, slices=args.slices, refine=args.refine,
+                     variant=args.variant)
     outs = [torch.empty((b, b), dtype=dt, device="cuda") for _ in range(bps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     # each rank takes its own share of the block sequence (replicas, no collective)
@@ -781,8 +784,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(args), "data": "synthetic",
             "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, "
-                                   + (f"{args.together} runs executed together" if args.together
-                                      else "blocks one at a time") + f" ({args.precision})",
+                                   + (f"{args.together} runs merged" if args.together
+                                      else "blocks one at a time") + f" ({args.precision}"
+                                   + (", principal-Schur variant" if args.variant == "principal" else "") + ")",
                        "blocks_per_step": bps, "precision": args.precision, "slices": args.slices,
                        "refine": args.refine,
                        "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",
@@ -803,7 +807,8 @@ def main():
         t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 2))
         for s in range(e2e_steps):
-            with mb.Context(mh, k, precision=args.precision, slices=args.slices, refine=args.refine) as hc:
+            with mb.Context(mh, k, precision=args.precision, slices=args.slices, refine=args.refine,
+                            variant=args.variant) as hc:
                 ij = block_list(k, s * bps, bps)
                 if args.together:
                     hc.blocks(ij, outs=houts, width=args.together)

@@ -90,6 +90,25 @@ typedef enum { MBINV_FP64 = 0, MBINV_FP32 = 1, MBINV_MIXED_BF16 = 2, MBINV_FP64_
  *                           (MBINV_ENOTSUP). */
 typedef enum { MBINV_SCHEDULE_AUTO = 0, MBINV_SCHEDULE_LEVELS = 1, MBINV_SCHEDULE_BOUNDED = 2 } mbinv_schedule;
 
+/* The method.
+ *   MBINV_VARIANT_PAPER      the paper's recursion (Sec. 3): frames of non-
+ *                            principal submatrices reduced by their roles'
+ *                            Schur complements, memoized and merged.
+ *   MBINV_VARIANT_PRINCIPAL  the reformulation around the Schur complement
+ *                            M/A of Eq. SchurofA that the paper names as
+ *                            future work (Sec. 8): the blocks other than i
+ *                            and j are eliminated in ascending order with
+ *                            principal pivots S[c][c] (S the running Schur
+ *                            complement), then N_ii = S_ii^-1, or for i != j
+ *                            N_ij = -S_ii^-1 S_ij (S_jj - S_ji S_ii^-1 S_ij)^-1.
+ *                            Principal pivots keep the stability of block
+ *                            elimination (and exist wherever the principal
+ *                            minors do); the work is about (2/3) k^3 b^3 per
+ *                            block.  M on the device, k dividing n, no
+ *                            MBINV_MIXED_BF16, blocks returned in the working
+ *                            type; else MBINV_ENOTSUP. */
+typedef enum { MBINV_VARIANT_PAPER = 0, MBINV_VARIANT_PRINCIPAL = 1 } mbinv_variant;
+
 typedef struct {
     size_t struct_size;         /* sizeof(mbinv_options) */
     mbinv_precision precision;
@@ -116,13 +135,15 @@ typedef struct {
                                    candidate is at most sing_tol times the
                                    matrix's largest magnitude; 0 = b times
                                    the unit roundoff of the working type */
+    int variant;                /* an mbinv_variant: the paper's recursion
+                                   or the principal-Schur variant */
     int no_graphs;              /* 1: never replay a CUDA graph.  0: a call
                                    whose launch sequence equals the previous
                                    call's on this context (same blocks,
                                    buffers and schedule; not profiled; no
                                    host copies) is captured into a graph
                                    the second time and replayed after */
-    int reserved[3];
+    int reserved[2];
 } mbinv_options;
 
 typedef struct {

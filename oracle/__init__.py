@@ -18,6 +18,7 @@ plain definitions the tests compare against:
                          of the inverse.
 * ``refine_block``       N_ij <- X_i E_j + (E_i^T - X_i M) Y_j.
 * ``adjoint``            dL/dM = -(M^-T)[:, rows i] G (M^-T)[cols j, :].
+* ``principal_block``    N_ij by the principal-Schur-complement variant.
 """
 from __future__ import annotations
 
@@ -217,6 +218,44 @@ def adjoint(minv, g, i: int, j: int, b: int) -> np.ndarray:
     x_row = minv[i * b:(i + 1) * b, :]
     y_col = minv[:, j * b:(j + 1) * b]
     return -(x_row.T @ _f64(g) @ y_col.T)
+
+
+def principal_block(m, k: int, i: int, j: int):
+    """N_ij by the principal-Schur-complement variant (the reformulation
+    around M/A, Eq. SchurofA, that Sec. 8 names as future work): the blocks
+    other than i and j are eliminated in ascending order,
+        S[r][q] <- S[r][q] - S[r][c] (S[c][c]^-1 S[c][q]),
+    each pivot S[c][c] a principal Schur complement; then N_ii = S_ii^-1, or
+    N_ij = -(S_ii^-1 S_ij) (S_jj - S_ji S_ii^-1 S_ij)^-1 for i != j.  Products
+    and inverses are the oracle's own (plain loops, Gauss-Jordan).  Returns
+    (N_ij, status)."""
+    m = _f64(m)
+    n = m.shape[0]
+    assert n % k == 0
+    b = n // k
+    S = {(r, q): m[r * b:(r + 1) * b, q * b:(q + 1) * b].copy() for r in range(k) for q in range(k)}
+    order = [x for x in range(k) if x not in (i, j)]
+    alive = order + ([i] if i == j else [i, j])
+    for t, c in enumerate(order):
+        p, st = gj_inverse(S[c, c])
+        if st:
+            return None, st
+        rest = alive[t + 1:]
+        z = {q: matmul(p, S[c, q]) for q in rest}
+        for r in rest:
+            for q in rest:
+                S[r, q] = S[r, q] - matmul(S[r, c], z[q])
+    pi, st = gj_inverse(S[i, i])
+    if st:
+        return None, st
+    if i == j:
+        return pi, OK
+    z = matmul(pi, S[i, j])
+    t_ = S[j, j] - matmul(S[j, i], z)
+    ti, st = gj_inverse(t_)
+    if st:
+        return None, st
+    return -matmul(z, ti), OK
 
 
 def rel_fro(a, ref) -> float:

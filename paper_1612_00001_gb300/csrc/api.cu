@@ -416,16 +416,99 @@ int fit_group(mbinv_ctx* c, const std::vector<Req>& v, int want) {
   return 1;
 }
 
+// The principal-Schur variant (Sec. 8's reformulation around M/A): each
+// request its own schedule (the eliminated sets differ between blocks), the
+// schedules of a group - all of one shape - executed together, step t of
+// every request in the same grouped launches.
+const Schedule* psc_plan(mbinv_ctx* c, int64_t i, int64_t j) {
+  auto key = std::vector<std::pair<int, int>>{{(int)i, (int)j}, {-1, -1}};  // marks the variant
+  auto it = c->plans.find(key);
+  if (it == c->plans.end()) {
+    Schedule S = build_psc_schedule((int)c->k, (int)i, (int)j);
+    S.inv_chunk = 1;
+    S.planned = run_bytes(c, S, 1);
+    if (c->plans.size() > 256) c->plans.clear();
+    it = c->plans.emplace(key, std::make_pair(Plan{}, std::move(S))).first;
+  }
+  return &it->second.second;
+}
+
+int fit_group_psc(mbinv_ctx* c, const std::vector<Req>& v, int want) {
+  const size_t cap = c->opt.device_cap_bytes;
+  if (!cap) return want;
+  const size_t per = psc_plan(c, v[0].i, v[0].j)->planned;
+  const size_t base = base_bytes(c);
+  int G = want;
+  while (G > 1 && base + (size_t)G * per > cap) G /= 2;
+  return G;
+}
+
+mbinv_status run_group_psc(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report* rep) {
+  if (reqs.empty()) return MBINV_OK;
+  if (c->l > 0 || c->hM || c->gen || c->opt.precision == MBINV_MIXED_BF16) return MBINV_ENOTSUP;
+  const int G = (int)reqs.size();
+  std::vector<const Schedule*> sch(G);
+  for (int q = 0; q < G; ++q) sch[q] = psc_plan(c, reqs[q].i, reqs[q].j);
+  if (c->opt.device_cap_bytes && base_bytes(c) + (size_t)G * sch[0]->planned > c->opt.device_cap_bytes)
+    return MBINV_ENOMEM_CAP;
+  release_sweep(c);
+  const size_t planned = c->track.live + (size_t)G * sch[0]->planned;
+  const int prec = c->opt.precision;
+  const size_t sb = slot_bytes_for((int)c->b, prec);
+  size_t per = 0;
+  for (const Schedule* S : sch) per = std::max(per, (size_t)S->nslots * sb);
+  CU(c->slots.ensure(per * G + 256));
+  std::vector<Job> jobs(G);
+  for (int q = 0; q < G; ++q) {
+    Job& J = jobs[q];
+    J.dM = c->dM;
+    J.ldm = c->ldm;
+    J.mdt = c->mdt;
+    J.b = (int)c->b;
+    J.slots = (char*)c->slots.p + per * q;
+    J.slot_bytes = sb;
+    J.slot_dt = env_slot_type(prec);
+    J.out = reqs[q].dst;
+    J.ldo = reqs[q].ldd;
+    J.out_dt = c->odt;
+    J.S = sch[q];
+  }
+  c->env.stream = c->stream;
+  c->env.precision = prec;
+  c->env.slices = c->opt.bf16_slices;
+  c->env.profile = c->opt.profile != 0;
+  c->env.inv_chunk = G;
+  c->env.sing_tol = c->opt.sing_tol;
+  c->env.use_graphs = c->opt.no_graphs == 0;
+  const size_t replays0 = c->env.graph_replays;
+  mbinv_status s = run_jobs(c->env, jobs);
+  if (s == MBINV_ECUDA) last_cuda_error() = c->env.last_error;
+  if (rep) {
+    for (const Schedule* S : sch) add_report(rep, c, *S);
+    rep->launches += (size_t)c->env.launches;
+    rep->gemm_launches += (size_t)c->env.gemm_launches;
+    add_env_report(rep, c->env);
+    rep->planned_device_bytes = std::max(rep->planned_device_bytes, planned);
+    rep->max_pivot_cond = std::max(rep->max_pivot_cond, c->env.max_cond);
+    rep->graph_replays += c->env.graph_replays - replays0;
+    if (s == MBINV_ESINGULAR && rep->failed_pivot < 0) rep->failed_pivot = c->env.failed_inverse;
+  }
+  return s;
+}
+
 // Runs any list of requests: groups of at most `width` with one border each.
 mbinv_status run_requests(mbinv_ctx* c, const std::vector<Req>& reqs, int width, mbinv_report* rep) {
   std::map<int, std::vector<Req>> by_border;
-  for (const Req& r : reqs) by_border[border_of(c, r.i, r.j)].push_back(r);
+  const bool psc = c->opt.variant == MBINV_VARIANT_PRINCIPAL && c->k >= 2;
+  // the variant's diagonal and off-diagonal schedules have different shapes
+  for (const Req& r : reqs) by_border[border_of(c, r.i, r.j) + (psc && r.i == r.j ? 8 : 0)].push_back(r);
   for (auto& kv : by_border) {
     const std::vector<Req>& v = kv.second;
-    const int G = std::max(1, fit_group(c, v, std::min<int>(std::max(1, width), (int)v.size())));
+    const int want = std::min<int>(std::max(1, width), (int)v.size());
+    const int G = std::max(1, psc ? fit_group_psc(c, v, want) : fit_group(c, v, want));
     for (size_t q0 = 0; q0 < v.size(); q0 += G) {
       std::vector<Req> grp(v.begin() + q0, v.begin() + std::min(v.size(), q0 + G));
-      mbinv_status s = run_group(c, grp, rep);
+      mbinv_status s = psc ? run_group_psc(c, grp, rep) : run_group(c, grp, rep);
       if (s != MBINV_OK) return s;
     }
   }
@@ -891,7 +974,8 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   if (o.precision < MBINV_FP64 || o.precision > MBINV_FP64_TC) return MBINV_EINVAL;
   if (o.precision == MBINV_MIXED_BF16 && (o.bf16_slices < 1 || o.bf16_slices > 3)) return MBINV_EINVAL;
   if (o.refine_steps < 0 || o.refine_steps > 1) return MBINV_EINVAL;
-  if (o.out_dtype < 0 || o.out_dtype > 2 || o.schedule < 0 || o.schedule > 2 || !(o.sing_tol >= 0.0))
+  if (o.out_dtype < 0 || o.out_dtype > 2 || o.schedule < 0 || o.schedule > 2 || !(o.sing_tol >= 0.0) ||
+      o.variant < 0 || o.variant > 1)
     return MBINV_EINVAL;
   std::unique_ptr<mbinv_ctx> c(new (std::nothrow) mbinv_ctx);
   if (!c) return MBINV_EINVAL;

@@ -213,7 +213,8 @@ extern "C" int mbinv_debug_plan_group(int k, int count, const int* ij, int pad_l
 // pairs) on a k x k grid and runs it on scalars, b = 1: M is k x k row-major,
 // an inverse is 1/x, a product alpha A B + beta Cin, a copy moves a value.
 // mode 0: level by level; mode 1: bounded, in `slots` slots, M blocks read
-// from "host memory" when host_m.  outs[t] receives request t's result;
+// from "host memory" when host_m; mode 2: the principal-Schur variant (one
+// request).  outs[t] receives request t's result;
 // stats: steps, peak slots, host spill slots, loads, spills, inversions,
 // product units (b^3).  0; -1 for invalid arguments; -2 when the schedule
 // cannot be built in that many slots; -3 when a value is read before it is
@@ -230,7 +231,10 @@ extern "C" int mbinv_debug_run_schedule_scalar(int k, int count, const int* ij, 
     const Plan P = build_plan(k, reqs, false);
     Schedule S;
     if (mode == 0) S = build_schedule(P, 0);
-    else if (!build_bounded_schedule(P, slots, host_m != 0, &S)) return -2;
+    else if (mode == 2) {
+      if (count != 1) return -1;
+      S = build_psc_schedule(k, ij[0], ij[1]);
+    } else if (!build_bounded_schedule(P, slots, host_m != 0, &S)) return -2;
     const double nan = std::numeric_limits<double>::quiet_NaN();
     std::vector<double> sl((size_t)std::max(1, S.nslots), nan), sp((size_t)std::max(1, S.nspill), nan);
     std::vector<char> wsl(sl.size(), 0), wsp(sp.size(), 0);

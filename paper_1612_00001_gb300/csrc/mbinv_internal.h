@@ -116,6 +116,11 @@ Schedule build_schedule(const Plan& p, int zchunk);
 // when `slots` is too small for a single operation.
 bool build_bounded_schedule(const Plan& p, int slots, bool host_m, Schedule* out);
 
+// The principal-Schur-complement variant of block (i, j) (see plan.cpp): the
+// other blocks eliminated in ascending order with principal pivots, then the
+// 2 x 2 (or 1 x 1) remainder inverted.  One request; its output is OUT 0.
+Schedule build_psc_schedule(int k, int i, int j);
+
 // --------------------------------------------------------------- kernels
 struct GemmDesc {
   const void* A;
