@@ -569,7 +569,8 @@ def run_large(args, rank, world, dist):
     i, j = args.block
     stream = torch.cuda.current_stream()
     out = torch.empty((b, b), dtype=torch.float64, device="cuda")
-    ctx = mb.Context(mh, k, precision=args.precision, cap=cap, out_dtype=torch.float64, sing_tol=args.sing_tol)
+    ctx = mb.Context(mh, k, precision=args.precision, cap=cap, out_dtype=torch.float64, sing_tol=args.sing_tol,
+                     pivot_cond=True)
     for _ in range(args.warmup):
         ctx.block(i, j, out=out)
     clocks = _clock_region(0)

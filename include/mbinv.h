@@ -137,13 +137,16 @@ typedef struct {
                                    the unit roundoff of the working type */
     int variant;                /* an mbinv_variant: the paper's recursion
                                    or the principal-Schur variant */
+    int pivot_cond;             /* 1: estimate ||P||_1 ||P^-1||_1 of every
+                                   inverted pivot (reported as
+                                   max_pivot_cond; about 2% of a step) */
     int no_graphs;              /* 1: never replay a CUDA graph.  0: a call
                                    whose launch sequence equals the previous
                                    call's on this context (same blocks,
                                    buffers and schedule; not profiled; no
                                    host copies) is captured into a graph
                                    the second time and replayed after */
-    int reserved[2];
+    int reserved;
 } mbinv_options;
 
 typedef struct {
@@ -199,9 +202,9 @@ typedef struct {
                                    spilled values took at once */
     size_t graph_replays;       /* launch sequences replayed from a CUDA
                                    graph during the call */
-    double max_pivot_cond;      /* largest 1-norm condition estimate
-                                   ||P||_1 ||P^-1||_1 over the inverted
-                                   pivots (0 when not computed) */
+    double max_pivot_cond;      /* pivot_cond = 1: largest 1-norm condition
+                                   estimate ||P||_1 ||P^-1||_1 over the
+                                   inverted pivots (0 when not computed) */
 } mbinv_report;
 
 typedef struct mbinv_ctx mbinv_ctx;

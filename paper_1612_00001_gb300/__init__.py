@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("bf16_slices", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("pad_seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("out_dtype", ctypes.c_int), ("sing_tol", ctypes.c_double), ("variant", ctypes.c_int),
-                ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("pivot_cond", ctypes.c_int), ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -166,7 +166,7 @@ def _ptr(t) -> int:
 
 def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3, stream=None,
                  pad_seed: int = 0, profile: bool = False, schedule="auto", sing_tol: float = 0.0,
-                 out_dtype=None, graphs: bool = True, variant="paper") -> Options:
+                 out_dtype=None, graphs: bool = True, variant="paper", pivot_cond: bool = False) -> Options:
     o = Options()
     lib().mbinv_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -180,6 +180,7 @@ def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 
     o.sing_tol = float(sing_tol)
     o.no_graphs = 0 if graphs else 1
     o.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
+    o.pivot_cond = int(bool(pivot_cond))
     o.out_dtype = {None: 0, "float64": 1, "float32": 2}[None if out_dtype is None else str(out_dtype).split(".")[-1]]
     return o
 
@@ -192,7 +193,7 @@ class Context:
 
     def __init__(self, M, k: int, precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3,
                  pad_seed: int = 0, stream=None, profile: bool = False, schedule="auto", sing_tol: float = 0.0,
-                 out_dtype=None, graphs: bool = True, variant="paper"):
+                 out_dtype=None, graphs: bool = True, variant="paper", pivot_cond: bool = False):
         torch = _torch()
         if M.dim() != 2 or M.shape[0] != M.shape[1]:
             raise ValueError("M must be square")
@@ -209,7 +210,7 @@ class Context:
             stream = torch.cuda.current_stream(self.device).cuda_stream
         self.stream = stream
         self.opts = make_options(precision, cap, refine, slices, stream, pad_seed, profile, schedule, sing_tol,
-                                 out_dtype, graphs, variant)
+                                 out_dtype, graphs, variant, pivot_cond)
         h = ctypes.c_void_p()
         _check(lib().mbinv_create(ctypes.byref(h), self.n, self.k, _dtype_code(M), _ptr(M), M.stride(0),
                                   ctypes.byref(self.opts)), "mbinv_create")

@@ -14,6 +14,8 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -386,6 +388,7 @@ mbinv_status run_group(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_report*
   c->env.profile = c->opt.profile != 0;
   c->env.inv_chunk = std::max(1, S->inv_chunk);
   c->env.sing_tol = c->opt.sing_tol;
+  c->env.pivot_cond = c->opt.pivot_cond != 0;
   c->env.use_graphs = c->opt.no_graphs == 0;
   const size_t replays0 = c->env.graph_replays;
   s = run_jobs(c->env, {J});
@@ -479,6 +482,7 @@ mbinv_status run_group_psc(mbinv_ctx* c, const std::vector<Req>& reqs, mbinv_rep
   c->env.profile = c->opt.profile != 0;
   c->env.inv_chunk = G;
   c->env.sing_tol = c->opt.sing_tol;
+  c->env.pivot_cond = c->opt.pivot_cond != 0;
   c->env.use_graphs = c->opt.no_graphs == 0;
   const size_t replays0 = c->env.graph_replays;
   mbinv_status s = run_jobs(c->env, jobs);
@@ -1299,6 +1303,7 @@ static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void
         rep->rel_residual = res;
         rep->gemm_flops += 2.0 * (double)n * n * n;
       }
+      if (getenv("MBINV_TRACE_NS")) fprintf(stderr, "newton-schulz %d residual %.3e\n", it, res);
       if (!(res < 0.5 * last) || res < 1e-14) break;  // converged, or no longer contracting
       last = res;
       s = prod64(c, Nt, n, 0, E, n, 0, Nt, n, Nn, n, (int)n, (int)n, (int)n, 1.0, 1.0);
@@ -1488,6 +1493,7 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
   env.slices = o.bf16_slices;
   env.profile = o.profile != 0;
   env.sing_tol = o.sing_tol;
+  env.pivot_cond = o.pivot_cond != 0;
   env.use_graphs = false;  // every wave is a different launch sequence
   std::vector<int64_t> order;
   for (int64_t t = 0; t < count; ++t)

@@ -458,7 +458,7 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           d.b = J.b;
           d.tag = ninv_seen++;
           d.tol_rel = E.sing_tol;
-          d.cond = (unsigned long long*)E.condw.p;
+          d.cond = E.pivot_cond ? (unsigned long long*)E.condw.p : nullptr;
           d.flag = dflags + ops[u].first;
           bm = std::max(bm, J.b);
           double pf, uf;
@@ -782,8 +782,10 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           CUE(run_inverse_batch(l.in_dt, l.out_dt, wt, (const InvDesc*)(dbase + l.off), l.count, l.bmax,
                                 (DevStatus*)E.status.p, E.stream, &E.launches, ozk ? &itc : nullptr,
                                 E.profile ? &tm : nullptr));
-          CUE(launch_cond1((const InvDesc*)(dbase + l.off), l.count, l.in_dt, l.out_dt, E.stream));
-          ++E.launches;
+          if (E.pivot_cond) {
+            CUE(launch_cond1((const InvDesc*)(dbase + l.off), l.count, l.in_dt, l.out_dt, E.stream));
+            ++E.launches;
+          }
           pused += tm.n;
         }
           break;

@@ -127,6 +127,7 @@ struct Env {
   DevBuf stage;        // a block of a host matrix on its way to a slot of another type
   DevBuf condw;        // largest condition estimate of the run's inverses (bits of a double)
   double sing_tol = 0; // relative singularity threshold of the pivots (0 = b eps)
+  bool pivot_cond = false;  // estimate every inverted pivot's condition
   // CUDA graph of the last repeated launch sequence (see run_jobs)
   bool use_graphs = true;
   cudaStream_t cstream = nullptr;  // capture stream
