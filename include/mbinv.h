@@ -338,8 +338,9 @@ mbinv_status mbinv_block_col(mbinv_ctx *ctx, int64_t j, void *out, int64_t ldo, 
  * the tensor cores on FP64_TC), and with refine_steps = 1 every block of
  * M^-1 is first computed (runs merged) and that whole approximate inverse
  * N~ is improved by Newton-Schulz steps N~ <- N~ + N~ (I - M N~), each of
- * which squares ||I - M N~||, until that residual stops falling (at most 6;
- * its last value in rel_residual), X_i and Y_j then being its block row and
+ * which squares ||I - M N~|| (converging when it is below 1), until that
+ * residual stops falling (at most 12; the best N~ is kept and its residual
+ * reported in rel_residual), X_i and Y_j then being its block row and
  * column (3 n^2 doubles of device memory; M on the device, k dividing n,
  * else MBINV_ENOTSUP).  The paper has no gradient; this is the derivative of
  * its output. */

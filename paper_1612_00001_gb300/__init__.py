@@ -375,8 +375,8 @@ class _BlockInverse:
 
             class BlockInverse(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, M, k, i, j, precision, cap, refine):
-                    c = Context(M.detach(), k, precision=precision, cap=cap, refine=refine)
+                def forward(ctx, M, k, i, j, precision, cap, refine, variant):
+                    c = Context(M.detach(), k, precision=precision, cap=cap, refine=refine, variant=variant)
                     out = c.block(i, j)
                     ctx.mb = c
                     ctx.ij = (i, j)
@@ -387,15 +387,15 @@ class _BlockInverse:
                     c = ctx.mb
                     dM = c.backward(ctx.ij[0], ctx.ij[1], G.contiguous())
                     c.close()
-                    return dM, None, None, None, None, None, None
+                    return dM, None, None, None, None, None, None, None
 
             cls.fn = BlockInverse
         return cls.fn
 
 
-def block(M, k: int, i: int, j: int, precision="fp64", cap: int = 0, refine: int = 0):
+def block(M, k: int, i: int, j: int, precision="fp64", cap: int = 0, refine: int = 0, variant="paper"):
     """Differentiable N_ij of M^-1: the backward pass is the hand-written
     adjoint dM = -(X_i)^T G (Y_j)^T, with X_i and Y_j recomputed block by block
     (refine = 1: the forward block refined, and X_i, Y_j taken from the
     whole approximate inverse after Newton-Schulz steps)."""
-    return _BlockInverse.get().apply(M, k, i, j, precision, cap, refine)
+    return _BlockInverse.get().apply(M, k, i, j, precision, cap, refine, variant)

@@ -1277,8 +1277,9 @@ static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void
     if (s != MBINV_OK) return s;
     release_sweep(c);
     // Newton-Schulz on the whole approximate inverse: E = I - M N~,
-    // N~ <- N~ + N~ E, which squares ||E|| each time; until ||E||_F / sqrt(n)
-    // stops falling or is at the rounding level (at most 6 steps)
+    // N~ <- N~ + N~ E, which squares ||E|| each time (it converges when
+    // ||E|| < 1); until ||E||_F / sqrt(n) stops falling - the last better N~
+    // is kept - or is at the rounding level (at most 12 steps)
     CU(c->rowbuf.ensure((size_t)n * n * 8 + 256));
     CU(c->colbuf.ensure((size_t)n * n * 8 + 256));
     CU(c->resid.ensure(512));
@@ -1287,7 +1288,7 @@ static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void
     double* Nn = (double*)c->colbuf.p;
     double* acc = (double*)c->resid.p;
     double last = 1e300;
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 12; ++it) {
       s = prod64(c, (const double*)c->dM, c->ldm, 0, Nt, n, 0, nullptr, 0, E, n, (int)n, (int)n, (int)n, -1.0, 0.0);
       if (s != MBINV_OK) return s;
       add_eye_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(E, n, 0, n);
@@ -1304,7 +1305,12 @@ static mbinv_status backward_fp64(mbinv_ctx* c, int64_t i, int64_t j, const void
         rep->gemm_flops += 2.0 * (double)n * n * n;
       }
       if (getenv("MBINV_TRACE_NS")) fprintf(stderr, "newton-schulz %d residual %.3e\n", it, res);
-      if (!(res < 0.5 * last) || res < 1e-14) break;  // converged, or no longer contracting
+      if (!(res < last)) {  // no longer contracting: keep the previous, better N~
+        if (it > 0) std::swap(Nt, Nn);
+        if (rep) rep->rel_residual = last;
+        break;
+      }
+      if (res < 1e-14) break;
       last = res;
       s = prod64(c, Nt, n, 0, E, n, 0, Nt, n, Nn, n, (int)n, (int)n, (int)n, 1.0, 1.0);
       if (s != MBINV_OK) return s;

@@ -276,22 +276,25 @@ def test_merged_runs_bitwise_equal_runs_alone_with_padding(mb):
             assert np.array_equal(t, to_np(c1.block(i, j))), (i, j)
 
 
-def test_refined_adjoint_mid_size_spd(mb):
-    """n = 2048, k = 8 (b = 256), SPD M = Q diag(mu) Q^T with cond 1e3: the
-    adjoint with refined X_i, Y_j (Newton steps against the merged all-blocks
-    inverse) is within 1e-8 of the FP64 reference gradient -(M^-T) ... built
-    from a dense LAPACK inverse; unrefined it is much further (the paper's
-    order is unstable at k = 8)."""
+def test_adjoint_mid_size_spd(mb):
+    """n = 2048, k = 8 (b = 256), SPD M = Q diag(mu) Q^T with cond 1e3, against
+    the FP64 reference gradient built from a dense LAPACK inverse.  The
+    paper's order is unstable here (its block rows and columns carry about
+    5e-5 of error, and so does the gradient); Newton-Schulz refinement of the
+    whole approximate inverse cannot converge from that far (its residual
+    does not contract) and keeps the best iterate, which is no worse; the
+    principal-Schur variant, whose pivots are principal Schur complements of
+    an SPD matrix, gives the gradient within 1e-10."""
     n, k, i, j = 2048, 8, 1, 6
     b = n // k
     m = bi.spd(n, 1e3, 4)
     g = bi.gaussian_matrix(b, b, 6)
     ref = oracle.adjoint(np.linalg.inv(m), g, i, j, b)
     errs = {}
-    for refine in (0, 1):
+    for variant, refine in (("paper", 0), ("paper", 1), ("principal", 0)):
         M = dev(m).requires_grad_(True)
-        out = mb.block(M, k, i, j, precision=P, refine=refine)
+        out = mb.block(M, k, i, j, precision=P, refine=refine, variant=variant)
         (out * dev(g)).sum().backward()
-        errs[refine] = oracle.rel_fro(to_np(M.grad), ref)
-    assert errs[1] <= 1e-8, errs
-    assert errs[1] < errs[0], errs
+        errs[variant, refine] = oracle.rel_fro(to_np(M.grad), ref)
+    assert errs["paper", 1] <= errs["paper", 0], errs
+    assert errs["principal", 0] <= 1e-10, errs
