@@ -147,6 +147,9 @@ typedef struct {
                                    host copies) is captured into a graph
                                    the second time and replayed after */
     int reserved;
+    const char *tune_cache_path; /* file written by mbinv_autotune (may be
+                                   NULL): its tuned panel-cluster settings are
+                                   loaded when the context is created */
 } mbinv_options;
 
 typedef struct {
@@ -358,6 +361,21 @@ mbinv_status mbinv_batched_blocks(int64_t count, mbinv_problem *probs, int dtype
                                   mbinv_report *report);
 
 void mbinv_destroy(mbinv_ctx *ctx);
+
+/* Autotuner of the pivot inverses' panel factorisation (the leaf and level
+ * inverses of the recursion, Sec. 5 and 7): for count matrices of order b
+ * inverted together in `precision`, times the batched inversion of count
+ * synthetic matrices (uniform[-1, 1) + b I) with the panel's thread-block
+ * clusters scaled by 2^bias, bias = -2..2 around the built-in rule, keeps the
+ * fastest (it applies to every later batch of that order and size in the
+ * process) and appends "b count precision bias seconds" to cache_path (may be
+ * NULL), which a context reads back through tune_cache_path.  The cluster
+ * size changes where rows are eliminated, not how: results are bit for bit
+ * the same.  *best_bias and *best_seconds (either may be NULL) receive the
+ * choice and its device time per batch.  Allocates and frees its own
+ * scratch (count x b x b doubles and the inverses' workspace). */
+mbinv_status mbinv_autotune(int64_t b, int64_t count, int precision, const char *cache_path, int *best_bias,
+                            double *best_seconds);
 
 /* Largest order accepted by mbinv_invert_noalloc. */
 #define MBINV_NOALLOC_MAX_B 512

@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("bf16_slices", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("pad_seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("out_dtype", ctypes.c_int), ("sing_tol", ctypes.c_double), ("variant", ctypes.c_int),
-                ("pivot_cond", ctypes.c_int), ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("pivot_cond", ctypes.c_int), ("no_graphs", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("tune_cache_path", ctypes.c_void_p)]
 
 
 class Report(ctypes.Structure):
@@ -108,6 +109,8 @@ SIGNATURES = {
                                        ctypes.c_void_p]),
     "mbinv_invert_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]),
+    "mbinv_autotune": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_char_p,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "mbinv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mbinv_version": (ctypes.c_char_p, []),
     "mbinv_last_cuda_error": (ctypes.c_char_p, []),
@@ -166,7 +169,8 @@ def _ptr(t) -> int:
 
 def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3, stream=None,
                  pad_seed: int = 0, profile: bool = False, schedule="auto", sing_tol: float = 0.0,
-                 out_dtype=None, graphs: bool = True, variant="paper", pivot_cond: bool = False) -> Options:
+                 out_dtype=None, graphs: bool = True, variant="paper", pivot_cond: bool = False,
+                 tune_cache_path=None) -> Options:
     o = Options()
     lib().mbinv_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -181,6 +185,9 @@ def make_options(precision="fp64", cap: int = 0, refine: int = 0, slices: int = 
     o.no_graphs = 0 if graphs else 1
     o.variant = VARIANT[variant] if isinstance(variant, str) else int(variant)
     o.pivot_cond = int(bool(pivot_cond))
+    if tune_cache_path:
+        o._path = ctypes.create_string_buffer(str(tune_cache_path).encode())  # kept alive with the options
+        o.tune_cache_path = ctypes.cast(o._path, ctypes.c_void_p)
     o.out_dtype = {None: 0, "float64": 1, "float32": 2}[None if out_dtype is None else str(out_dtype).split(".")[-1]]
     return o
 
@@ -193,7 +200,8 @@ class Context:
 
     def __init__(self, M, k: int, precision="fp64", cap: int = 0, refine: int = 0, slices: int = 3,
                  pad_seed: int = 0, stream=None, profile: bool = False, schedule="auto", sing_tol: float = 0.0,
-                 out_dtype=None, graphs: bool = True, variant="paper", pivot_cond: bool = False):
+                 out_dtype=None, graphs: bool = True, variant="paper", pivot_cond: bool = False,
+                 tune_cache_path=None):
         torch = _torch()
         if M.dim() != 2 or M.shape[0] != M.shape[1]:
             raise ValueError("M must be square")
@@ -210,7 +218,7 @@ class Context:
             stream = torch.cuda.current_stream(self.device).cuda_stream
         self.stream = stream
         self.opts = make_options(precision, cap, refine, slices, stream, pad_seed, profile, schedule, sing_tol,
-                                 out_dtype, graphs, variant, pivot_cond)
+                                 out_dtype, graphs, variant, pivot_cond, tune_cache_path)
         h = ctypes.c_void_p()
         _check(lib().mbinv_create(ctypes.byref(h), self.n, self.k, _dtype_code(M), _ptr(M), M.stride(0),
                                   ctypes.byref(self.opts)), "mbinv_create")
@@ -335,6 +343,17 @@ class Context:
                "mbinv_backward")
         self.last_report = rep.as_dict()
         return dM
+
+
+def autotune(b: int, count: int, precision="fp64_tc", cache_path=None):
+    """Tunes the panel clusters of batched inverses of order b (see
+    mbinv_autotune); returns (bias, seconds per batch)."""
+    bias = ctypes.c_int()
+    secs = ctypes.c_double()
+    p = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().mbinv_autotune(int(b), int(count), p, cache_path.encode() if cache_path else None,
+                                ctypes.byref(bias), ctypes.byref(secs)), "mbinv_autotune")
+    return bias.value, secs.value
 
 
 def batched_blocks(problems, precision="fp64", cap: int = 0, stream=None):

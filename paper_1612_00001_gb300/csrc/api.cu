@@ -891,6 +891,32 @@ mbinv_status refined_blocks(mbinv_ctx* c, const std::vector<std::pair<int64_t, i
 
 }  // namespace
 
+// Synthetic matrices of the autotuner: uniform[-1, 1) (a SplitMix64 hash of
+// the element index) plus b on the diagonal.
+__global__ void tune_fill_kernel(double* a, int64_t count, int64_t b) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count * b * b) return;
+  const uint64_t u = sm64_mix(sm64_mix(0x7475ull) + (uint64_t)(e + 1) * 0x9E3779B97F4A7C15ull);
+  double v = 2.0 * ((double)(u >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+  const int64_t r = (e / b) % b, c = e % b;
+  if (r == c) v += (double)b;
+  a[e] = v;
+}
+
+// Applies the lines "b count precision bias seconds" of a cache file.
+void load_tune_cache(const char* path) {
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  long long b, count;
+  int prec, bias;
+  double secs;
+  while (fscanf(f, "%lld %lld %d %d %lf", &b, &count, &prec, &bias, &secs) == 5)
+    if (b > 0 && count > 0 && prec >= MBINV_FP64 && prec <= MBINV_FP64_TC && bias >= -3 && bias <= 3)
+      set_cluster_bias((int)b, (int)count, env_work_type(prec), prec == MBINV_FP64_TC, bias);
+  fclose(f);
+}
+
 // Nothing may be thrown across the C ABI: a failed host allocation or any
 // other exception inside a call becomes a status.
 template <typename F>
@@ -991,6 +1017,7 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
   c->dtype = dtype;
   c->odt = o.out_dtype == 1 ? F64 : (o.out_dtype == 2 ? F32 : dtype);
   c->opt = o;
+  load_tune_cache(o.tune_cache_path);
   c->track.cap = shared ? 0 : o.device_cap_bytes;
   MemTrack* tr = shared ? shared : &c->track;
   for (DevBuf* d : c->bufs()) d->track = tr;
@@ -1087,6 +1114,7 @@ static mbinv_status mbinv_create_from_fn_impl(mbinv_ctx** out, int64_t n, int64_
   c->dtype = dtype;
   c->odt = o.out_dtype == 1 ? F64 : (o.out_dtype == 2 ? F32 : dtype);
   c->opt = o;
+  load_tune_cache(o.tune_cache_path);
   c->track.cap = o.device_cap_bytes;
   for (DevBuf* d : c->bufs()) d->track = &c->track;
   c->stream = (cudaStream_t)o.cuda_stream;
@@ -1602,6 +1630,63 @@ static mbinv_status mbinv_batched_blocks_impl(int64_t count, mbinv_problem* prob
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return first;
+}
+
+static mbinv_status mbinv_autotune_impl(int64_t b, int64_t count, int precision, const char* path, int* best_bias,
+                                        double* best_seconds) {
+  if (b < 1 || count < 1 || count > (1 << 20) || precision < MBINV_FP64 || precision > MBINV_FP64_TC ||
+      precision == MBINV_MIXED_BF16)
+    return MBINV_EINVAL;
+  const int wt = env_work_type(precision);
+  const bool tc = precision == MBINV_FP64_TC;
+  DevBuf A, O;
+  const size_t bytes = (size_t)count * b * b * 8;
+  CU(A.ensure(bytes));
+  CU(O.ensure(bytes));
+  tune_fill_kernel<<<(unsigned)((count * b * b + 255) / 256), 256>>>((double*)A.p, count, b);
+  CU(cudaGetLastError());
+  CU(cudaDeviceSynchronize());
+  std::vector<mbinv_problem> probs((size_t)count);
+  for (int64_t t = 0; t < count; ++t)
+    probs[t] = mbinv_problem{b, 1, 0, 0, (double*)A.p + t * b * b, b, (double*)O.p + t * b * b, b, 0};
+  mbinv_options o;
+  mbinv_default_options(&o);
+  o.precision = (mbinv_precision)precision;
+  o.profile = 1;
+  int best = 0;
+  double best_t = 1e300;
+  for (int bias : {0, -1, 1, -2, 2}) {
+    set_cluster_bias((int)b, (int)count, wt, tc, bias);
+    double t = 0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+      mbinv_report r;
+      const mbinv_status s = mbinv_batched_blocks(count, probs.data(), F64, &o, &r);
+      if (s != MBINV_OK) {
+        set_cluster_bias((int)b, (int)count, wt, tc, 0);
+        return s;
+      }
+      t = r.inv_device_seconds;
+    }
+    if (t < best_t) {
+      best_t = t;
+      best = bias;
+    }
+  }
+  set_cluster_bias((int)b, (int)count, wt, tc, best);
+  if (path) {
+    FILE* f = fopen(path, "a");
+    if (!f) return MBINV_EINVAL;
+    fprintf(f, "%lld %lld %d %d %.9g\n", (long long)b, (long long)count, precision, best, best_t);
+    fclose(f);
+  }
+  if (best_bias) *best_bias = best;
+  if (best_seconds) *best_seconds = best_t;
+  return MBINV_OK;
+}
+
+mbinv_status mbinv_autotune(int64_t b, int64_t count, int precision, const char* path, int* best_bias,
+                            double* best_seconds) {
+  return guarded([&] { return mbinv_autotune_impl(b, count, precision, path, best_bias, best_seconds); });
 }
 
 mbinv_status mbinv_create(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,

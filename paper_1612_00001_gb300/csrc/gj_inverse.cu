@@ -27,6 +27,9 @@
 // the matrix singular through the status word; the elimination still runs to
 // the end so that no thread waits on another.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cfloat>
 
 #include "mbinv_internal.h"
@@ -481,6 +484,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   // eliminations: measured 18% less panel time than one 135 KB CTA per SM)
   // (m rows eliminated per matrix: b, or with tensor-core updates only the
   // b - p rows not yet used as pivots, so later panels take smaller clusters)
+  // a tuned bias (mbinv_autotune) scales the heuristic's choice by 2^bias
+  const int bias = cluster_bias(b, count, sizeof(TW) == 8 ? F64 : F32, tc != nullptr);
   auto cluster_for = [&](int m) {
     int CL = 8;
     while (CL > 1 && count * CL > 2 * 152) CL >>= 1;
@@ -488,6 +493,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     while (CL > 1 && count * (CL / 2) >= 152 && (m + CL / 2 - 1) / (CL / 2) * (nb + 1) * sizeof(TW) <= 64 * 1024)
       CL >>= 1;
     while (CL < 8 && ((size_t)((m + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > 72 * 1024) CL <<= 1;
+    for (int t = 0; t < bias && CL < 8; ++t) CL <<= 1;
+    for (int t = 0; t < -bias && CL > 1; ++t) CL >>= 1;
     while (CL < 8 && ((size_t)((m + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
     return CL;
   };
@@ -618,6 +625,27 @@ void inv_flop_split(int b, int wtype, bool tc, double* panel_flops, double* upda
   }
   *panel_flops = pf;
   *update_flops = uf;
+}
+
+namespace {
+std::mutex g_bias_mu;
+std::map<std::tuple<int, int, int, int>, int> g_bias;  // (b, count bucket, wtype, tc) -> bias
+int count_bucket(int count) {
+  int q = 1;
+  while (q < count) q <<= 1;
+  return q;
+}
+}  // namespace
+
+void set_cluster_bias(int b, int count, int wtype, bool tc, int bias) {
+  std::lock_guard<std::mutex> lock(g_bias_mu);
+  g_bias[std::make_tuple(b, count_bucket(count), wtype, (int)tc)] = bias;
+}
+
+int cluster_bias(int b, int count, int wtype, bool tc) {
+  std::lock_guard<std::mutex> lock(g_bias_mu);
+  auto it = g_bias.find(std::make_tuple(b, count_bucket(count), wtype, (int)tc));
+  return it == g_bias.end() ? 0 : it->second;
 }
 
 cudaError_t run_inverse_batch(int in_dtype, int out_dtype, int wtype, const InvDesc* d_desc, int count, int b,

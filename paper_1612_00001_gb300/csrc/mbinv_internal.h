@@ -193,6 +193,11 @@ struct InvTiming {
   int cap;
   int n;
 };
+// Tuned panel-cluster bias for inverse batches of count matrices of order b
+// (the cluster the heuristic picks is scaled by 2^bias, within the shared-
+// memory limit); 0 until set.  Thread safe.
+void set_cluster_bias(int b, int count, int wtype, bool tc, int bias);
+int cluster_bias(int b, int count, int wtype, bool tc);
 // Panel width and algorithmic flops of the panel factorisations and of the
 // trailing updates of one inverse of order b.
 void inv_flop_split(int b, int wtype, bool tc, double* panel_flops, double* update_flops);
