@@ -83,6 +83,9 @@ def parse():
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--batched", type=int, default=0,
                    help="batched workload: this many independent matrices of uneven n and k, one block each")
+    p.add_argument("--autotune", action="store_true",
+                   help="before the warm-up, tune the pivot inverses' panel clusters (mbinv_autotune) for the "
+                        "inverse batch sizes of the step (untimed)")
     p.add_argument("--peaks", action="store_true",
                    help="measure the FP64 and FP32 (no TF32) library GEMM rates that the FP64/FP32 rooflines "
                         "are read against: torch.matmul on 8192^3, best of 5, CUDA events")
@@ -638,7 +641,7 @@ def run_backward(args, rank, world, dist):
     M = torch.tensor(m, dtype=dt, device="cuda")
     W = torch.tensor(bi.gaussian_matrix(b, b, 0), dtype=dt, device="cuda")
     i, j = 1, k - 2
-    ctx = mb.Context(M, k, precision=args.precision, slices=args.slices, refine=args.refine)
+    ctx = mb.Context(M, k, precision=args.precision, slices=args.slices, refine=args.refine, variant=args.variant)
     dM = torch.zeros((n, n), dtype=dt, device="cuda")
 
     def step():
@@ -672,7 +675,8 @@ def run_backward(args, rank, world, dist):
             "dtype": dtype_name(args),
             "data": "synthetic",
             "config": {"workload": f"n={n} k={k} b={b} {matrix_name(args)}, L = sum(W * N_{i}{j}), "
-                                   f"forward + adjoint ({args.precision}, refine {args.refine})",
+                                   f"forward + adjoint ({args.precision}, refine {args.refine}"
+                                   + (", principal-Schur variant" if args.variant == "principal" else "") + ")",
                        "rel_err_forward_vs_dense": ferr, "rel_err_grad_vs_fp64_reference": gerr},
             "clocks": clk}
     if rank == 0:
@@ -734,6 +738,13 @@ def main():
             reps.append(c.last_report)
         return reps
 
+    tuned = None
+    if args.autotune:
+        # the step's inverse batches: the merged plan's pivots per level (powers
+        # of two bucket the batch sizes)
+        tuned = {}
+        for cnt in (1, 4, 8, 64, 128, 512, 1024):
+            tuned[cnt] = mb.autotune(b, cnt, args.precision)[0]
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
@@ -792,6 +803,7 @@ def main():
                        "refine": args.refine,
                        "l2": "M larger than L2 and a 256 MB L2 flush between timed steps",
                        "max_rel_err_vs_dense_inverse": max(errs),
+                       "autotuned_cluster_bias": tuned,
                        "frames_evaluated_per_step": agg["frames"] // args.steps,
                        "frames_of_the_runs_alone_per_step": agg["request_frames"] // args.steps},
             "fp64_path": fp64_arm,
