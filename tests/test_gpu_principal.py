@@ -62,19 +62,21 @@ def test_variant_haar_cond_1e4(mb):
     diagonal dominance, so its error is the block elimination's growth times
     cond times the unit roundoff: measured 3.4e-8 (FP64) and 4.2e-8 (FP64_TC)
     - asserted within 1e-6, four orders of magnitude below the paper's
-    order's error."""
+    order's error (asserted: at least 100 times smaller)."""
     n, k = 1024, 8
     b = n // k
     m = bi.haar_svd(n, 1e4, 3)
     inv = np.linalg.inv(m)
     ref = inv[2 * b:3 * b, 5 * b:6 * b]
+    errs = []
     for prec, bar in (("fp64_tc", 1e-6), ("fp64", 1e-6)):
         with mb.Context(dev(m), k, precision=prec, variant="principal") as ctx:
             got = to_np(ctx.block(2, 5))
-        assert oracle.rel_fro(got, ref) <= bar, prec
+        errs.append(oracle.rel_fro(got, ref))
+        assert errs[-1] <= bar, (prec, errs[-1])
     with mb.Context(dev(m), k, precision="fp64") as ctx:
         try:
             paper = to_np(ctx.block(2, 5))
-            assert oracle.rel_fro(paper, ref) > 1e-2
+            assert oracle.rel_fro(paper, ref) > 100 * max(errs)
         except mb.MbinvError as e:  # or it stops on a singular pivot
             assert e.status == mb.ESINGULAR
