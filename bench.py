@@ -83,9 +83,9 @@ def parse():
     p.add_argument("--kappa", type=float, default=1e4)
     p.add_argument("--batched", type=int, default=0,
                    help="batched workload: this many independent matrices of uneven n and k, one block each")
-    p.add_argument("--autotune", action="store_true",
-                   help="before the warm-up, tune the pivot inverses' panel clusters (mbinv_autotune) for the "
-                        "inverse batch sizes of the step (untimed)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="skip the tuning of the pivot inverses' panel clusters (mbinv_autotune) that runs, untimed, "
+                        "before the warm-up for the inverse batch sizes of the step")
     p.add_argument("--peaks", action="store_true",
                    help="measure the FP64 and FP32 (no TF32) library GEMM rates that the FP64/FP32 rooflines "
                         "are read against: torch.matmul on 8192^3, best of 5, CUDA events")
@@ -739,7 +739,7 @@ def main():
         return reps
 
     tuned = None
-    if args.autotune:
+    if not args.no_autotune and args.precision in ("fp64", "fp64_tc"):
         # the step's inverse batches: the merged plan's pivots per level (powers
         # of two bucket the batch sizes)
         tuned = {}
