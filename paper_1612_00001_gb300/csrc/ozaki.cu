@@ -38,9 +38,10 @@
 //                      once the epilogue has read the previous one out.
 //   warps 2-17:        epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..
 //                      (a row per thread) and one quarter of the columns,
-//                      combines the groups and writes beta * Cin + alpha * C,
-//                      16 contiguous entries per thread; Cin is fetched while
-//                      the MMAs run.
+//                      combines the groups into registers, hands TMEM back to
+//                      the MMA warp, then reads Cin and writes
+//                      beta * Cin + alpha * C (16 contiguous entries per
+//                      thread) while the next tile's MMAs run.
 // Every mbarrier wait is bounded (about two seconds of %globaltimer); a wait
 // that runs out raises the error word and the CTA drains, frees its TMEM and
 // returns.
@@ -138,13 +139,18 @@ __device__ __noinline__ double scale_rare(uint64_t mant, int e2, bool neg) {
   return neg ? -v : v;
 }
 
-// +-2^e * S with S = sum_g a_g 128^(7 - g) (|a_g| < 2^24, so |S| < 2^75),
-// rounded once to FP64 (ties to even), negated when neg_alpha; 64-bit integer
-// instructions only, the exponent field assembled directly.  S is carried as
-// H 2^28 + l with 0 <= l < 2^28, then as sign and magnitude Hm 2^28 + lm.
+// +-2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64 (ties to
+// even), negated when neg_alpha; integer instructions only, the exponent
+// field assembled directly.  Group g sums g + 1 digit pairs over at most 512
+// terms, so |a_g| <= (g + 1) 2^21 and |S| < 2^75.  S is carried as
+// H 2^28 + l with 0 <= l < 2^28, then as sign and magnitude Hm 2^28 + lm;
+// H and L are each one 32 x 32 -> 64-bit multiply-add of two 32-bit
+// Horner pairs (|a_{2t} 128 + a_{2t+1}| < 2^31 for every t by the bound).
 __device__ __forceinline__ double combine(const int (&a)[ND], int e, bool neg_alpha) {
-  long long H = (long long)a[0] * (1 << 21) + (long long)a[1] * (1 << 14) + (long long)a[2] * 128 + a[3];
-  const long long L = (long long)a[4] * (1 << 21) + (long long)a[5] * (1 << 14) + (long long)a[6] * 128 + a[7];
+  const int h0 = a[0] * 128 + a[1], h1 = a[2] * 128 + a[3];
+  const int l0 = a[4] * 128 + a[5], l1 = a[6] * 128 + a[7];
+  long long H = (long long)h0 * (1 << 14) + h1;
+  const long long L = (long long)l0 * (1 << 14) + l1;
   H += L >> 28;  // floor: the low part becomes the non-negative l
   const uint32_t l = (uint32_t)L & 0x0FFFFFFFu;
   const bool neg = H < 0;
@@ -336,8 +342,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w mod 4) ..
     // (one row of the tile per thread) and one quarter of the columns; it
     // combines the eight groups two columns at a time and writes each row's
-    // 16 entries (128 contiguous bytes per thread).  Cin is fetched before the
-    // tile's accumulators are complete.
+    // 16 entries (128 contiguous bytes per thread).  Cin is read after TMEM
+    // has been handed back, under the next tile's MMAs.
     const int q = warp & 3, c0 = 16 * ((warp - 2) >> 2);
     const bool neg_alpha = P.alpha < 0.0;  // alpha is +-1 and beta 0 or 1 (checked at launch)
     const bool use_cin = P.beta != 0.0;
@@ -353,10 +359,6 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int fcol = P.eb[(int64_t)pr.b_slab * P.eb_rows + col0 + (lane & 15)];  // lane % 16 = column
       const bool row_ok = grow < pr.m;
       const bool row_cin = use_cin && pr.cin && row_ok && (grow < pr.nocin_r0 || grow >= pr.nocin_r1);
-      double cpre[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c)
-        cpre[c] = (row_cin && col0 + c < pr.n) ? pr.cin[(int64_t)grow * pr.ldcin + col0 + c] : 0.0;
       const bool ok = mbar_wait(tfull, (uint32_t)it & 1u);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok || *(volatile int*)failed) {
@@ -366,30 +368,28 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
       double* orow = pr.out + (int64_t)grow * pr.ldo;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(pr.out) | (uintptr_t)(pr.ldo * 8)) & 15u) == 0;
       if (col0 >= pr.n) {  // columns past this problem (narrow updates): nothing to read
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty);
       } else {
-#pragma unroll
-        for (int cq = 0; cq < 16; cq += 2) {
-          uint32_t acc[ND][2];
+        // One column pair at a time: eight TMEM loads, then a wait that names
+        // the loaded registers (so nothing reads them early).  The combined
+        // products stay in registers; TMEM is released as soon as
+        // the last pair is read, so the Schur update's FP64 add and the
+        // stores (GB300's FP64 pipe is narrow) run under the next tile's MMAs.
+        auto load = [&](uint32_t (&acc)[ND][2], int cq) {
 #pragma unroll
           for (int gg = 0; gg < ND; ++gg) tmem_ld2_async(trow + 64 * gg + c0 + cq, acc[gg]);
-          tmem_wait();
-          if (cq == 14) {
-            // every accumulator of this tile has been read: the MMA warp may
-            // start the next tile
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty);
-          }
+        };
+        double vout[16];
+        auto comb = [&](const uint32_t (&acc)[ND][2], int cq) {
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const int c = cq + u;
             const int fj = __shfl_sync(0xffffffffu, fcol, c);
-            double v;
             if (ei >= kNonFinite || fj >= kNonFinite) {
-              v = __longlong_as_double(0x7FF8000000000000LL);
+              vout[c] = __longlong_as_double(0x7FF8000000000000LL);
             } else {
               int a[ND];
               if (small_k) {
@@ -402,11 +402,50 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
               }
-              v = combine(a, ei + fj - 61, neg_alpha);
+              vout[c] = combine(a, ei + fj - 61, neg_alpha);
             }
-            const int col = col0 + c;
-            // the one FP64 instruction per entry: the Schur update's add
-            if (row_ok && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1)) orow[col] = cpre[c] + v;
+          }
+        };
+        uint32_t acc[ND][2];
+#pragma unroll
+        for (int cq = 0; cq < 16; cq += 2) {
+          load(acc, cq);
+          tmem_wait_regs(acc);
+          comb(acc, cq);
+        }
+        // every accumulator of this tile has been read: the MMA warp may
+        // start the next tile
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty);
+        // the addend (fetched now, under the next tile's MMAs), the one FP64
+        // instruction per entry - the Schur update's add - and the stores:
+        // two columns per 16-byte access where both are used (col is even;
+        // rows start on 16 bytes when the base and leading dimension allow)
+        double cpre[16];
+        const double* crow = pr.cin + (int64_t)grow * pr.ldcin + col0;
+        if (row_cin && col0 + 16 <= pr.n && ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0)) {
+#pragma unroll
+          for (int c = 0; c < 16; c += 2) {
+            const double2 t = *reinterpret_cast<const double2*>(crow + c);
+            cpre[c] = t.x;
+            cpre[c + 1] = t.y;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) cpre[c] = (row_cin && col0 + c < pr.n) ? crow[c] : 0.0;
+        }
+#pragma unroll
+        for (int cq = 0; cq < 16; cq += 2) {
+          const int col = col0 + cq;
+          const double v0 = cpre[cq] + vout[cq], v1 = cpre[cq + 1] + vout[cq + 1];
+          const bool w0 = row_ok && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1);
+          const bool w1 = row_ok && col + 1 < pr.n && (col + 1 < pr.skip_c0 || col + 1 >= pr.skip_c1);
+          if (w0 && w1 && vec_ok) {
+            *reinterpret_cast<double2*>(orow + col) = make_double2(v0, v1);
+          } else {
+            if (w0) orow[col] = v0;
+            if (w1) orow[col + 1] = v1;
           }
         }
       }

@@ -129,6 +129,17 @@ __device__ __forceinline__ void tmem_ld2_async(uint32_t taddr, uint32_t (&r)[2])
 
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// The same wait, naming the sixteen registers the pending loads write: the
+// compiler then orders every later read of them after the wait.
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[8][2]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[2][0]), "+r"(r[2][1]),
+                 "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[4][0]), "+r"(r[4][1]), "+r"(r[5][0]), "+r"(r[5][1]),
+                 "+r"(r[6][0]), "+r"(r[6][1]), "+r"(r[7][0]), "+r"(r[7][1])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void split_bf16(float x, int S, __nv_bfloat16 (&s)[3]) {
   float r = x;
 #pragma unroll
