@@ -33,11 +33,12 @@ FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
 # panels of 512 rows x 64 columns read and wrote 99.4 MB for 1.258 GFLOP).
 # With 64 columns a panel's flops and its row traffic both grow with its rows.
 PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
-# The same for the FP64_TC trailing-update digit product (per FP64-equivalent
-# flop), from profiles/oz_gemm_kernel_trailing_update_b512_x300.md: one launch
-# updating 300 matrices of order 512 (panel of 64, 448 other columns) read
-# and wrote 1.274 GB for 8.81 GFLOP.
-UPDATE_DRAM_BYTES_PER_FLOP = 1.274e9 / (300 * 2 * 512 * 64 * 448)
+# The same for the FP64_TC pivot inverses' digit products (per FP64-equivalent
+# flop), from profiles/oz_gemm_kernel_trailing_update_b512_x300.md: the four
+# products of the first panel pair of 300 matrices of order 512 (two cross
+# products, the second panel's done rows, the K = 128 trailing update) read
+# and wrote 1.971 GB for the two panels' update work.
+UPDATE_DRAM_BYTES_PER_FLOP = 1.970924288e9 / (300 * (2 * 2 * 512 * 64 * 448 + 2 * 64 ** 3))
 # The same for the FP64_TC Schur products, from
 # profiles/oz_gemm_kernel_schur_products_n4096_k8_together4.md: two grouped
 # launches of 400 products of order 512 each (84 waves) read and wrote
@@ -67,6 +68,9 @@ def parse():
     p.add_argument("--no-fp64-check", action="store_true",
                    help="skip the plain FP64 arm (fp64_tc): its blocks/s on the same step and the distance of the "
                         "last step's first block to it")
+    p.add_argument("--products", type=int, default=0,
+                   help="time this many grouped FP64_TC products Cin - A B of order n <= 512 (the Schur products' "
+                        "kernels alone, through the library's product test hook) in one launch per step")
     p.add_argument("--inverses", type=int, default=0,
                    help="time this many independent pivoted inverses of order n (k = 1) in one batch")
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
@@ -518,6 +522,69 @@ def run_inverses(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_products(args, rank, world, dist):
+    """The Schur products' digit-product kernel alone: args.products
+    independent FP64 products out = Cin - A B of order n (A, B, Cin uniform
+    [-1, 1)), one grouped launch per step (the operands' digit packs
+    included), through the library's product test hook."""
+    import ctypes
+
+    import torch
+
+    import paper_1612_00001_gb300 as mb
+    n, cnt = args.n, args.products
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.rand((cnt, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+    B = torch.rand((cnt, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+    C = torch.rand((cnt, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+    out = torch.empty_like(C)
+    L = mb.lib()
+    L.mbinv_debug_oz_products_bytes.restype = ctypes.c_size_t
+    L.mbinv_debug_oz_products_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    f = L.mbinv_debug_oz_products
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] * 2 + [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    wsb = L.mbinv_debug_oz_products_bytes(n, cnt)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rc = f(A.data_ptr(), B.data_ptr(), C.data_ptr(), out.data_ptr(), n, cnt, ws.data_ptr(), wsb,
+               stream.cuda_stream)
+        assert rc == 0, rc
+
+    for _ in range(args.warmup):
+        step()
+    clocks = _clock_region(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        step()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
+    ref = C[0] - A[0] @ B[0]
+    err = float(torch.linalg.norm(out[0] - ref) / torch.linalg.norm(ref))
+    flops = 2.0 * n ** 3 * cnt * args.steps
+    pk, pk_src = peaks()
+    peak = pk["bf16_tflops_sustained"]
+    executed = DIGIT_PAIRS * flops / secs / 1e12
+    line = {"metric": "FP64 products/s (digit products on the BF16 tensor cores)", "value": cnt * args.steps / secs,
+            "unit": "products/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (exact bf16 digit products, f32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"{cnt} products Cin - A B of order {n}, uniform[-1,1) (fp64_tc), packs included",
+                       "tflops_fp64_equivalent": flops / secs / 1e12, "rel_err_vs_torch_fp64": err},
+            "roofline": {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
+                         "frac": executed / peak, "peak_source": f"bf16_tflops_sustained ({pk_src}), executed "
+                                                                 "BF16 digit-pair products (36 per FP64 product)"},
+            "gpu_launches": 4 * args.steps, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_peaks(args, rank):
     """FP64 and FP32 GEMM rates of the library (cuBLAS through torch.matmul,
     TF32 off) on 8192^3: the measured ceilings beside the nominal FP64 1.25
@@ -708,6 +775,8 @@ def main():
         return run_batched(args, rank, world, dist)
     if args.inverses:
         return run_inverses(args, rank, world, dist)
+    if args.products:
+        return run_products(args, rank, world, dist)
     if args.backward:
         return run_backward(args, rank, world, dist)
     if args.large:

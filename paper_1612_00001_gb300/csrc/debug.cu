@@ -286,3 +286,78 @@ extern "C" int mbinv_debug_run_schedule_scalar(int k, int count, const int* ij, 
 // memory.
 extern "C" void mbinv_debug_set_stall_ns(unsigned long long ns) { oz::set_debug_stall(ns); }
 extern "C" void mbinv_debug_fail_allocations(int n) { injected_alloc_failures() = n > 0 ? n : 0; }
+
+namespace {
+
+// Descriptors of count independent products out_g = Cin_g - A_g B_g (n x n,
+// row-major, consecutive in memory).
+__global__ void products_setup_kernel(const double* A, const double* B, const double* Cin, double* C, int n,
+                                      int count, oz::PackDesc* pd, oz::Problem* pr) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  const size_t off = (size_t)g * n * n;
+  pd[g] = oz::PackDesc{A + off, n, n, n, 0, g};
+  pd[count + g] = oz::PackDesc{B + off, n, n, n, 1, g};  // slab row = column of B
+  pr[g] = oz::Problem{g, g, Cin + off, n, C + off, n, n, n, 0, 0, 0, 0};
+}
+
+}  // namespace
+
+// Bytes of workspace mbinv_debug_oz_products needs for count products of
+// order n (n <= 512).
+extern "C" size_t mbinv_debug_oz_products_bytes(int n, int count) {
+  const int TM = oz::tile_m(), TN = oz::tile_n(), KT = oz::tile_k();
+  const size_t mpad = (n + TM - 1) / TM * TM, npad = (n + TN - 1) / TN * TN, kpad = (n + KT - 1) / KT * KT;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return al(count * oz::kDigits * mpad * kpad * 2) + al(count * oz::kDigits * npad * kpad * 2) +
+         al(count * mpad * 4) + al(count * npad * 4) + al(2 * count * sizeof(oz::PackDesc)) +
+         al(count * sizeof(oz::Problem)) + al(sizeof(int));
+}
+
+// count products out_g = Cin_g - A_g B_g of order n <= 512 (one K chunk) on
+// the FP64_TC digit-product kernels, in caller-given device workspace, with
+// no allocation and no synchronisation: a setup kernel, two packs and one
+// grouped product on the stream (the Schur products' kernels, timed alone).
+// 0, or nonzero for invalid arguments or a launch error.
+extern "C" int mbinv_debug_oz_products(const double* A, const double* B, const double* Cin, double* C, int n,
+                                       int count, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > 512 || count < 1 || !A || !B || !Cin || !C || !ws ||
+      ws_bytes < mbinv_debug_oz_products_bytes(n, count))
+    return 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int TM = oz::tile_m(), TN = oz::tile_n(), KT = oz::tile_k();
+  const int mpad = (n + TM - 1) / TM * TM, npad = (n + TN - 1) / TN * TN, kpad = (n + KT - 1) / KT * KT;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* p = (char*)ws;
+  auto* apk = (__nv_bfloat16*)p;
+  p += al((size_t)count * oz::kDigits * mpad * kpad * 2);
+  auto* bpk = (__nv_bfloat16*)p;
+  p += al((size_t)count * oz::kDigits * npad * kpad * 2);
+  int* ea = (int*)p;
+  p += al((size_t)count * mpad * 4);
+  int* eb = (int*)p;
+  p += al((size_t)count * npad * 4);
+  auto* pd = (oz::PackDesc*)p;
+  p += al(2 * (size_t)count * sizeof(oz::PackDesc));
+  auto* pr = (oz::Problem*)p;
+  p += al((size_t)count * sizeof(oz::Problem));
+  int* derr = (int*)p;
+  products_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(A, B, Cin, C, n, count, pd, pr);
+  if (cudaGetLastError() != cudaSuccess) return 2;
+  if (oz::launch_pack(pd, count, mpad, kpad, apk, ea, s) != cudaSuccess) return 3;
+  if (oz::launch_pack(pd + count, count, npad, kpad, bpk, eb, s) != cudaSuccess) return 4;
+  oz::Params P{};
+  P.kpad = kpad;
+  P.kb0 = 0;
+  P.nkb = kpad / KT;
+  P.tiles_m = mpad / TM;
+  P.tiles_n = npad / TN;
+  P.alpha = -1.0;
+  P.beta = 1.0;
+  P.ea = ea;
+  P.eb = eb;
+  P.ea_rows = mpad;
+  P.eb_rows = npad;
+  P.err = derr;
+  return oz::launch_gemm(apk, count, mpad, bpk, count, npad, P, pr, count, s) == cudaSuccess ? 0 : 5;
+}

@@ -18,7 +18,10 @@
 //      with the rows of J zeroed first - a rank-nb GEMM on the CUDA cores,
 //      or (FP64_TC) an exact digit product on the tensor cores (ozaki.cu):
 //      T[:, J] by rows and W by columns are digit-packed and one grouped
-//      product per panel forms the update in FP64.
+//      product forms the update in FP64.  On FP64_TC the update is delayed
+//      over two panels (K = 2 nb; the second panel's columns are brought up
+//      to date first, and the first panel's columns take the second panel's
+//      transform after it - two narrow products), see run_batch_t.
 // After the last panel the recorded row interchanges are undone as column
 // interchanges in reverse order while the result is written out.  For b at
 // most 128 the panel is the whole matrix and step 2 never runs.
@@ -390,6 +393,38 @@ __global__ void gj_tc_done_setup_kernel(const InvDesc* __restrict__ descs, int c
   pr[u] = q;
 }
 
+// Descriptors of a cross product inside a panel pair J1 = [p, p + nb),
+// J2 = [p + nb, p + 2 nb) (see run_batch_t): dir 0 brings the columns of J2
+// up to date with the transform of J1, X[:, J2] = T1 X[J1, J2] + X[:, J2];
+// dir 1 applies the transform of J2 to the columns of J1,
+// X[:, J1] = T2 X[J2, J1] + X[:, J1]; the transform's own pivot rows take no
+// addend.  A matrix without a second panel gets an empty problem.
+__global__ void gj_tc_cross_setup_kernel(const InvDesc* __restrict__ descs, int count, int p, int nb, int dir,
+                                         oz::PackDesc* __restrict__ pa, oz::PackDesc* __restrict__ pb,
+                                         oz::Problem* __restrict__ pr) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= count) return;
+  const InvDesc d = descs[u];
+  const int b = d.b;
+  const int w1 = max(0, min(nb, b - p)), w2 = max(0, min(nb, b - p - nb));
+  const bool live = w1 > 0 && w2 > 0;
+  const int ca = dir ? p + nb : p, wa = dir ? w2 : w1;  // the transform's columns (and pivot rows)
+  const int cc = dir ? p : p + nb, wc = dir ? w1 : w2;  // the columns brought up to date
+  double* X = (double*)d.work;
+  pa[u] = oz::PackDesc{X + (live ? ca : 0), b, live ? b : 0, live ? wa : 0, 0, u};
+  pb[u] = oz::PackDesc{X + (live ? (int64_t)ca * b + cc : 0), b, live ? wa : 0, live ? wc : 0, 1, u};
+  oz::Problem q{};
+  q.a_slab = q.b_slab = u;
+  q.cin = X + (live ? cc : 0);
+  q.out = X + (live ? cc : 0);
+  q.ldcin = q.ldo = b;
+  q.m = live ? b : 0;
+  q.n = live ? wc : 0;
+  q.nocin_r0 = live ? ca : 0;
+  q.nocin_r1 = live ? ca + wa : 0;
+  pr[u] = q;
+}
+
 struct TcLayout {
   int rpa, rpb, kpad;
   size_t da, db, ea, eb, pa, pb, pr, total;
@@ -400,9 +435,10 @@ TcLayout tc_layout(int bmax, int count) {
   TcLayout L;
   L.rpa = (bmax + oz::tile_m() - 1) / oz::tile_m() * oz::tile_m();
   L.rpb = (bmax + oz::tile_n() - 1) / oz::tile_n() * oz::tile_n();
-  // the inner length of the updates is the panel width
+  // the inner length of the widest update is two panel widths (updates
+  // delayed over panel pairs)
   const int nb = inv_panel_width(bmax, F64, true);
-  L.kpad = (std::min(nb, bmax) + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
+  L.kpad = (std::min(2 * nb, bmax) + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
   const size_t K = L.kpad;
   size_t o = 0;
   L.da = o;
@@ -508,9 +544,10 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     });
     if (e != cudaSuccess) return e;
   }
-  for (int p = 0; p < b; p += nb) {
-    const int w = std::min(nb, b - p);  // widest panel of this step (b is the largest order)
-    const int m = tc && w < b ? b - p : b;
+  // one panel factorisation [pp, pp + nb) of every matrix (event-timed when asked)
+  auto panel = [&](int pp) -> cudaError_t {
+    const int w = std::min(nb, b - pp);  // widest panel of this step (b is the largest order)
+    const int m = tc && w < b ? b - pp : b;
     const int CL = cluster_for(m);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * CL, 1, 1);
@@ -526,61 +563,97 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     cfg.numAttrs = 1;
     const bool timed = tm && tm->n + 2 <= tm->cap;
     if (timed) cudaEventRecord(tm->ev[tm->n], s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, p, w, d_status, tc && w < b ? 1 : 0);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, pp, w, d_status, tc && w < b ? 1 : 0);
     if (e != cudaSuccess) return e;
     if (timed) {
       cudaEventRecord(tm->ev[tm->n + 1], s);
       tm->n += 2;
     }
     ++nl;
-    if (w < b && tc) {  // the rows done before this panel, then the trailing update, on the tensor cores
-      const TcLayout T = tc_layout(b, count);
-      char* base = (char*)tc->scratch;
-      auto* pa = (oz::PackDesc*)(base + T.pa);
-      auto* pb = (oz::PackDesc*)(base + T.pb);
-      auto* pr = (oz::Problem*)(base + T.pr);
-      auto* da = (__nv_bfloat16*)(base + T.da);
-      auto* db = (__nv_bfloat16*)(base + T.db);
-      int* ea = (int*)(base + T.ea);
-      int* eb = (int*)(base + T.eb);
-      oz::Params Q{};
-      Q.kpad = T.kpad;
-      Q.kb0 = 0;
-      Q.nkb = T.kpad / oz::tile_k();  // at most kMaxKBlocks: panels are far narrower than 512
-      Q.ea = ea;
-      Q.eb = eb;
-      Q.ea_rows = T.rpa;
-      Q.eb_rows = T.rpb;
-      Q.err = tc->err;
-      Q.coprime_grid = 1;  // the skipped panel columns recur every tiles_n tiles
-      auto product = [&](double alpha, double beta, int tiles_m, int tiles_n) -> cudaError_t {
-        cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, T.kpad, da, ea, s);
-        if (e2 != cudaSuccess) return e2;
-        e2 = oz::launch_pack(pb, count, T.rpb, T.kpad, db, eb, s);
-        if (e2 != cudaSuccess) return e2;
-        Q.alpha = alpha;
-        Q.beta = beta;
-        Q.tiles_m = tiles_m;
-        Q.tiles_n = tiles_n;
-        nl += 3;
-        return oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
-      };
-      if (p > 0) {
-        gj_tc_done_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
-        ++nl;
-        // p x w outputs per matrix: the tile grid of the largest
-        if ((e = product(-1.0, 0.0, (p + oz::tile_m() - 1) / oz::tile_m(), (w + oz::tile_n() - 1) / oz::tile_n())) !=
-            cudaSuccess)
-          return e;
+    return cudaSuccess;
+  };
+  cudaError_t e;
+  if (tc && nb < b) {
+    // Tensor-core updates, delayed over panel pairs J1 = [p, p + nb),
+    // J2 = [p + nb, p + 2 nb): the columns outside J = J1 u J2 receive one
+    // rank-2nb update (K = 128) instead of two rank-nb ones, which halves the
+    // per-entry epilogues of the widest products.  The panel columns carry
+    // the composite transform first:
+    //   panel J1; rows done before J1 (product); X[:, J2] += T1 X[J1, J2];
+    //   panel J2; rows done before J2 (product); X[:, J1] += T2 X[J2, J1];
+    //   X[:, rest] += X[:, J] X[J, rest]
+    // (each "+=" with the rows of the transform's own pivots taking no
+    // addend), which is the sequence of single-panel updates regrouped: the
+    // pivot rows X[J, rest] are untouched (only exchanged) until the last one.
+    const TcLayout T = tc_layout(b, count);
+    char* base = (char*)tc->scratch;
+    auto* pa = (oz::PackDesc*)(base + T.pa);
+    auto* pb = (oz::PackDesc*)(base + T.pb);
+    auto* pr = (oz::Problem*)(base + T.pr);
+    auto* da = (__nv_bfloat16*)(base + T.da);
+    auto* db = (__nv_bfloat16*)(base + T.db);
+    int* ea = (int*)(base + T.ea);
+    int* eb = (int*)(base + T.eb);
+    oz::Params Q{};
+    Q.kb0 = 0;
+    Q.ea = ea;
+    Q.eb = eb;
+    Q.ea_rows = T.rpa;
+    Q.eb_rows = T.rpb;
+    Q.err = tc->err;
+    Q.coprime_grid = 1;  // the skipped panel columns recur every tiles_n tiles
+    // one grouped digit product over K = kpad (a multiple of 64, at most T.kpad)
+    auto product = [&](int kpad, double alpha, double beta, int tiles_m, int tiles_n) -> cudaError_t {
+      cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, kpad, da, ea, s);
+      if (e2 != cudaSuccess) return e2;
+      e2 = oz::launch_pack(pb, count, T.rpb, kpad, db, eb, s);
+      if (e2 != cudaSuccess) return e2;
+      Q.kpad = kpad;
+      Q.nkb = kpad / oz::tile_k();
+      Q.alpha = alpha;
+      Q.beta = beta;
+      Q.tiles_m = tiles_m;
+      Q.tiles_n = tiles_n;
+      nl += 3;
+      return oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
+    };
+    const int k1 = (nb + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
+    const int g = (count + 127) / 128;
+    // rows [0, pp) of the panel [pp, pp + nb): p x nb outputs per matrix
+    auto done = [&](int pp) -> cudaError_t {
+      if (pp == 0) return cudaSuccess;
+      gj_tc_done_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, pp, nb, pa, pb, pr);
+      ++nl;
+      return product(k1, -1.0, 0.0, (pp + oz::tile_m() - 1) / oz::tile_m(), (nb + oz::tile_n() - 1) / oz::tile_n());
+    };
+    auto cross = [&](int pp, int dir) -> cudaError_t {
+      gj_tc_cross_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, pp, nb, dir, pa, pb, pr);
+      ++nl;
+      return product(k1, 1.0, 1.0, T.rpa / oz::tile_m(), (nb + oz::tile_n() - 1) / oz::tile_n());
+    };
+    for (int p = 0; p < b; p += 2 * nb) {
+      if ((e = panel(p)) != cudaSuccess) return e;
+      if ((e = done(p)) != cudaSuccess) return e;
+      if (p + nb < b) {
+        if ((e = cross(p, 0)) != cudaSuccess) return e;
+        if ((e = panel(p + nb)) != cudaSuccess) return e;
+        if ((e = done(p + nb)) != cudaSuccess) return e;
+        if ((e = cross(p, 1)) != cudaSuccess) return e;
       }
-      gj_tc_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_desc, count, p, w, pa, pb, pr);
+      gj_tc_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, p, 2 * nb, pa, pb, pr);
       ++nl;
-      if ((e = product(1.0, 1.0, T.rpa / oz::tile_m(), T.rpb / oz::tile_n())) != cudaSuccess) return e;
-    } else if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
-      using Cfg = TileCfg<TW>;
-      dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);
-      gj_update_kernel<TW><<<g, 256, 0, s>>>(d_desc, p, w);
-      ++nl;
+      if ((e = product(T.kpad, 1.0, 1.0, T.rpa / oz::tile_m(), T.rpb / oz::tile_n())) != cudaSuccess) return e;
+    }
+  } else {
+    for (int p = 0; p < b; p += nb) {
+      if ((e = panel(p)) != cudaSuccess) return e;
+      const int w = std::min(nb, b - p);
+      if (w < b) {  // matrices whose panel is not the whole matrix need the trailing update
+        using Cfg = TileCfg<TW>;
+        dim3 g((b + Cfg::BN - 1) / Cfg::BN, (b + Cfg::BM - 1) / Cfg::BM, count);
+        gj_update_kernel<TW><<<g, 256, 0, s>>>(d_desc, p, w);
+        ++nl;
+      }
     }
   }
   {

@@ -139,38 +139,61 @@ __device__ __noinline__ double scale_rare(uint64_t mant, int e2, bool neg) {
   return neg ? -v : v;
 }
 
+// r += b for 96-bit two's-complement integers held as three 32-bit limbs
+// (one carry chain).
+__device__ __forceinline__ void add96(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t b0, uint32_t b1,
+                                      uint32_t b2) {
+  asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+      : "+r"(r0), "+r"(r1), "+r"(r2)
+      : "r"(b0), "r"(b1), "r"(b2));
+}
+
 // +-2^e * S with S = sum_g a_g 128^(7 - g), rounded once to FP64 (ties to
-// even), negated when neg_alpha; integer instructions only, the exponent
-// field assembled directly.  Group g sums g + 1 digit pairs over at most 512
-// terms, so |a_g| <= (g + 1) 2^21 and |S| < 2^75.  S is carried as
-// H 2^28 + l with 0 <= l < 2^28, then as sign and magnitude Hm 2^28 + lm;
-// H and L are each one 32 x 32 -> 64-bit multiply-add of two 32-bit
-// Horner pairs (|a_{2t} 128 + a_{2t+1}| < 2^31 for every t by the bound).
+// even), negated when neg_alpha; 32-bit integer instructions only (carry
+// chains in place of 64-bit arithmetic), the exponent field assembled
+// directly.  Group g sums g + 1 digit pairs over at most 512 terms, so
+// |a_g| <= (g + 1) 2^21 and |S| < 2^75.  With the Horner pairs
+// h0 = a_0 128 + a_1, h1, l0, l1 (each below 2^31 in magnitude by that bound)
+//     S = h0 2^42 + h1 2^28 + l0 2^14 + l1,
+// summed as a 96-bit integer in three 32-bit limbs, then taken to sign and
+// magnitude, whose leading 53 bits are rounded with the bits below them.
 __device__ __forceinline__ double combine(const int (&a)[ND], int e, bool neg_alpha) {
   const int h0 = a[0] * 128 + a[1], h1 = a[2] * 128 + a[3];
   const int l0 = a[4] * 128 + a[5], l1 = a[6] * 128 + a[7];
-  long long H = (long long)h0 * (1 << 14) + h1;
-  const long long L = (long long)l0 * (1 << 14) + l1;
-  H += L >> 28;  // floor: the low part becomes the non-negative l
-  const uint32_t l = (uint32_t)L & 0x0FFFFFFFu;
-  const bool neg = H < 0;
-  // -(H 2^28 + l) = (-H - 1) 2^28 + (2^28 - l) when l > 0
-  const uint64_t Hm = neg ? (uint64_t)(-H) - (l != 0u ? 1u : 0u) : (uint64_t)H;
-  const uint32_t lm = (neg && l != 0u) ? (1u << 28) - l : l;
-  if ((Hm | lm) == 0) return 0.0;
-  const int top = Hm ? 91 - __clzll((long long)Hm) : 31 - __clz((int)lm);  // leading bit of |S|, <= 74
-  const int sh = top > 52 ? top - 52 : 0;                                  // bits rounded off, <= 22
-  uint64_t mant = (Hm << (28 - sh)) | (uint64_t)(lm >> sh);                // floor(|S| / 2^sh)
-  const uint32_t rmask = (1u << sh) - 1u, rem = lm & rmask, half = (rmask >> 1) + 1u;
-  mant += (rem > half || (rem == half && (mant & 1u))) ? 1u : 0u;
-  mant <<= (sh ? 0 : 52 - top);  // leading bit to 52 (53 after a carry out of the rounding)
-  const bool neg_out = neg != neg_alpha;
-  const int e2 = top + e;        // value = mant 2^(e2 - 52)
-  const int e2n = e2 + (int)(mant >> 53);
-  if (e2n < -1022 || e2n > 1023) return scale_rare(mant, e2, neg_out);
-  // a carry out of the rounding leaves mant = 2^53, whose low 52 bits are zero
-  return __longlong_as_double((long long)(((uint64_t)neg_out << 63) | ((uint64_t)(e2n + 1023) << 52) |
-                                          (mant & 0xFFFFFFFFFFFFFull)));
+  uint32_t s0 = (uint32_t)l1, s1 = (uint32_t)(l1 >> 31), s2 = s1;
+  add96(s0, s1, s2, (uint32_t)l0 << 14, (uint32_t)(l0 >> 18), (uint32_t)(l0 >> 31));
+  add96(s0, s1, s2, (uint32_t)h1 << 28, (uint32_t)(h1 >> 4), (uint32_t)(h1 >> 31));
+  add96(s0, s1, s2, 0u, (uint32_t)h0 << 10, (uint32_t)(h0 >> 22));
+  const uint32_t sg = (uint32_t)((int)s2 >> 31);  // all ones when S < 0
+  uint32_t m0 = s0 ^ sg, m1 = s1 ^ sg, m2 = s2 ^ sg;
+  add96(m0, m1, m2, sg & 1u, 0u, 0u);  // |S|
+  if ((m0 | m1 | m2) == 0u) return 0.0;
+  const int top = m2 ? 95 - __clz((int)m2) : (m1 ? 63 - __clz((int)m1) : 31 - __clz((int)m0));  // <= 74
+  uint32_t mh, ml;  // the significand, leading bit at bit 52 of mh:ml (bit 53 after a carry)
+  if (top <= 52) {  // exact: shift up
+    const int k = 52 - top;
+    if (k >= 32) {
+      mh = m0 << (k - 32);
+      ml = 0u;
+    } else {
+      mh = __funnelshift_l(m0, m1, k);
+      ml = m0 << k;
+    }
+  } else {  // sh = top - 52 <= 22 bits rounded off
+    const int sh = top - 52;
+    ml = __funnelshift_r(m0, m1, sh);
+    mh = __funnelshift_r(m1, m2, sh);
+    const uint32_t rem = m0 & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    const uint32_t up = (rem > half || (rem == half && (ml & 1u))) ? 1u : 0u;
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(ml), "+r"(mh) : "r"(up));
+  }
+  const bool neg_out = (sg != 0u) != neg_alpha;
+  const int e2 = top + e;  // value = mant 2^(e2 - 52)
+  const int e2n = e2 + (int)(mh >> 21);
+  if (e2n < -1022 || e2n > 1023) return scale_rare(((uint64_t)mh << 32) | ml, e2, neg_out);
+  // a carry out of the rounding leaves 2^53, whose low 52 bits are zero
+  const uint32_t hi = ((uint32_t)neg_out << 31) | ((uint32_t)(e2n + 1023) << 20) | (mh & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)ml);
 }
 
 // Decodes grid tile t: problem g, row tile tm, column tile tn; false when the
@@ -341,13 +364,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w mod 4) ..
     // (one row of the tile per thread) and one quarter of the columns; it
-    // combines the eight groups two columns at a time and writes each row's
+    // combines the eight groups four columns at a time and writes each row's
     // 16 entries (128 contiguous bytes per thread).  Cin is read after TMEM
     // has been handed back, under the next tile's MMAs.
     const int q = warp & 3, c0 = 16 * ((warp - 2) >> 2);
     const bool neg_alpha = P.alpha < 0.0;  // alpha is +-1 and beta 0 or 1 (checked at launch)
     const bool use_cin = P.beta != 0.0;
-    const bool small_k = P.nkb == 1;  // one K block of 64
+    const bool small_k = P.nkb <= 2;  // K <= 128: every group sum within 2^22
     int it = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
       int g, tm, tn;
@@ -359,6 +382,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int fcol = P.eb[(int64_t)pr.b_slab * P.eb_rows + col0 + (lane & 15)];  // lane % 16 = column
       const bool row_ok = grow < pr.m;
       const bool row_cin = use_cin && pr.cin && row_ok && (grow < pr.nocin_r0 || grow >= pr.nocin_r1);
+      const double* crow = row_cin ? pr.cin + (int64_t)grow * pr.ldcin + col0 : nullptr;
+      if (row_cin && col0 < pr.n) {
+        // the row's 16 addends (one or two 128-byte lines) into L2 while the
+        // MMAs run; they are read after TMEM has been handed back
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(crow));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + 15));
+      }
       const bool ok = mbar_wait(tfull, (uint32_t)it & 1u);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok || *(volatile int*)failed) {
@@ -373,19 +403,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty);
       } else {
-        // One column pair at a time: eight TMEM loads, then a wait that names
+        // Four columns at a time: eight TMEM loads, then a wait that names
         // the loaded registers (so nothing reads them early).  The combined
-        // products stay in registers; TMEM is released as soon as
-        // the last pair is read, so the Schur update's FP64 add and the
-        // stores (GB300's FP64 pipe is narrow) run under the next tile's MMAs.
-        auto load = [&](uint32_t (&acc)[ND][2], int cq) {
-#pragma unroll
-          for (int gg = 0; gg < ND; ++gg) tmem_ld2_async(trow + 64 * gg + c0 + cq, acc[gg]);
-        };
+        // products stay in registers; TMEM is released as soon as the last
+        // columns are read, so the Schur update's add and the stores run
+        // under the next tile's MMAs.
         double vout[16];
-        auto comb = [&](const uint32_t (&acc)[ND][2], int cq) {
+        uint32_t acc[ND][4];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+        for (int cq = 0; cq < 16; cq += 4) {
+#pragma unroll
+          for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
+          tmem_wait_regs(acc);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
             const int c = cq + u;
             const int fj = __shfl_sync(0xffffffffu, fcol, c);
             if (ei >= kNonFinite || fj >= kNonFinite) {
@@ -393,8 +424,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             } else {
               int a[ND];
               if (small_k) {
-                // |G_g| <= 8 * 64 * 2^12 = 2^21: adding 1.5 * 2^23 puts the
-                // integer in the low mantissa bits (an FP32 add, not a conversion)
+                // |G_g| <= 8 * 128 * 2^12 = 2^22: adding 1.5 * 2^23 gives an
+                // FP32 in [2^23, 2^24] whose bit pattern less that of 1.5 * 2^23
+                // is the integer (an FP32 add, not a conversion; at 2^24 the
+                // pattern difference is still exactly 2^22)
 #pragma unroll
                 for (int gg = 0; gg < ND; ++gg)
                   a[gg] = __float_as_int(__uint_as_float(acc[gg][u]) + 12582912.0f) - 0x4B400000;
@@ -405,25 +438,17 @@ __global__ void __launch_bounds__(THREADS, 1)
               vout[c] = combine(a, ei + fj - 61, neg_alpha);
             }
           }
-        };
-        uint32_t acc[ND][2];
-#pragma unroll
-        for (int cq = 0; cq < 16; cq += 2) {
-          load(acc, cq);
-          tmem_wait_regs(acc);
-          comb(acc, cq);
         }
         // every accumulator of this tile has been read: the MMA warp may
         // start the next tile
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty);
-        // the addend (fetched now, under the next tile's MMAs), the one FP64
-        // instruction per entry - the Schur update's add - and the stores:
-        // two columns per 16-byte access where both are used (col is even;
-        // rows start on 16 bytes when the base and leading dimension allow)
+        // the addends (from L2), the one FP64 instruction per entry - the
+        // Schur update's add - and the stores: two columns per 16-byte access
+        // where both are used (col is even; rows start on 16 bytes when the
+        // base and leading dimension allow)
         double cpre[16];
-        const double* crow = pr.cin + (int64_t)grow * pr.ldcin + col0;
         if (row_cin && col0 + 16 <= pr.n && ((reinterpret_cast<uintptr_t>(crow) & 15u) == 0)) {
 #pragma unroll
           for (int c = 0; c < 16; c += 2) {
