@@ -40,10 +40,11 @@ PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
 # and wrote 1.971 GB for the two panels' update work.
 UPDATE_DRAM_BYTES_PER_FLOP = 1.970924288e9 / (300 * (2 * 2 * 512 * 64 * 448 + 2 * 64 ** 3))
 # The same for the FP64_TC Schur products, from
-# profiles/oz_gemm_kernel_schur_products_n4096_k8_together4.md: two grouped
-# launches of 400 products of order 512 each (84 waves) read and wrote
-# 1.936 GB and 4.033 GB - the algorithmic bytes of their distinct operands.
-SCHUR_DRAM_BYTES_PER_FLOP = (1.128e9 + 0.808e9 + 3.206e9 + 0.827e9) / (800 * 2 * 512 ** 3)
+# profiles/oz_gemm_kernel_schur_products_n512_x200.md: one grouped launch of
+# 200 independent products of order 512 (42 waves) read and wrote 2.512 GB -
+# the algorithmic bytes of its operands; an upper bound for the recursion's
+# launches, whose products share operands.
+SCHUR_DRAM_BYTES_PER_FLOP = (2.109816832e9 + 0.402289152e9) / (200 * 2 * 512 ** 3)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
 
