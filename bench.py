@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--inverses", type=int, default=0,
                    help="time this many independent pivoted inverses of order n (k = 1) in one batch")
     p.add_argument("--cpu-sample-blocks", type=int, default=1)
+    p.add_argument("--cpu-threads", type=int, default=0,
+                   help="host threads of the CPU oracle (cpu_baseline and the reference arm); 0 = all cores")
     p.add_argument("--slices", type=int, default=3)
     p.add_argument("--refine", type=int, default=None,
                    help="two-sided refinement steps (0 or 1); default 1 on fp64_tc and fp64, where it meets the "
@@ -382,10 +384,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_time(m, k, blocks):
-    """Seconds per block of the oracle (memoized recursion, all host cores)."""
+def cpu_oracle_time(m, k, blocks, threads=0):
+    """Seconds per block of the oracle (memoized recursion; all host cores, or
+    `threads` of them)."""
     import oracle
     oracle.build()
+    if threads > 0:
+        oracle.set_num_threads(threads)
     t0 = time.perf_counter()
     for (i, j) in blocks:
         _, st, _ = oracle.bri_block(m, k, i, j, memo=True)
@@ -402,10 +407,10 @@ def run_reference(args, rank):
     k = args.k
     seq = block_list(k, 0, args.warmup + args.steps)
     for t in range(args.warmup):
-        cpu_oracle_time(m, k, [seq[t]])
+        cpu_oracle_time(m, k, [seq[t]], args.cpu_threads)
     per = []
     for t in range(args.steps):
-        s, cores = cpu_oracle_time(m, k, [seq[args.warmup + t]])
+        s, cores = cpu_oracle_time(m, k, [seq[args.warmup + t]], args.cpu_threads)
         per.append(s)
     secs = sum(per)
     value = args.steps / secs
@@ -544,44 +549,54 @@ def run_products(args, rank, world, dist):
     L.mbinv_debug_oz_products_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
     f = L.mbinv_debug_oz_products
     f.restype = ctypes.c_int
-    f.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] * 2 + [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    f.argtypes = ([ctypes.c_void_p] * 4 + [ctypes.c_int] * 2 + [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                                                 ctypes.c_void_p])
     wsb = L.mbinv_debug_oz_products_bytes(n, cnt)
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        rc = f(A.data_ptr(), B.data_ptr(), C.data_ptr(), out.data_ptr(), n, cnt, ws.data_ptr(), wsb,
+    def step(pack):
+        rc = f(A.data_ptr(), B.data_ptr(), C.data_ptr(), out.data_ptr(), n, cnt, ws.data_ptr(), wsb, pack,
                stream.cuda_stream)
         assert rc == 0, rc
 
     for _ in range(args.warmup):
-        step()
+        step(1)
     clocks = _clock_region(0)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        ev[s][0].record(stream)
-        step()
-        ev[s][1].record(stream)
-    torch.cuda.synchronize()
+
+    def timed(pack):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            ev[s][0].record(stream)
+            step(pack)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(z) for a, z in ev) / 1e3
+
+    secs = timed(1)
+    secs_gemm = timed(0)  # the product launch alone (operands > L2: 200 x 8 MB of digits)
     clk = clocks.stop()
-    secs = sum(a.elapsed_time(z) for a, z in ev) / 1e3
     ref = C[0] - A[0] @ B[0]
     err = float(torch.linalg.norm(out[0] - ref) / torch.linalg.norm(ref))
     flops = 2.0 * n ** 3 * cnt * args.steps
     pk, pk_src = peaks()
     peak = pk["bf16_tflops_sustained"]
-    executed = DIGIT_PAIRS * flops / secs / 1e12
+    executed = DIGIT_PAIRS * flops / secs_gemm / 1e12
     line = {"metric": "FP64 products/s (digit products on the BF16 tensor cores)", "value": cnt * args.steps / secs,
             "unit": "products/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (exact bf16 digit products, f32 accumulate)", "data": "synthetic",
             "config": {"workload": f"{cnt} products Cin - A B of order {n}, uniform[-1,1) (fp64_tc), packs included",
-                       "tflops_fp64_equivalent": flops / secs / 1e12, "rel_err_vs_torch_fp64": err},
-            "roofline": {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
-                         "frac": executed / peak, "peak_source": f"bf16_tflops_sustained ({pk_src}), executed "
-                                                                 "BF16 digit-pair products (36 per FP64 product)"},
-            "gpu_launches": 4 * args.steps, "clocks": clk}
+                       "tflops_fp64_equivalent": flops / secs / 1e12, "rel_err_vs_torch_fp64": err,
+                       "product_launch_ms": 1e3 * secs_gemm / args.steps,
+                       "l2": "operands larger than L2 (digits 8 MB per product)"},
+            "roofline": {"bound": "tensor", "kernel": "oz_gemm_kernel", "achieved": executed, "peak": peak,
+                         "unit": "TFLOP/s", "frac": executed / peak, "device_seconds": secs_gemm,
+                         "traffic": SCHUR_DRAM_BYTES_PER_FLOP * 2.0 * n ** 3 * cnt,
+                         "peak_source": f"bf16_tflops_sustained ({pk_src}), executed BF16 digit-pair products "
+                                        "(36 per FP64 product), the product launch alone"},
+            "gpu_launches": 5 * args.steps, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -886,25 +901,35 @@ def main():
     if not args.no_e2e and rank == 0:
         mh = torch.tensor(m_host, dtype=dt).pin_memory()
         houts = [torch.empty((b, b), dtype=dt).pin_memory() for _ in range(bps)]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_steps = max(1, min(args.steps, 2))
-        for s in range(e2e_steps):
-            with mb.Context(mh, k, precision=args.precision, slices=args.slices, refine=args.refine,
-                            variant=args.variant) as hc:
+        e2e_steps = max(1, min(args.steps, 3))
+        # one context for the stream of matrices (created, planned and warmed
+        # up once); every timed step re-reads M from pinned host memory
+        # (mbinv_reload: the H2D copy) and returns its blocks to pinned host
+        # memory (the D2H copies)
+        with mb.Context(mh, k, precision=args.precision, slices=args.slices, refine=args.refine,
+                        variant=args.variant) as hc:
+            def e2e_step(s):
+                hc.reload()
                 ij = block_list(k, s * bps, bps)
                 if args.together:
                     hc.blocks(ij, outs=houts, width=args.together)
                 else:
                     for q, (i, j) in enumerate(ij):
                         hc.block(i, j, out=houts[q])
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+            e2e_step(0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in range(e2e_steps):
+                e2e_step(s)
+            torch.cuda.synchronize()
+            te = time.perf_counter() - t0
         es = dt.itemsize if hasattr(dt, "itemsize") else (8 if dt == torch.float64 else 4)
         line["e2e"] = {"value": e2e_steps * bps / te, "unit": "blocks/s", "h2d_bytes_per_step": n * n * es,
-                       "d2h_bytes_per_step": bps * b * b * es, "steps": e2e_steps}
+                       "d2h_bytes_per_step": bps * b * b * es, "steps": e2e_steps,
+                       "timing": "host wall clock; one context created and warmed up before the timed steps, "
+                                 "each step mbinv_reload (H2D of M) + mbinv_blocks (D2H of the blocks)"}
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        secs_cpu, cores = cpu_oracle_time(m_host, k, block_list(k, 0, args.cpu_sample_blocks))
+        secs_cpu, cores = cpu_oracle_time(m_host, k, block_list(k, 0, args.cpu_sample_blocks), args.cpu_threads)
         line["cpu_baseline"] = {"value": 1.0 / secs_cpu, "unit": "blocks/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_sample_blocks} block(s) from (0,0) of the same matrix, "
                                           "memoized recursion, FP64"}

@@ -270,6 +270,18 @@ void mbinv_default_options(mbinv_options *opt);
 mbinv_status mbinv_create(mbinv_ctx **out, int64_t n, int64_t k, int dtype, const void *M, int64_t ld,
                           const mbinv_options *opt);
 
+/* Re-reads M after the caller changed its contents (same buffer, shape and
+ * dtype as given to mbinv_create): the next problem of a stream of matrices
+ * of one shape, without a new context (its plans, workspace and captured
+ * launch graphs stay).  A context that copied M to the device (host M; device
+ * M that is padded or converted) copies it again on the context's stream and
+ * returns when the copy is complete; a context that reads the caller's
+ * buffer in place (device M of the sweep's type, host-resident M of the
+ * bounded schedule) or produces M has nothing to refresh and returns
+ * MBINV_OK.  The caller's buffer must be valid for the call; with host
+ * memory it is free to change again once the call returns. */
+mbinv_status mbinv_reload(mbinv_ctx *ctx);
+
 /* A context whose M (n x n, type dtype) is produced on demand by fn and
  * never stored: every block the recursion reads is written by fn into a
  * device value slot just before its use, under the bounded schedule (depth

@@ -101,6 +101,7 @@ SIGNATURES = {
     "mbinv_batched_blocks": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Problem), ctypes.c_int,
                                             ctypes.POINTER(Options), ctypes.POINTER(Report)]),
     "mbinv_destroy": (None, [ctypes.c_void_p]),
+    "mbinv_reload": (ctypes.c_int, [ctypes.c_void_p]),
     "mbinv_create_from_fn": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(Options)]),
@@ -253,6 +254,16 @@ class Context:
         self._h = h
         self.last_report = None
         return self
+
+    def reload(self, M=None):
+        """Re-reads M after its contents changed (the next matrix of a stream
+        of one shape).  M: optionally new contents, copied into the tensor
+        given at construction first (same shape and dtype)."""
+        if M is not None:
+            if getattr(self, "M", None) is None:
+                raise ValueError("this context produces M; there is nothing to reload")
+            self.M.copy_(M)
+        _check(lib().mbinv_reload(self._h), "mbinv_reload")
 
     def extent(self, t: int) -> int:
         return self.n - (self.k - 1) * self.b if t == self.k - 1 else self.b

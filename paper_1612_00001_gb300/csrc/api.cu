@@ -129,6 +129,9 @@ struct mbinv_ctx {
   mbinv_block_fn gen = nullptr;  // produced M (bounded schedule): never stored
   void* gen_user = nullptr;
   HostBuf spill;             // pinned host slots of the values a bounded run spills
+  const void* srcM = nullptr;  // the caller's M as given to create (borrowed), its ld and space
+  int64_t srcld = 0;
+  bool srcdev = false;
   DevBuf own_M;
   int border_mode = -1;
   DevBuf slots, outtmp, rowbuf, colbuf, resid, gbuf, wbuf, dmbuf, gemmdesc;
@@ -988,6 +991,57 @@ const char* mbinv_version(void) { return "mbinv 0.2 (sm_103a)"; }
 
 const char* mbinv_last_cuda_error(void) { return cudaGetErrorString(last_cuda_error()); }
 
+// Copies the caller's M (c->srcM) into the context's own device matrix,
+// converting it to the sweep's element type where they differ, and writes the
+// padded corner (identity) and border strips.  On c->stream; returns once the
+// copy is complete (the caller may then change its buffer).
+static mbinv_status upload_m(mbinv_ctx* c, MemTrack* tr) {
+  const int64_t n = c->n;
+  const int dtype = c->dtype;
+  const size_t es = dtype_size(dtype), mes = dtype_size(c->mdt);
+  const void* M = c->srcM;
+  const int64_t ld = c->srcld;
+  const bool dev = c->srcdev;
+  if (c->mdt == dtype) {
+    CU(cudaMemcpy2DAsync(c->own_M.p, (size_t)c->npad * mes, M, (size_t)ld * es, (size_t)n * es, (size_t)n,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  } else {
+    // stage the caller's matrix on the device, then convert it
+    DevBuf stage;
+    stage.track = tr;
+    CU(stage.ensure((size_t)n * n * es));
+    CU(cudaMemcpy2DAsync(stage.p, (size_t)n * es, M, (size_t)ld * es, (size_t)n * es, (size_t)n,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    const int64_t nel = n * n;
+    const int blocks = (int)((nel + 255) / 256);
+    if (dtype == F64)
+      convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double*)stage.p, n, (float*)c->own_M.p,
+                                                                    c->npad, n, n);
+    else
+      convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float*)stage.p, n, (double*)c->own_M.p,
+                                                                    c->npad, n, n);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    stage.release();
+  }
+  if (c->l) {
+    // identity in the padded corner; the border strips are written per request
+    std::vector<char> eye((size_t)c->l * c->npad * mes, 0);
+    for (int64_t q = 0; q < c->l; ++q) {
+      if (c->mdt == F64) ((double*)eye.data())[q * c->npad + n + q] = 1.0;
+      else ((float*)eye.data())[q * c->npad + n + q] = 1.0f;
+    }
+    CU(cudaMemcpyAsync((char*)c->own_M.p + (size_t)n * c->npad * mes, eye.data(), eye.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->border_mode = -1;
+    mbinv_status s = set_border(c, 0);
+    if (s != MBINV_OK) return s;
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  return MBINV_OK;
+}
+
 // shared: the tracker of a batched call, whose contexts count their bytes
 // together (no cap of their own); null for an ordinary context.
 static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int dtype, const void* M, int64_t ld,
@@ -1048,41 +1102,11 @@ static mbinv_status mbinv_create_impl(mbinv_ctx** out, int64_t n, int64_t k, int
     CU(c->own_M.ensure(mbytes));
     c->dM = c->own_M.p;
     c->ldm = c->npad;
-    if (c->mdt == dtype) {
-      CU(cudaMemcpy2DAsync(c->own_M.p, (size_t)c->npad * mes, M, (size_t)ld * es, (size_t)n * es, (size_t)n,
-                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    } else {
-      // stage the caller's matrix on the device, then convert it
-      DevBuf stage;
-      stage.track = tr;
-      CU(stage.ensure((size_t)n * n * es));
-      CU(cudaMemcpy2DAsync(stage.p, (size_t)n * es, M, (size_t)ld * es, (size_t)n * es, (size_t)n,
-                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-      const int64_t nel = n * n;
-      const int blocks = (int)((nel + 255) / 256);
-      if (dtype == F64)
-        convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double*)stage.p, n, (float*)c->own_M.p,
-                                                                      c->npad, n, n);
-      else
-        convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float*)stage.p, n, (double*)c->own_M.p,
-                                                                      c->npad, n, n);
-      CU(cudaGetLastError());
-      CU(cudaStreamSynchronize(c->stream));
-      stage.release();
-    }
-    if (c->l) {
-      // identity in the padded corner; the border strips are written per request
-      std::vector<char> eye((size_t)c->l * c->npad * mes, 0);
-      for (int64_t q = 0; q < c->l; ++q) {
-        if (c->mdt == F64) ((double*)eye.data())[q * c->npad + n + q] = 1.0;
-        else ((float*)eye.data())[q * c->npad + n + q] = 1.0f;
-      }
-      CU(cudaMemcpyAsync((char*)c->own_M.p + (size_t)n * c->npad * mes, eye.data(), eye.size(),
-                         cudaMemcpyHostToDevice, c->stream));
-      CU(cudaStreamSynchronize(c->stream));
-      mbinv_status s = set_border(c.get(), 0);
-      if (s != MBINV_OK) return s;
-    }
+    c->srcM = M;
+    c->srcld = ld;
+    c->srcdev = dev;
+    mbinv_status s = upload_m(c.get(), tr);
+    if (s != MBINV_OK) return s;
     CU(cudaStreamSynchronize(c->stream));
   }
   *out = c.release();
@@ -1696,6 +1720,15 @@ mbinv_status mbinv_create(mbinv_ctx** out, int64_t n, int64_t k, int dtype, cons
 mbinv_status mbinv_create_from_fn(mbinv_ctx** out, int64_t n, int64_t k, int dtype, mbinv_block_fn fn, void* user,
                                   const mbinv_options* opt) {
   return guarded([&] { return mbinv_create_from_fn_impl(out, n, k, dtype, fn, user, opt); });
+}
+mbinv_status mbinv_reload(mbinv_ctx* c) {
+  return on_context(c, nullptr, [&]() -> mbinv_status {
+    // a context that copied M re-reads it; one that reads the caller's
+    // buffer in place (device M, host-resident M) or produces M has nothing
+    // to refresh
+    if (!c->own_M.p || !c->srcM) return MBINV_OK;
+    return upload_m(c, c->own_M.track);
+  });
 }
 mbinv_status mbinv_block(mbinv_ctx* c, int64_t i, int64_t j, void* out, int64_t ldo, mbinv_report* rep) {
   return on_context(c, rep, [&] { return mbinv_block_impl(c, i, j, out, ldo, rep); });

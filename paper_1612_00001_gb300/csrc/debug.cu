@@ -318,9 +318,11 @@ extern "C" size_t mbinv_debug_oz_products_bytes(int n, int count) {
 // the FP64_TC digit-product kernels, in caller-given device workspace, with
 // no allocation and no synchronisation: a setup kernel, two packs and one
 // grouped product on the stream (the Schur products' kernels, timed alone).
-// 0, or nonzero for invalid arguments or a launch error.
+// pack = 0 launches the product alone, on the digits an earlier call with
+// the same operands and workspace left there.  0, or nonzero for invalid
+// arguments or a launch error.
 extern "C" int mbinv_debug_oz_products(const double* A, const double* B, const double* Cin, double* C, int n,
-                                       int count, void* ws, size_t ws_bytes, void* stream) {
+                                       int count, void* ws, size_t ws_bytes, int pack, void* stream) {
   if (n < 1 || n > 512 || count < 1 || !A || !B || !Cin || !C || !ws ||
       ws_bytes < mbinv_debug_oz_products_bytes(n, count))
     return 1;
@@ -342,10 +344,12 @@ extern "C" int mbinv_debug_oz_products(const double* A, const double* B, const d
   auto* pr = (oz::Problem*)p;
   p += al((size_t)count * sizeof(oz::Problem));
   int* derr = (int*)p;
-  products_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(A, B, Cin, C, n, count, pd, pr);
-  if (cudaGetLastError() != cudaSuccess) return 2;
-  if (oz::launch_pack(pd, count, mpad, kpad, apk, ea, s) != cudaSuccess) return 3;
-  if (oz::launch_pack(pd + count, count, npad, kpad, bpk, eb, s) != cudaSuccess) return 4;
+  if (pack) {
+    products_setup_kernel<<<(count + 127) / 128, 128, 0, s>>>(A, B, Cin, C, n, count, pd, pr);
+    if (cudaGetLastError() != cudaSuccess) return 2;
+    if (oz::launch_pack(pd, count, mpad, kpad, apk, ea, s) != cudaSuccess) return 3;
+    if (oz::launch_pack(pd + count, count, npad, kpad, bpk, eb, s) != cudaSuccess) return 4;
+  }
   oz::Params P{};
   P.kpad = kpad;
   P.kb0 = 0;
