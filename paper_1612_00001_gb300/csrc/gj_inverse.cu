@@ -19,9 +19,10 @@
 //      or (FP64_TC) an exact digit product on the tensor cores (ozaki.cu):
 //      T[:, J] by rows and W by columns are digit-packed and one grouped
 //      product forms the update in FP64.  On FP64_TC the update is delayed
-//      over two panels (K = 2 nb; the second panel's columns are brought up
-//      to date first, and the first panel's columns take the second panel's
-//      transform after it - two narrow products), see run_batch_t.
+//      over blocks of two panels (K = 2 nb; each panel's columns are brought
+//      up to date with the earlier panels of its block before it, and the
+//      earlier panels' columns take its transform after it - narrow
+//      products), see run_batch_t.
 // After the last panel the recorded row interchanges are undone as column
 // interchanges in reverse order while the result is written out.  For b at
 // most 128 the panel is the whole matrix and step 2 never runs.
@@ -393,23 +394,27 @@ __global__ void gj_tc_done_setup_kernel(const InvDesc* __restrict__ descs, int c
   pr[u] = q;
 }
 
-// Descriptors of a cross product inside a panel pair J1 = [p, p + nb),
-// J2 = [p + nb, p + 2 nb) (see run_batch_t): dir 0 brings the columns of J2
-// up to date with the transform of J1, X[:, J2] = T1 X[J1, J2] + X[:, J2];
-// dir 1 applies the transform of J2 to the columns of J1,
-// X[:, J1] = T2 X[J2, J1] + X[:, J1]; the transform's own pivot rows take no
-// addend.  A matrix without a second panel gets an empty problem.
-__global__ void gj_tc_cross_setup_kernel(const InvDesc* __restrict__ descs, int count, int p, int nb, int dir,
+// Descriptors of a cross product inside a block of delayed panels
+// J_0 = [p, p + nb), J_1, ... (see run_batch_t), for its panel J_i (i >= 1)
+// and the earlier ones J_<i = [p, p + i nb):
+//   dir 0 brings the columns of J_i up to date with the composite transform
+//         of J_<i:  X[:, J_i] = X[:, J_<i] X[J_<i, J_i] + X[:, J_i];
+//   dir 1 applies the transform of J_i to the columns of J_<i:
+//         X[:, J_<i] = X[:, J_i] X[J_i, J_<i] + X[:, J_<i];
+// the transform's own pivot rows take no addend.  A matrix without panel J_i
+// gets an empty problem.
+__global__ void gj_tc_cross_setup_kernel(const InvDesc* __restrict__ descs, int count, int p, int nb, int i, int dir,
                                          oz::PackDesc* __restrict__ pa, oz::PackDesc* __restrict__ pb,
                                          oz::Problem* __restrict__ pr) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= count) return;
   const InvDesc d = descs[u];
   const int b = d.b;
-  const int w1 = max(0, min(nb, b - p)), w2 = max(0, min(nb, b - p - nb));
-  const bool live = w1 > 0 && w2 > 0;
-  const int ca = dir ? p + nb : p, wa = dir ? w2 : w1;  // the transform's columns (and pivot rows)
-  const int cc = dir ? p : p + nb, wc = dir ? w1 : w2;  // the columns brought up to date
+  const int wi = max(0, min(nb, b - p - i * nb));  // width of J_i in this matrix
+  const int wl = max(0, min(i * nb, b - p));       // width of J_<i
+  const bool live = wi > 0 && wl > 0;
+  const int ca = dir ? p + i * nb : p, wa = dir ? wi : wl;  // the transform's columns (and pivot rows)
+  const int cc = dir ? p : p + i * nb, wc = dir ? wl : wi;  // the columns brought up to date
   double* X = (double*)d.work;
   pa[u] = oz::PackDesc{X + (live ? ca : 0), b, live ? b : 0, live ? wa : 0, 0, u};
   pb[u] = oz::PackDesc{X + (live ? (int64_t)ca * b + cc : 0), b, live ? wa : 0, live ? wc : 0, 1, u};
@@ -425,6 +430,12 @@ __global__ void gj_tc_cross_setup_kernel(const InvDesc* __restrict__ descs, int 
   pr[u] = q;
 }
 
+// Panels per block of delayed tensor-core updates (the code takes any S >= 2).
+// Two: with four (K = 256) the trailing product's tiles lose the FP32 integer
+// shortcut of K <= 128 and the cross products grow with the block; measured
+// on the 64-block default step, 216.3 against 212.0 ms.
+int inv_delay(int, int) { return 2; }
+
 struct TcLayout {
   int rpa, rpb, kpad;
   size_t da, db, ea, eb, pa, pb, pr, total;
@@ -435,10 +446,10 @@ TcLayout tc_layout(int bmax, int count) {
   TcLayout L;
   L.rpa = (bmax + oz::tile_m() - 1) / oz::tile_m() * oz::tile_m();
   L.rpb = (bmax + oz::tile_n() - 1) / oz::tile_n() * oz::tile_n();
-  // the inner length of the widest update is two panel widths (updates
-  // delayed over panel pairs)
+  // the inner length of the widest update is the width of a block of
+  // delayed panels
   const int nb = inv_panel_width(bmax, F64, true);
-  L.kpad = (std::min(2 * nb, bmax) + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
+  L.kpad = (std::min(inv_delay(bmax, nb) * nb, bmax) + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
   const size_t K = L.kpad;
   size_t o = 0;
   L.da = o;
@@ -574,17 +585,18 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   };
   cudaError_t e;
   if (tc && nb < b) {
-    // Tensor-core updates, delayed over panel pairs J1 = [p, p + nb),
-    // J2 = [p + nb, p + 2 nb): the columns outside J = J1 u J2 receive one
-    // rank-2nb update (K = 128) instead of two rank-nb ones, which halves the
-    // per-entry epilogues of the widest products.  The panel columns carry
-    // the composite transform first:
-    //   panel J1; rows done before J1 (product); X[:, J2] += T1 X[J1, J2];
-    //   panel J2; rows done before J2 (product); X[:, J1] += T2 X[J2, J1];
-    //   X[:, rest] += X[:, J] X[J, rest]
-    // (each "+=" with the rows of the transform's own pivots taking no
-    // addend), which is the sequence of single-panel updates regrouped: the
-    // pivot rows X[J, rest] are untouched (only exchanged) until the last one.
+    // Tensor-core updates, delayed over blocks of S panels J_0 = [p, p + nb),
+    // J_1, ..., J_{S-1} (S = inv_delay, two): the columns outside the block J receive
+    // one rank-S nb update (K = S nb) instead of S rank-nb ones, which divides
+    // the per-entry epilogues of the widest products by S.  The block's
+    // columns carry the composite transform first; for i = 0 .. S-1:
+    //   (i > 0) X[:, J_i]  += X[:, J_<i] X[J_<i, J_i]   (J_i up to date)
+    //   panel J_i; rows done before J_i (product)
+    //   (i > 0) X[:, J_<i] += X[:, J_i] X[J_i, J_<i]    (J_i's transform on J_<i)
+    // then X[:, rest] += X[:, J] X[J, rest] (each "+=" with the rows of the
+    // transform's own pivots taking no addend).  This is the sequence of
+    // single-panel updates regrouped: the pivot rows X[J, rest] are untouched
+    // (only exchanged) until the last product.
     const TcLayout T = tc_layout(b, count);
     char* base = (char*)tc->scratch;
     auto* pa = (oz::PackDesc*)(base + T.pa);
@@ -617,7 +629,9 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       nl += 3;
       return oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
     };
-    const int k1 = (nb + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k();
+    auto kround = [](int x) { return (x + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k(); };
+    const int k1 = kround(nb);
+    const int S = inv_delay(b, nb);
     const int g = (count + 127) / 128;
     // rows [0, pp) of the panel [pp, pp + nb): p x nb outputs per matrix
     auto done = [&](int pp) -> cudaError_t {
@@ -626,23 +640,25 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       ++nl;
       return product(k1, -1.0, 0.0, (pp + oz::tile_m() - 1) / oz::tile_m(), (nb + oz::tile_n() - 1) / oz::tile_n());
     };
-    auto cross = [&](int pp, int dir) -> cudaError_t {
-      gj_tc_cross_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, pp, nb, dir, pa, pb, pr);
+    auto cross = [&](int pp, int i, int dir) -> cudaError_t {
+      gj_tc_cross_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, pp, nb, i, dir, pa, pb, pr);
       ++nl;
-      return product(k1, 1.0, 1.0, T.rpa / oz::tile_m(), (nb + oz::tile_n() - 1) / oz::tile_n());
+      const int wl = std::min(i * nb, b - pp);  // J_<i of the largest matrix
+      if (dir == 0) return product(kround(wl), 1.0, 1.0, T.rpa / oz::tile_m(), (nb + oz::tile_n() - 1) / oz::tile_n());
+      return product(k1, 1.0, 1.0, T.rpa / oz::tile_m(), (wl + oz::tile_n() - 1) / oz::tile_n());
     };
-    for (int p = 0; p < b; p += 2 * nb) {
-      if ((e = panel(p)) != cudaSuccess) return e;
-      if ((e = done(p)) != cudaSuccess) return e;
-      if (p + nb < b) {
-        if ((e = cross(p, 0)) != cudaSuccess) return e;
-        if ((e = panel(p + nb)) != cudaSuccess) return e;
-        if ((e = done(p + nb)) != cudaSuccess) return e;
-        if ((e = cross(p, 1)) != cudaSuccess) return e;
+    for (int p = 0; p < b; p += S * nb) {
+      for (int i = 0; i < S && p + i * nb < b; ++i) {
+        const int pi = p + i * nb;
+        if (i > 0 && (e = cross(p, i, 0)) != cudaSuccess) return e;
+        if ((e = panel(pi)) != cudaSuccess) return e;
+        if ((e = done(pi)) != cudaSuccess) return e;
+        if (i > 0 && (e = cross(p, i, 1)) != cudaSuccess) return e;
       }
-      gj_tc_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, p, 2 * nb, pa, pb, pr);
+      gj_tc_setup_kernel<<<g, 128, 0, s>>>(d_desc, count, p, S * nb, pa, pb, pr);
       ++nl;
-      if ((e = product(T.kpad, 1.0, 1.0, T.rpa / oz::tile_m(), T.rpb / oz::tile_n())) != cudaSuccess) return e;
+      const int kt = kround(std::min(S * nb, b - p));
+      if ((e = product(kt, 1.0, 1.0, T.rpa / oz::tile_m(), T.rpb / oz::tile_n())) != cudaSuccess) return e;
     }
   } else {
     for (int p = 0; p < b; p += nb) {
