@@ -544,7 +544,7 @@ def run_products(args, rank, world, dist):
     B = torch.rand((cnt, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1
     C = torch.rand((cnt, n, n), dtype=torch.float64, device="cuda", generator=g) * 2 - 1
     out = torch.empty_like(C)
-    L = mb.lib()
+    L = mb.test_lib()
     L.mbinv_debug_oz_products_bytes.restype = ctypes.c_size_t
     L.mbinv_debug_oz_products_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
     f = L.mbinv_debug_oz_products

@@ -20,6 +20,7 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmbinv.so")
+TEST_LIB_PATH = os.path.join(_HERE, "_build", "libmbinv_test.so")
 
 OK, EINVAL, ENOMEM_CAP, ESINGULAR, ENOTCONV, ETIMEOUT, ECUDA, ENOTSUP = range(8)
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_bf16": 2, "fp64_tc": 3}
@@ -139,6 +140,22 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+_test_lib = None
+
+
+def test_lib():
+    """The test hooks (libmbinv_test.so, not part of the public header): the
+    tests and the bench load them; they call into the product library."""
+    global _test_lib
+    lib()
+    with _lock:
+        if _test_lib is None:
+            if not os.path.exists(TEST_LIB_PATH):
+                raise RuntimeError(f"{TEST_LIB_PATH} missing; call paper_1612_00001_gb300.build() first")
+            _test_lib = ctypes.CDLL(TEST_LIB_PATH)
+    return _test_lib
 
 
 def _check(status: int, what: str):

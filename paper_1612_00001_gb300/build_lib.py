@@ -1,7 +1,9 @@
 """Builds libmbinv.so in-tree with nvcc for sm_103a (no CMake).
 
 Every translation unit is compiled in parallel, then linked into
-``paper_1612_00001_gb300/_build/libmbinv.so``.
+``paper_1612_00001_gb300/_build/libmbinv.so`` (the product) and the test
+hooks of ``csrc/testhooks`` into ``_build/libmbinv_test.so``, which links
+against the product library and is loaded only by the tests and the bench.
 """
 from __future__ import annotations
 
@@ -15,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmbinv.so")
+TEST_SRC = os.path.join(CSRC, "testhooks")
+TEST_LIB = os.path.join(BUILD, "libmbinv_test.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,12 +33,17 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
+def test_sources():
+    return sorted(os.path.join(TEST_SRC, f) for f in os.listdir(TEST_SRC) if f.endswith((".cu", ".cpp")))
+
+
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(TEST_LIB):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "mbinv.h")]
-    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+    t = min(os.path.getmtime(LIB), os.path.getmtime(TEST_LIB))
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(TEST_SRC, f) for f in os.listdir(TEST_SRC)]
+            + [os.path.join(HERE, "..", "include", "mbinv.h"), os.path.abspath(__file__)])
+    return any(os.path.getmtime(d) > t for d in deps if os.path.isfile(d))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -58,14 +67,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    tsrcs = test_sources()
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs) + len(tsrcs))) as ex:
+        objs = list(ex.map(compile_one, srcs + tsrcs))
+    objs, tobjs = objs[:len(srcs)], objs[len(srcs):]
+
+    def link(out, cmd_tail):
+        tmp = out + f".{os.getpid()}.tmp"
+        r = subprocess.run([nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + cmd_tail,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {os.path.basename(out)} failed:\n{r.stderr}")
+        os.replace(tmp, out)
+
+    link(LIB, objs)
+    # the test hooks call into the product library, found next to them
+    link(TEST_LIB, tobjs + ["-L", BUILD, "-lmbinv", "-Xlinker", "-rpath", "-Xlinker", "$ORIGIN"])
     return LIB
 
 

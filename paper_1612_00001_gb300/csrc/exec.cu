@@ -23,6 +23,11 @@
 
 namespace mbinv {
 
+std::atomic<int>& injected_alloc_failures() {
+  static std::atomic<int> n{0};
+  return n;
+}
+
 cudaError_t once_per_device(const void* key, const std::function<cudaError_t()>& setup) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -27,10 +27,8 @@ inline bool& cap_refused() {
 
 // Test hook: the next n device allocations of the library fail as if the
 // device were out of memory (cudaErrorMemoryAllocation), before cudaMalloc.
-inline std::atomic<int>& injected_alloc_failures() {
-  static std::atomic<int> n{0};
-  return n;
-}
+// One counter per process (defined once, in exec.cu).
+std::atomic<int>& injected_alloc_failures();
 
 // A device buffer that grows on demand.  With a tracker attached, every byte
 // it holds is counted there, and growth that would take the tracker past its

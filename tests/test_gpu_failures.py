@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 def mb():
     import paper_1612_00001_gb300 as mb
     mb.build()
-    L = mb.lib()
+    L = mb.test_lib()
     L.mbinv_debug_set_stall_ns.argtypes = [ctypes.c_ulonglong]
     L.mbinv_debug_set_stall_ns.restype = None
     L.mbinv_debug_fail_allocations.argtypes = [ctypes.c_int]
@@ -38,7 +38,7 @@ def dev(a):
 
 def test_device_wait_that_runs_out_is_reported(mb):
     m = bi.uniform_shift(768, 1)  # b = 192: Schur products and inverse updates are digit products
-    L = mb.lib()
+    L = mb.test_lib()
     with mb.Context(dev(m), 4, precision="fp64_tc") as ctx:
         ref = to_np(ctx.block(1, 2))
         L.mbinv_debug_set_stall_ns(1000000)  # 1 ms
@@ -54,7 +54,7 @@ def test_device_wait_that_runs_out_is_reported(mb):
 
 def test_failed_allocation_is_reported_before_launch(mb):
     m = bi.uniform_shift(512, 2)
-    L = mb.lib()
+    L = mb.test_lib()
     with mb.Context(dev(m), 8, precision="fp64_tc") as c0:
         ref = to_np(c0.block(3, 4))
     with mb.Context(dev(m), 8, precision="fp64_tc") as ctx:

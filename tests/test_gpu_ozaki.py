@@ -26,7 +26,7 @@ KCHUNK = 512  # K of one exact accumulation
 def hook():
     import paper_1612_00001_gb300 as mb
     mb.build()
-    f = mb.lib().mbinv_debug_oz_gemm
+    f = mb.test_lib().mbinv_debug_oz_gemm
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] * 4 + [ctypes.c_double] * 2 + [ctypes.c_void_p]
     return f

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 def hook():
     import paper_1612_00001_gb300 as mb
     mb.build()
-    f = mb.lib().mbinv_debug_tc_gemm
+    f = mb.test_lib().mbinv_debug_tc_gemm
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 6 + [ctypes.c_void_p]
     return f

@@ -15,7 +15,7 @@ import oracle
 def plan():
     import paper_1612_00001_gb300 as mb
     mb.build()
-    f = mb.lib().mbinv_debug_plan
+    f = mb.test_lib().mbinv_debug_plan
     f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     f.restype = ctypes.c_int
 
@@ -61,7 +61,7 @@ def test_k8_and_k16_counts(plan):
 
 def test_invalid_arguments():
     import paper_1612_00001_gb300 as mb
-    f = mb.lib().mbinv_debug_plan
+    f = mb.test_lib().mbinv_debug_plan
     f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     out = (ctypes.c_double * 6)()
     assert f(8, 8, 0, 0, out) == -1
@@ -143,7 +143,7 @@ def _merged(k, reqs):
 def plan_group():
     import paper_1612_00001_gb300 as mb
     mb.build()
-    f = mb.lib().mbinv_debug_plan_group
+    f = mb.test_lib().mbinv_debug_plan_group
     f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                   ctypes.POINTER(ctypes.c_double)]
     f.restype = ctypes.c_int

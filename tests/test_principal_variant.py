@@ -75,7 +75,7 @@ def test_variant_is_stable_where_the_recursion_is_not():
 def interp():
     import paper_1612_00001_gb300 as mb
     mb.build()
-    f = mb.lib().mbinv_debug_run_schedule_scalar
+    f = mb.test_lib().mbinv_debug_run_schedule_scalar
     dp = ctypes.POINTER(ctypes.c_double)
     f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                   ctypes.c_int, dp, dp, dp]
