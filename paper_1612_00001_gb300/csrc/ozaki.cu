@@ -415,6 +415,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
           tmem_wait_regs(acc);
+          // Group sums within 2^22 in magnitude - always for K <= 128
+          // (8 * 128 * 2^12), and for longer K whenever the warp's 32 sums of
+          // these four columns are (checked) - become integers by an FP32 add:
+          // adding 1.5 * 2^23 gives an FP32 in [2^23, 2^24] whose bit pattern
+          // less that of 1.5 * 2^23 is the integer (at 2^24 the difference is
+          // still exactly 2^22).  Otherwise (K up to 512: up to 2^24) a
+          // float-to-integer conversion each.
+          bool fast = small_k;
+          if (!fast) {
+            float mx = 0.0f;
+#pragma unroll
+            for (int gg = 0; gg < ND; ++gg)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) mx = fmaxf(mx, fabsf(__uint_as_float(acc[gg][u])));
+            fast = __all_sync(0xffffffffu, mx <= 4194304.0f);
+          }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int c = cq + u;
@@ -423,11 +439,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               vout[c] = __longlong_as_double(0x7FF8000000000000LL);
             } else {
               int a[ND];
-              if (small_k) {
-                // |G_g| <= 8 * 128 * 2^12 = 2^22: adding 1.5 * 2^23 gives an
-                // FP32 in [2^23, 2^24] whose bit pattern less that of 1.5 * 2^23
-                // is the integer (an FP32 add, not a conversion; at 2^24 the
-                // pattern difference is still exactly 2^22)
+              if (fast) {
 #pragma unroll
                 for (int gg = 0; gg < ND; ++gg)
                   a[gg] = __float_as_int(__uint_as_float(acc[gg][u]) + 12582912.0f) - 0x4B400000;

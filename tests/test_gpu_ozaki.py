@@ -123,6 +123,32 @@ def test_bitwise_against_integer_scheme(hook, m, n, k, count):
             assert np.array_equal(got[g], want), (alpha, g, np.max(np.abs(got[g] - want)))
 
 
+def test_bitwise_with_group_sums_past_2_22(hook):
+    """Entries whose six leading balanced digits are all 63 make the group
+    sums of K = 512 exceed 2^22 (group 5: 6 pairs x 512 x 63^2 > 2^23), where
+    the epilogue's FP32-add shortcut would not be exact: the warps holding
+    such rows must take the conversions.  Rows 0-15 and 64-79 of A hold the
+    value, the others random entries (warps see both), and the result is still
+    the integer scheme bit for bit."""
+    x = 63.0 * sum(128.0 ** (7 - p) for p in range(6)) * 2.0 ** -55  # digits 63 x 6, 0, 0 (row exponent 0)
+    E = row_exponents(np.array([[x]]))
+    d = digits(np.array([[x]]), E)
+    assert [int(v) for v in d[:, 0, 0]] == [63] * 6 + [0, 0]
+    rng = np.random.default_rng(12)
+    m, n, k = 128, 64, 512
+    A = rng.standard_normal((1, m, k))
+    A[0, 0:16, :] = x
+    A[0, 64:80, :] = x
+    B = np.full((1, k, n), x)
+    B[0, :, 40:] = rng.standard_normal((k, n - 40))
+    C = rng.standard_normal((1, m, n))
+    G5 = 6 * k * 63 * 63
+    assert G5 > 2 ** 22
+    got = run(hook, A, B, C, -1.0, 1.0)
+    want = scheme(A[0], B[0], C[0], -1.0, 1.0)
+    assert np.array_equal(got[0], want), np.max(np.abs(got[0] - want))
+
+
 def bound(A, B, ref, k):
     amax = np.max(np.abs(A), axis=2, keepdims=True)
     bmax = np.max(np.abs(B), axis=1, keepdims=True)
