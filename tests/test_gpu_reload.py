@@ -27,22 +27,29 @@ def blocks_of(ctx):
     return [to_np(o) for o in ctx.blocks(REQ)]
 
 
-@pytest.mark.parametrize("where,n,prec", [("host", 512, "fp64_tc"), ("host", 512, "fp64"),
-                                          ("device", 512, "fp64_tc"), ("device_padded", 510, "fp64_tc")])
-def test_reload_equals_a_fresh_context(mb, where, n, prec):
+@pytest.mark.parametrize("where,n,prec,dt", [("host", 512, "fp64_tc", "f64"), ("host", 512, "fp64", "f64"),
+                                             ("device", 512, "fp64_tc", "f64"),
+                                             ("device_padded", 510, "fp64_tc", "f64"),
+                                             ("device", 512, "fp64_tc", "f32")])
+def test_reload_equals_a_fresh_context(mb, where, n, prec, dt):
+    """dt = f32: an FP32 M on an FP64-valued path is converted on the device
+    (staged, then widened) at creation and again at every reload."""
     k = 4
+    tdt = torch.float64 if dt == "f64" else torch.float32
     m1, m2 = bi.uniform_shift(n, 1), bi.uniform_shift(n, 2)
+    if dt == "f32":
+        m2 = m2.astype(np.float32).astype(np.float64)  # the values the context sees
     if where == "host":
-        buf = torch.tensor(m1, dtype=torch.float64).pin_memory()
+        buf = torch.tensor(m1, dtype=tdt).pin_memory()
     else:
-        buf = torch.tensor(m1, dtype=torch.float64, device="cuda")
-    ctx = mb.Context(buf, k, precision=prec)
+        buf = torch.tensor(m1, dtype=tdt, device="cuda")
+    ctx = mb.Context(buf, k, precision=prec, out_dtype=torch.float64)
     first = blocks_of(ctx)
-    ctx.reload(torch.tensor(m2, dtype=torch.float64))
+    ctx.reload(torch.tensor(m2, dtype=tdt))
     torch.cuda.synchronize()
     got = blocks_of(ctx)
-    fresh_buf = torch.tensor(m2, dtype=torch.float64, device="cuda" if where != "host" else "cpu")
-    with mb.Context(fresh_buf, k, precision=prec) as fresh:
+    fresh_buf = torch.tensor(m2, dtype=tdt, device="cuda" if where != "host" else "cpu")
+    with mb.Context(fresh_buf, k, precision=prec, out_dtype=torch.float64) as fresh:
         want = blocks_of(fresh)
     for (i, j), a, b_, f in zip(REQ, got, want, first):
         assert np.array_equal(a, b_), (where, i, j)
