@@ -502,8 +502,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // is read from global memory once, all its loads in flight together; longer
 // K takes two passes over chunks.  Pass 1 finds each row's largest magnitude
 // (the bit patterns of |x| order like the values; Inf and NaN sort above every
-// finite value), pass 2 writes the digits as pairs of BF16 (128 contiguous
-// bytes per warp instruction).
+// finite value), pass 2 writes the digits, four BF16 per lane and digit
+// (256 contiguous bytes per warp instruction; two for chunks of 64 entries).
 __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
                                                        int rpc, __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
   extern __shared__ double S[];  // [rpc][kc + 1]
@@ -595,14 +595,36 @@ __global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restr
       const int E = sE[rr];
       const double* row = S + rr * lds;
       __nv_bfloat16* out = dst + ((int64_t)d.slab * ND * rows_pad + r0 + rr) * kpad + k0;
+      // four entries per lane, one 8-byte store per digit, when the chunk is
+      // a multiple of 128 entries (the slab rows start on 128 bytes); else two
+      // entries per lane (kw is a multiple of 64), so that no lane idles
+      if (kw % 128) {
 #pragma unroll 1
-      for (int kk = 2 * lane; kk < kw; kk += 64) {
-        int d0[ND], d1[ND];
+        for (int kk = 2 * lane; kk < kw; kk += 64) {
+          int d0[ND], d1[ND];
+          digits8(row[kk], E, d0);
+          digits8(row[kk + 1], E, d1);
+#pragma unroll
+          for (int p = 0; p < ND; ++p)
+            *(__nv_bfloat162*)&out[(int64_t)p * rows_pad * kpad + kk] = digit_pair(d0[p], d1[p]);
+        }
+        continue;
+      }
+#pragma unroll 1
+      for (int kk = 4 * lane; kk < kw; kk += 128) {
+        int d0[ND], d1[ND], d2[ND], d3[ND];
         digits8(row[kk], E, d0);
         digits8(row[kk + 1], E, d1);
+        digits8(row[kk + 2], E, d2);
+        digits8(row[kk + 3], E, d3);
 #pragma unroll
-        for (int p = 0; p < ND; ++p)
-          *(__nv_bfloat162*)&out[(int64_t)p * rows_pad * kpad + kk] = digit_pair(d0[p], d1[p]);
+        for (int p = 0; p < ND; ++p) {
+          const __nv_bfloat162 lo = digit_pair(d0[p], d1[p]), hi = digit_pair(d2[p], d3[p]);
+          uint2 v;
+          v.x = *reinterpret_cast<const uint32_t*>(&lo);
+          v.y = *reinterpret_cast<const uint32_t*>(&hi);
+          *reinterpret_cast<uint2*>(&out[(int64_t)p * rows_pad * kpad + kk]) = v;
+        }
       }
     }
   }
