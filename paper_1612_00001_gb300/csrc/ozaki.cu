@@ -496,15 +496,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// One CTA per rpc slab rows (64 for K <= 128, down to 16 for K >= 512: about
-// 66 KB staged either way).  The source rows (or columns, transposed) are
+// One CTA per rpc slab rows (64 for K <= 64, down to 8 for K >= 512: about
+// 33 KB staged either way).  The source rows (or columns, transposed) are
 // staged in shared memory up to 512 entries of K at a time: a slab of K <= 512
 // is read from global memory once, all its loads in flight together; longer
 // K takes two passes over chunks.  Pass 1 finds each row's largest magnitude
 // (the bit patterns of |x| order like the values; Inf and NaN sort above every
 // finite value), pass 2 writes the digits, four BF16 per lane and digit
 // (256 contiguous bytes per warp instruction; two for chunks of 64 entries).
-__global__ void __launch_bounds__(256, 3) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
+__global__ void __launch_bounds__(256, 4) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
                                                        int rpc, __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
   extern __shared__ double S[];  // [rpc][kc + 1]
   __shared__ int sE[PMAXR];
@@ -654,8 +654,9 @@ cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kp
     if (e != cudaSuccess) return e;
   }
   const int kc = kpad < PKC ? kpad : PKC;
-  // rows per CTA: about 66 KB of staged entries, 16..64 rows (rows_pad is a multiple of 64)
-  int rpc = PR * (PKC / kc);
+  // rows per CTA: about 33 KB of staged entries, 8..64 rows (rows_pad is a
+  // multiple of 64), so that four CTAs share an SM
+  int rpc = (PR / 2) * (PKC / kc);
   rpc = rpc > PMAXR ? PMAXR : rpc;
   if (rows_pad % rpc) rpc = PR;
   if ((size_t)rpc * (kc + 1) * sizeof(double) > (size_t)kPackSmemMax) return cudaErrorInvalidValue;
