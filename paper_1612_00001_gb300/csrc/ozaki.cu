@@ -25,23 +25,28 @@
 // Kernel.  Persistent: one CTA per SM (the eight 64-column group
 // accumulators take all 512 TMEM columns) walks the 128 x 64 output tiles of
 // the launch, with three roles:
-//   warp 0, one lane:  TMA producer.  Per K block of 64 it loads all eight
-//                      digits of the B tile in one 3-D copy (64 KB, double
-//                      buffered) and each digit of the A tile (16 KB) into a
+//   warp 0, one lane:  TMA producer.  Per pass and K block of 64 it loads
+//                      the B digits of the pass (0-3 or 0-7, 3-D copies of
+//                      four digits, 32 KB each; double buffered) and the A
+//                      digits of the pass (0-3 or 0-7, 16 KB each) into a
 //                      four-deep ring; it runs ahead into the next tile while
 //                      the current one is read out.
-//   warp 1, one lane:  MMA issuer.  For A digit p one tcgen05.mma (two when
-//                      more than four B digits remain) multiplies it by the
-//                      B digits q = 0..7-p stacked along N, writing TMEM
+//   warp 1, one lane:  MMA issuer, two passes per tile.  Pass 0: the pairs
+//                      with p + q <= 3 (groups 0-3, TMEM columns 0-255);
+//                      pass 1: the others (groups 4-7, columns 256-511).  One
+//                      tcgen05.mma per A digit and pass multiplies it by the
+//                      B digits q of that pass stacked along N, writing TMEM
 //                      columns 64 (p + q) - so every pair lands in its group
-//                      G_{p+q} without any data movement.  It starts a tile
-//                      once the epilogue has read the previous one out.
+//                      G_{p+q} without any data movement.  A pass starts once
+//                      the epilogue has read its half of the previous tile
+//                      out, so each half's read-out overlaps the other's MMAs.
 //   warps 2-17:        epilogue.  Warp w reads TMEM lanes 32 (w mod 4) ..
-//                      (a row per thread) and one quarter of the columns,
-//                      combines the groups into registers, hands TMEM back to
-//                      the MMA warp, then reads Cin and writes
-//                      beta * Cin + alpha * C (16 contiguous entries per
-//                      thread) while the next tile's MMAs run.
+//                      (a row per thread) and one quarter of the columns, one
+//                      half of the groups after each pass, combines them into
+//                      registers, hands each half back to the MMA warp, then
+//                      reads Cin and writes beta * Cin + alpha * C (16
+//                      contiguous entries per thread) while the next tile's
+//                      MMAs run.
 // Every mbarrier wait is bounded (about two seconds of %globaltimer); a wait
 // that runs out raises the error word and the CTA drains, frees its TMEM and
 // returns.
@@ -157,9 +162,7 @@ __device__ __forceinline__ void add96(uint32_t& r0, uint32_t& r1, uint32_t& r2, 
 //     S = h0 2^42 + h1 2^28 + l0 2^14 + l1,
 // summed as a 96-bit integer in three 32-bit limbs, then taken to sign and
 // magnitude, whose leading 53 bits are rounded with the bits below them.
-__device__ __forceinline__ double combine(const int (&a)[ND], int e, bool neg_alpha) {
-  const int h0 = a[0] * 128 + a[1], h1 = a[2] * 128 + a[3];
-  const int l0 = a[4] * 128 + a[5], l1 = a[6] * 128 + a[7];
+__device__ __forceinline__ double combine(int h0, int h1, int l0, int l1, int e, bool neg_alpha) {
   uint32_t s0 = (uint32_t)l1, s1 = (uint32_t)(l1 >> 31), s2 = s1;
   add96(s0, s1, s2, (uint32_t)l0 << 14, (uint32_t)(l0 >> 18), (uint32_t)(l0 >> 31));
   add96(s0, s1, s2, (uint32_t)h1 << 28, (uint32_t)(h1 >> 4), (uint32_t)(h1 >> 31));
@@ -209,13 +212,15 @@ __device__ __forceinline__ bool tile_live(const Params& P, const Problem* __rest
   return !(*tm * BM >= pr.m || *tn * BN >= pr.n || (*tn * BN >= pr.skip_c0 && *tn * BN + BN <= pr.skip_c1));
 }
 
-// All eight digits of the B tile of one K block into the next of two buffers.
+// The first nq (4 or 8) digits of the B tile of one K block into the next of
+// two buffers.
 __device__ __forceinline__ bool load_b_block(uint8_t* sB, uint64_t* fullB, uint64_t* emptyB, const CUtensorMap* tmB,
-                                             int* nbq, int kb, int tn, int bslab) {
+                                             int* nbq, int kb, int tn, int bslab, int nq) {
   const int s = *nbq & 1;
   if (*nbq >= 2 && !mbar_wait(&emptyB[s], ((uint32_t)(*nbq >> 1) & 1u) ^ 1u)) return false;
-  mbar_expect_tx(&fullB[s], B_BYTES);
-  tma_load_3d(sB + s * B_BYTES, tmB, &fullB[s], kb * BK, tn * BN, bslab * ND);
+  mbar_expect_tx(&fullB[s], nq * BQ_BYTES);
+  for (int h = 0; h < nq; h += 4)  // the map's box holds four digits
+    tma_load_3d(sB + s * B_BYTES + h * BQ_BYTES, tmB, &fullB[s], kb * BK, tn * BN, bslab * ND + h);
   ++*nbq;
   return true;
 }
@@ -231,9 +236,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* emptyB = fullB + 2;
   uint64_t* fullA = emptyB + 2;
   uint64_t* emptyA = fullA + ASTAGES;
-  uint64_t* tfull = emptyA + ASTAGES;   // accumulators of a tile complete (MMA -> epilogue)
-  uint64_t* tempty = tfull + 1;         // accumulators read out (epilogue -> MMA)
-  uint64_t* stall = tempty + 1;         // test of the timeout path: never arrived at
+  // The 36 digit pairs run in two passes per tile: pass 0 the pairs with
+  // p + q <= 3 (groups 0-3, TMEM columns 0-255), pass 1 the others (groups
+  // 4-7, columns 256-511); each half of TMEM is filled and handed back on its
+  // own, so the epilogue reads one half while the MMAs fill the other.
+  uint64_t* tfull = emptyA + ASTAGES;   // [2] a half's accumulators complete (MMA -> epilogue)
+  uint64_t* tempty = tfull + 2;         // [2] a half read out (epilogue -> MMA)
+  uint64_t* stall = tempty + 2;         // test of the timeout path: never arrived at
   uint32_t* tmem_slot = (uint32_t*)(stall + 1);
   int* failed = (int*)(tmem_slot + 1);
 
@@ -247,8 +256,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&fullA[s], 1);
       mbar_init(&emptyA[s], 1);
     }
-    mbar_init(tfull, 1);
-    mbar_init(tempty, NEPI);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&tfull[h], 1);
+      mbar_init(&tempty[h], NEPI);
+    }
     mbar_init(stall, 1);
     *failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -282,29 +293,35 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer: runs ahead into the next tile while the
-      // epilogue of the current one drains the accumulators
+      // epilogue of the current one drains the accumulators.  Per tile and
+      // pass the K blocks in order: B digits 0-3 (pass 0) or 0-7 (pass 1),
+      // and A digits 0-3 (pass 0) or 0-7 (pass 1).
       int na = 0, nbq = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
         int g, tm, tn;
         if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
         const int aslab = probs[g].a_slab, bslab = probs[g].b_slab;
-        ok = load_b_block(sB, fullB, emptyB, &tmB, &nbq, P.kb0, tn, bslab);
-        for (int u = 0; ok && u < P.nkb; ++u) {
-          for (int p = 0; p < ND; ++p) {
-            const int s = na % ASTAGES;
-            if ((na >= ASTAGES && !mbar_wait(&emptyA[s], ((uint32_t)(na / ASTAGES) & 1u) ^ 1u)) ||
-                *(volatile int*)failed) {
-              ok = false;
-              break;
-            }
-            mbar_expect_tx(&fullA[s], A_BYTES);
-            tma_load_3d(sA + s * A_BYTES, &tmA, &fullA[s], (P.kb0 + u) * BK, tm * BM, aslab * ND + p);
-            ++na;
-            // the next K block's B goes out early: its buffer was freed with block u - 1
-            if (p == 1 && u + 1 < P.nkb && !load_b_block(sB, fullB, emptyB, &tmB, &nbq, P.kb0 + u + 1, tn, bslab)) {
-              ok = false;
-              break;
+        for (int pass = 0; ok && pass < 2; ++pass) {
+          const int nd = pass ? ND : 4;
+          ok = load_b_block(sB, fullB, emptyB, &tmB, &nbq, P.kb0, tn, bslab, nd);
+          for (int u = 0; ok && u < P.nkb; ++u) {
+            for (int p = 0; p < nd; ++p) {
+              const int s = na % ASTAGES;
+              if ((na >= ASTAGES && !mbar_wait(&emptyA[s], ((uint32_t)(na / ASTAGES) & 1u) ^ 1u)) ||
+                  *(volatile int*)failed) {
+                ok = false;
+                break;
+              }
+              mbar_expect_tx(&fullA[s], A_BYTES);
+              tma_load_3d(sA + s * A_BYTES, &tmA, &fullA[s], (P.kb0 + u) * BK, tm * BM, aslab * ND + p);
+              ++na;
+              // the next K block's B goes out early: its buffer was freed with block u - 1
+              if (p == 1 && u + 1 < P.nkb &&
+                  !load_b_block(sB, fullB, emptyB, &tmB, &nbq, P.kb0 + u + 1, tn, bslab, nd)) {
+                ok = false;
+                break;
+              }
             }
           }
         }
@@ -313,60 +330,75 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- MMA issuer
+      // ---------------- MMA issuer.  Pass 0: A digit p (0-3) times B digits
+      // 0..3-p, into TMEM columns 64 p .. 255 (groups p..3).  Pass 1: A digit
+      // p < 4 times B digits 4-p..7-p into columns 256-511 (groups 4-7), A
+      // digit p >= 4 times B digits 0..7-p into columns 64 p .. 511.  Every
+      // pair with p + q = g lands in group g's 64 columns.
       int na = 0, nbq = 0, it = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
         int g, tm, tn;
         if (!tile_live(P, probs, t, &g, &tm, &tn)) continue;
-        // the epilogue has read the previous tile's accumulators out
-        if (it > 0 && !mbar_wait(tempty, (uint32_t)(it - 1) & 1u)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int u = 0; ok && u < P.nkb; ++u) {
-          const int sb = nbq & 1;
-          if (!mbar_wait(&fullB[sb], (uint32_t)(nbq >> 1) & 1u)) {
+        for (int pass = 0; ok && pass < 2; ++pass) {
+          const int nd = pass ? ND : 4;
+          // the epilogue has read this half of the previous tile's accumulators out
+          if (it > 0 && !mbar_wait(&tempty[pass], (uint32_t)(it - 1) & 1u)) {
             ok = false;
             break;
           }
-          const uint32_t b0 = smem_u32(sB + sb * B_BYTES);
-          for (int p = 0; p < ND; ++p) {
-            const int s = na % ASTAGES;
-            if (!mbar_wait(&fullA[s], (uint32_t)(na / ASTAGES) & 1u)) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int u = 0; ok && u < P.nkb; ++u) {
+            const int sb = nbq & 1;
+            if (!mbar_wait(&fullB[sb], (uint32_t)(nbq >> 1) & 1u)) {
               ok = false;
               break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA + s * A_BYTES);
-            const int nq0 = ND - p < 4 ? ND - p : 4, nq1 = ND - p - nq0;
-            const uint32_t id0 = idesc(64 * nq0), id1 = idesc(64 * (nq1 > 0 ? nq1 : 1));
+            const uint32_t b0 = smem_u32(sB + sb * B_BYTES);
+            for (int p = 0; p < nd; ++p) {
+              const int s = na % ASTAGES;
+              if (!mbar_wait(&fullA[s], (uint32_t)(na / ASTAGES) & 1u)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t a0 = smem_u32(sA + s * A_BYTES);
+              int col, q0, nq;
+              if (pass == 0) {
+                col = 64 * p, q0 = 0, nq = 4 - p;
+              } else if (p < 4) {
+                col = 256, q0 = 4 - p, nq = 4;
+              } else {
+                col = 64 * p, q0 = 0, nq = ND - p;
+              }
+              const uint32_t id = idesc(64 * nq);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              // the first MMAs (digit 0 of the first K block) start all eight groups
-              const uint32_t acc = (u > 0 || p > 0 || kk > 0) ? 1u : 0u;
-              const uint64_t ad = sdesc(a0 + kk * 32);
-              umma(tmem + 64 * p, ad, sdesc(b0 + kk * 32), id0, acc);
-              if (nq1 > 0) umma(tmem + 64 * (p + 4), ad, sdesc(b0 + 4 * BQ_BYTES + kk * 32), id1, acc);
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                // the first MMAs of a pass (digit 0 of the first K block) start its four groups
+                const uint32_t acc = (u > 0 || p > 0 || kk > 0) ? 1u : 0u;
+                umma(tmem + col, sdesc(a0 + kk * 32), sdesc(b0 + q0 * BQ_BYTES + kk * 32), id, acc);
+              }
+              umma_commit(&emptyA[s]);
+              ++na;
             }
-            umma_commit(&emptyA[s]);
-            ++na;
+            umma_commit(&emptyB[sb]);
+            ++nbq;
           }
-          umma_commit(&emptyB[sb]);
-          ++nbq;
+          umma_commit(&tfull[pass]);  // arrives when every MMA of this half has completed
         }
-        umma_commit(tfull);  // arrives when every MMA of this tile has completed
         ++it;
       }
       if (!ok) atomicExch(failed, 1);
     }
   } else {
     // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w mod 4) ..
-    // (one row of the tile per thread) and one quarter of the columns; it
-    // combines the eight groups four columns at a time and writes each row's
-    // 16 entries (128 contiguous bytes per thread).  Cin is read after TMEM
-    // has been handed back, under the next tile's MMAs.
+    // (one row of the tile per thread) and one quarter of the columns.  It
+    // reads groups 0-3 once the first pass is done (while the second runs),
+    // keeps their Horner pairs and hands that half back; then groups 4-7
+    // once the second pass is done (while the next tile's first pass runs),
+    // combines and rounds, hands the second half back, and reads Cin and
+    // writes each row's 16 entries (128 contiguous bytes per thread) under
+    // the next tile's MMAs.
     const int q = warp & 3, c0 = 16 * ((warp - 2) >> 2);
     const bool neg_alpha = P.alpha < 0.0;  // alpha is +-1 and beta 0 or 1 (checked at launch)
     const bool use_cin = P.beta != 0.0;
@@ -389,73 +421,105 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(crow));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + 15));
       }
-      const bool ok = mbar_wait(tfull, (uint32_t)it & 1u);
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      double* orow = pr.out + (int64_t)grow * pr.ldo;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(pr.out) | (uintptr_t)(pr.ldo * 8)) & 15u) == 0;
+      const bool live = col0 < pr.n;  // else columns past this problem (narrow updates): nothing to read
+      // Group sums within 2^22 in magnitude - always for K <= 128
+      // (8 * 128 * 2^12), and for longer K whenever the warp's 16 sums of a
+      // read are (checked) - become integers by an FP32 add: adding
+      // 1.5 * 2^23 gives an FP32 in [2^23, 2^24] whose bit pattern less that
+      // of 1.5 * 2^23 is the integer (at 2^24 the difference is still exactly
+      // 2^22).  Otherwise (K up to 512: up to 2^24) a float-to-integer
+      // conversion each.  A read: four groups (one half) of four columns, four
+      // TMEM loads and a wait that names the loaded registers.
+      uint32_t acc[4][4];
+      auto read_half = [&](int half, int cq) -> bool {
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg) tmem_ld4_async(trow + 64 * (4 * half + gg) + c0 + cq, acc[gg]);
+        tmem_wait_regs(acc);
+        if (small_k) return true;
+        float mx = 0.0f;
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) mx = fmaxf(mx, fabsf(__uint_as_float(acc[gg][u])));
+        return __all_sync(0xffffffffu, mx <= 4194304.0f);
+      };
+      // the Horner pairs of one half: x0 = G_0 128 + G_1, x1 = G_2 128 + G_3
+      // of its four groups, for column u of the read
+      auto pairs = [&](bool fast, int u, int& x0, int& x1) {
+        int a[4];
+#pragma unroll
+        for (int gg = 0; gg < 4; ++gg)
+          a[gg] = fast ? __float_as_int(__uint_as_float(acc[gg][u]) + 12582912.0f) - 0x4B400000
+                       : __float2int_rn(__uint_as_float(acc[gg][u]));
+        x0 = a[0] * 128 + a[1];
+        x1 = a[2] * 128 + a[3];
+      };
+      // ---- groups 0-3 (the first pass), kept as their Horner pairs
+      bool ok = mbar_wait(&tfull[0], (uint32_t)it & 1u);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok || *(volatile int*)failed) {
         if (lane == 0 && P.err) atomicExch(P.err, 1);
         atomicExch(failed, 1);
         break;
       }
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-      double* orow = pr.out + (int64_t)grow * pr.ldo;
-      const bool vec_ok = ((reinterpret_cast<uintptr_t>(pr.out) | (uintptr_t)(pr.ldo * 8)) & 15u) == 0;
-      if (col0 >= pr.n) {  // columns past this problem (narrow updates): nothing to read
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty);
-      } else {
-        // Four columns at a time: eight TMEM loads, then a wait that names
-        // the loaded registers (so nothing reads them early).  The combined
-        // products stay in registers; TMEM is released as soon as the last
-        // columns are read, so the Schur update's add and the stores run
-        // under the next tile's MMAs.
-        double vout[16];
-        uint32_t acc[ND][4];
+      // per column one 64-bit word: the first half's Horner pairs, then (in
+      // the second half) the bits of the combined product
+      unsigned long long hv[16];
+      if (live) {
 #pragma unroll
         for (int cq = 0; cq < 16; cq += 4) {
+          const bool fast = read_half(0, cq);
 #pragma unroll
-          for (int gg = 0; gg < ND; ++gg) tmem_ld4_async(trow + 64 * gg + c0 + cq, acc[gg]);
-          tmem_wait_regs(acc);
-          // Group sums within 2^22 in magnitude - always for K <= 128
-          // (8 * 128 * 2^12), and for longer K whenever the warp's 32 sums of
-          // these four columns are (checked) - become integers by an FP32 add:
-          // adding 1.5 * 2^23 gives an FP32 in [2^23, 2^24] whose bit pattern
-          // less that of 1.5 * 2^23 is the integer (at 2^24 the difference is
-          // still exactly 2^22).  Otherwise (K up to 512: up to 2^24) a
-          // float-to-integer conversion each.
-          bool fast = small_k;
-          if (!fast) {
-            float mx = 0.0f;
-#pragma unroll
-            for (int gg = 0; gg < ND; ++gg)
-#pragma unroll
-              for (int u = 0; u < 4; ++u) mx = fmaxf(mx, fabsf(__uint_as_float(acc[gg][u])));
-            fast = __all_sync(0xffffffffu, mx <= 4194304.0f);
+          for (int u = 0; u < 4; ++u) {
+            int x0, x1;
+            pairs(fast, u, x0, x1);
+            hv[cq + u] = ((unsigned long long)(uint32_t)x0 << 32) | (uint32_t)x1;
           }
+        }
+      }
+      // this half has been read: the MMA warp may start the next tile's first pass
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[0]);
+      // ---- groups 4-7 (the second pass), combined with the first half
+      ok = mbar_wait(&tfull[1], (uint32_t)it & 1u);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok || *(volatile int*)failed) {
+        if (lane == 0 && P.err) atomicExch(P.err, 1);
+        atomicExch(failed, 1);
+        break;
+      }
+      if (!live) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[1]);
+      } else {
+        // The combined products stay in registers; TMEM is released as soon
+        // as the last columns are read, so the Schur update's add and the
+        // stores run under the next tile's MMAs.
+#pragma unroll
+        for (int cq = 0; cq < 16; cq += 4) {
+          const bool fast = read_half(1, cq);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int c = cq + u;
             const int fj = __shfl_sync(0xffffffffu, fcol, c);
-            if (ei >= kNonFinite || fj >= kNonFinite) {
-              vout[c] = __longlong_as_double(0x7FF8000000000000LL);
-            } else {
-              int a[ND];
-              if (fast) {
-#pragma unroll
-                for (int gg = 0; gg < ND; ++gg)
-                  a[gg] = __float_as_int(__uint_as_float(acc[gg][u]) + 12582912.0f) - 0x4B400000;
-              } else {
-#pragma unroll
-                for (int gg = 0; gg < ND; ++gg) a[gg] = __float2int_rn(__uint_as_float(acc[gg][u]));
-              }
-              vout[c] = combine(a, ei + fj - 61, neg_alpha);
-            }
+            int l0, l1;
+            pairs(fast, u, l0, l1);
+            const double v = (ei >= kNonFinite || fj >= kNonFinite)
+                                 ? __longlong_as_double(0x7FF8000000000000LL)
+                                 : combine((int)(hv[c] >> 32), (int)(uint32_t)hv[c], l0, l1, ei + fj - 61, neg_alpha);
+            hv[c] = (unsigned long long)__double_as_longlong(v);
           }
         }
         // every accumulator of this tile has been read: the MMA warp may
-        // start the next tile
+        // start the next tile's second pass
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty);
+        if (lane == 0) mbar_arrive(&tempty[1]);
         // the addends (from L2), the one FP64 instruction per entry - the
         // Schur update's add - and the stores: two columns per 16-byte access
         // where both are used (col is even; rows start on 16 bytes when the
@@ -475,7 +539,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int cq = 0; cq < 16; cq += 2) {
           const int col = col0 + cq;
-          const double v0 = cpre[cq] + vout[cq], v1 = cpre[cq + 1] + vout[cq + 1];
+          const double v0 = cpre[cq] + __longlong_as_double((long long)hv[cq]),
+                       v1 = cpre[cq + 1] + __longlong_as_double((long long)hv[cq + 1]);
           const bool w0 = row_ok && col < pr.n && (col < pr.skip_c0 || col >= pr.skip_c1);
           const bool w1 = row_ok && col + 1 < pr.n && (col + 1 < pr.skip_c0 || col + 1 >= pr.skip_c1);
           if (w0 && w1 && vec_ok) {
@@ -676,7 +741,7 @@ cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, c
   if (((uintptr_t)apk | (uintptr_t)bpk) & 15) return cudaErrorInvalidValue;
   CUtensorMap ta, tb;
   if (!make_map(&ta, apk, P.kpad, a_rows_pad, a_slabs * ND, BM, BK, 1)) return cudaErrorInvalidValue;
-  if (!make_map(&tb, bpk, P.kpad, b_rows_pad, b_slabs * ND, BN, BK, ND)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, bpk, P.kpad, b_rows_pad, b_slabs * ND, BN, BK, 4)) return cudaErrorInvalidValue;
   const size_t sm = smem_bytes();
   {
     cudaError_t e = once_per_device((const void*)oz_gemm_kernel, [sm] {

@@ -140,6 +140,16 @@ __device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[8][2]) {
                : "memory");
 }
 
+// The same for four columns of four groups (16 registers).
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[4][4]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
+                 "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
+                 "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3])
+               :
+               : "memory");
+}
+
 // The same for four columns of eight groups (32 registers).
 __device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[8][4]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
