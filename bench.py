@@ -37,14 +37,14 @@ PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
 # flop), from profiles/oz_gemm_kernel_trailing_update_b512_x300.md: the four
 # products of the first panel pair of 300 matrices of order 512 (two cross
 # products, the second panel's done rows, the K = 128 trailing update) read
-# and wrote 1.970 GB for the two panels' update work.
-UPDATE_DRAM_BYTES_PER_FLOP = 1.969520384e9 / (300 * (2 * 2 * 512 * 64 * 448 + 2 * 64 ** 3))
+# and wrote 1.972 GB for the two panels' update work.
+UPDATE_DRAM_BYTES_PER_FLOP = 1.971966464e9 / (300 * (2 * 2 * 512 * 64 * 448 + 2 * 64 ** 3))
 # The same for the FP64_TC Schur products, from
 # profiles/oz_gemm_kernel_schur_products_n512_x200.md: one grouped launch of
-# 200 independent products of order 512 (42 waves) read and wrote 2.509 GB -
+# 200 independent products of order 512 (42 waves) read and wrote 2.539 GB -
 # the algorithmic bytes of its operands; an upper bound for the recursion's
 # launches, whose products share operands.
-SCHUR_DRAM_BYTES_PER_FLOP = (2.106525440e9 + 0.402201344e9) / (200 * 2 * 512 ** 3)
+SCHUR_DRAM_BYTES_PER_FLOP = (2.136734720e9 + 0.402228224e9) / (200 * 2 * 512 ** 3)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
 
