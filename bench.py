@@ -29,21 +29,22 @@ if ROOT not in sys.path:
 METRIC = "inverse blocks/sec & GEMM % of tensor peak, mixed vs FP64 at ≤1e-10 rel err"
 FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (DFMA / FP64 tensor), nominal
 # DRAM bytes per algorithmic flop of the FP64_TC panel factorisation, from one
-# ncu capture (profiles/gj_panel_kernel_fp64tc_b512_x300.md: a launch of 300
-# panels of 512 rows x 64 columns read and wrote 99.4 MB for 1.258 GFLOP).
-# With 64 columns a panel's flops and its row traffic both grow with its rows.
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the first panel
+# launch of `bench.py --inverses 300 --n 512`: 300 panels of 512 rows x 64
+# columns read and wrote 99.4 MB for 1.258 GFLOP).  With 64 columns a panel's
+# flops and its row traffic both grow with its rows.
 PANEL_DRAM_BYTES_PER_FLOP = 99.43e6 / (300 * 2 * 512 * 64 * 64)
 # The same for the FP64_TC pivot inverses' digit products (per FP64-equivalent
-# flop), from profiles/oz_gemm_kernel_trailing_update_b512_x300.md: the four
+# flop), from the first four oz_gemm_kernel launches of the same command: the
 # products of the first panel pair of 300 matrices of order 512 (two cross
 # products, the second panel's done rows, the K = 128 trailing update) read
 # and wrote 1.972 GB for the two panels' update work.
 UPDATE_DRAM_BYTES_PER_FLOP = 1.971966464e9 / (300 * (2 * 2 * 512 * 64 * 448 + 2 * 64 ** 3))
-# The same for the FP64_TC Schur products, from
-# profiles/oz_gemm_kernel_schur_products_n512_x200.md: one grouped launch of
-# 200 independent products of order 512 (42 waves) read and wrote 2.539 GB -
-# the algorithmic bytes of its operands; an upper bound for the recursion's
-# launches, whose products share operands.
+# The same for the FP64_TC Schur products, from the product launch of
+# `bench.py --products 200 --n 512`: one grouped launch of 200 independent
+# products of order 512 (42 waves) read and wrote 2.539 GB - the algorithmic
+# bytes of its operands; an upper bound for the recursion's launches, whose
+# products share operands.
 SCHUR_DRAM_BYTES_PER_FLOP = (2.136734720e9 + 0.402228224e9) / (200 * 2 * 512 ** 3)
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070  # SMs x FP32 lanes x 2 flop x max GHz
 DIGIT_PAIRS = 36  # BF16 digit-pair products per FP64 product on the fp64_tc path
