@@ -533,7 +533,9 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   // eliminations: measured 18% less panel time than one 135 KB CTA per SM)
   // (m rows eliminated per matrix: b, or with tensor-core updates only the
   // b - p rows not yet used as pivots, so later panels take smaller clusters)
-  // a tuned bias (mbinv_autotune) scales the heuristic's choice by 2^bias
+  // a tuned bias (mbinv_autotune) scales the heuristic's choice by 2^bias, up
+  // to clusters of 16 CTAs (non-portable; only where the device can co-schedule
+  // one, checked per launch) for the small, latency-bound batches
   const int bias = cluster_bias(b, count, sizeof(TW) == 8 ? F64 : F32, tc != nullptr);
   auto cluster_for = [&](int m) {
     int CL = 8;
@@ -542,7 +544,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     while (CL > 1 && count * (CL / 2) >= 152 && (m + CL / 2 - 1) / (CL / 2) * (nb + 1) * sizeof(TW) <= 64 * 1024)
       CL >>= 1;
     while (CL < 8 && ((size_t)((m + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > 72 * 1024) CL <<= 1;
-    for (int t = 0; t < bias && CL < 8; ++t) CL <<= 1;
+    for (int t = 0; t < bias && CL < 16; ++t) CL <<= 1;
     for (int t = 0; t < -bias && CL > 1; ++t) CL >>= 1;
     while (CL < 8 && ((size_t)((m + CL - 1) / CL) + 4) * (nb + 1) * sizeof(TW) > (size_t)kSmemLimit) CL <<= 1;
     return CL;
@@ -553,7 +555,9 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   }
   {
     cudaError_t e = once_per_device((const void*)gj_panel_kernel<TW>, [] {
-      return cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+      cudaError_t e2 = cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+      if (e2 != cudaSuccess) return e2;
+      return cudaFuncSetAttribute(gj_panel_kernel<TW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     });
     if (e != cudaSuccess) return e;
   }
@@ -561,19 +565,31 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
   auto panel = [&](int pp) -> cudaError_t {
     const int w = std::min(nb, b - pp);  // widest panel of this step (b is the largest order)
     const int m = tc && w < b ? b - pp : b;
-    const int CL = cluster_for(m);
+    int CL = cluster_for(m);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(count * CL, 1, 1);
-    cfg.blockDim = dim3(kPanelThreads, 1, 1);
-    cfg.dynamicSmemBytes = ((size_t)((m + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
-    cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    auto configure = [&]() {
+      cfg.gridDim = dim3(count * CL, 1, 1);
+      cfg.blockDim = dim3(kPanelThreads, 1, 1);
+      cfg.dynamicSmemBytes = ((size_t)((m + CL - 1) / CL) + 4) * (w + 1) * sizeof(TW);
+      cfg.stream = s;
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+    };
+    configure();
+    if (CL > 8) {
+      // a non-portable cluster: only if one can be resident at all
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, gj_panel_kernel<TW>, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();  // the query's error is not the call's
+        CL = 8;
+        configure();
+      }
+    }
     const bool timed = tm && tm->n + 2 <= tm->cap;
     if (timed) cudaEventRecord(tm->ev[tm->n], s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, gj_panel_kernel<TW>, d_desc, pp, w, d_status, tc && w < b ? 1 : 0);
