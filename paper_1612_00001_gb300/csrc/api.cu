@@ -709,10 +709,9 @@ mbinv_status oz_list(mbinv_ctx* c, const std::vector<OzOp>& ops, int k, double a
   char* d = (char*)c->gemmdesc.p;
   CU(cudaMemcpyAsync(d, h.data(), h.size(), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemsetAsync(E.tcerr.p, 0, sizeof(int), c->stream));
-  CU(oz::launch_pack((const oz::PackDesc*)(d + oa), (int)pa.size(), rpa, kpad, (__nv_bfloat16*)E.apk.p, ea,
-                     c->stream));
-  CU(oz::launch_pack((const oz::PackDesc*)(d + ob), (int)pb.size(), rpb, kpad, (__nv_bfloat16*)E.bpk.p, eb,
-                     c->stream));
+  CU(oz::launch_pack2(oz::PackSet{(const oz::PackDesc*)(d + oa), (int)pa.size(), rpa, (__nv_bfloat16*)E.apk.p, ea},
+                      oz::PackSet{(const oz::PackDesc*)(d + ob), (int)pb.size(), rpb, (__nv_bfloat16*)E.bpk.p, eb},
+                      kpad, c->stream));
   oz::Params Q{};
   Q.kpad = kpad;
   Q.tiles_m = rpa / oz::tile_m();

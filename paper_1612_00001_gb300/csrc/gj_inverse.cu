@@ -634,9 +634,8 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
     Q.coprime_grid = 1;  // the skipped panel columns recur every tiles_n tiles
     // one grouped digit product over K = kpad (a multiple of 64, at most T.kpad)
     auto product = [&](int kpad, double alpha, double beta, int tiles_m, int tiles_n) -> cudaError_t {
-      cudaError_t e2 = oz::launch_pack(pa, count, T.rpa, kpad, da, ea, s);
-      if (e2 != cudaSuccess) return e2;
-      e2 = oz::launch_pack(pb, count, T.rpb, kpad, db, eb, s);
+      cudaError_t e2 = oz::launch_pack2(oz::PackSet{pa, count, T.rpa, da, ea}, oz::PackSet{pb, count, T.rpb, db, eb},
+                                        kpad, s);
       if (e2 != cudaSuccess) return e2;
       Q.kpad = kpad;
       Q.nkb = kpad / oz::tile_k();
@@ -644,7 +643,7 @@ cudaError_t run_batch_t(int in_dtype, int out_dtype, const InvDesc* d_desc, int 
       Q.beta = beta;
       Q.tiles_m = tiles_m;
       Q.tiles_n = tiles_n;
-      nl += 3;
+      nl += 2;
       return oz::launch_gemm(da, count, T.rpa, db, count, T.rpb, Q, pr, count, s);
     };
     auto kround = [](int x) { return (x + oz::tile_k() - 1) / oz::tile_k() * oz::tile_k(); };

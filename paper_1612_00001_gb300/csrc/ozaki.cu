@@ -569,13 +569,20 @@ __global__ void __launch_bounds__(THREADS, 1)
 // (the bit patterns of |x| order like the values; Inf and NaN sort above every
 // finite value), pass 2 writes the digits, four BF16 per lane and digit
 // (256 contiguous bytes per warp instruction; two for chunks of 64 entries).
-__global__ void __launch_bounds__(256, 4) oz_pack_kernel(const PackDesc* __restrict__ descs, int rows_pad, int kpad,
-                                                       int rpc, __nv_bfloat16* __restrict__ dst, int* __restrict__ exps) {
+__global__ void __launch_bounds__(256, 4) oz_pack_kernel(const PackSet s0, const PackSet s1, int kpad, int rpc) {
   extern __shared__ double S[];  // [rpc][kc + 1]
   __shared__ int sE[PMAXR];
   __shared__ unsigned smx[PMAXR];  // running row maxima (high words of the bit patterns)
-  const PackDesc d = descs[blockIdx.y];
+  // grid rows [0, s0.count) pack the slabs of the first set, the others those
+  // of the second (two operands of one product in one launch)
+  const bool second = (int)blockIdx.y >= s0.count;
+  const PackSet ps = second ? s1 : s0;
+  const int rows_pad = ps.rows_pad;
+  __nv_bfloat16* __restrict__ dst = ps.dst;
+  int* __restrict__ exps = ps.exps;
+  const PackDesc d = ps.descs[second ? (int)blockIdx.y - s0.count : (int)blockIdx.y];
   const int r0 = blockIdx.x * rpc;
+  if (r0 >= rows_pad) return;  // the grid covers the set with more slab rows
   const int rw = rpc / 8;  // rows per warp
   const int R = d.transpose ? d.cols : d.rows, KD = d.transpose ? d.rows : d.cols;
   // slab rows past the last 128-row tile that holds a source row are never
@@ -707,10 +714,12 @@ int tile_k() { return BK; }
 int pack_rows() { return PR; }
 size_t smem_bytes() { return 2 * B_BYTES + ASTAGES * A_BYTES + 1024 + 256; }
 
-cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kpad, __nv_bfloat16* dst, int* exps,
-                        cudaStream_t s) {
+cudaError_t launch_pack2(const PackSet& a, const PackSet& b, int kpad, cudaStream_t s) {
+  const int count = (a.count > 0 ? a.count : 0) + (b.count > 0 ? b.count : 0);
   if (count <= 0) return cudaSuccess;
-  if (rows_pad % PR || kpad % BK || ((uintptr_t)dst & 3)) return cudaErrorInvalidValue;
+  for (const PackSet* p : {&a, &b})
+    if (p->count > 0 && (p->rows_pad % PR || ((uintptr_t)p->dst & 3))) return cudaErrorInvalidValue;
+  if (kpad % BK) return cudaErrorInvalidValue;
   {
     // the largest stage: 64 rows x 129 or 16 rows x 513 entries, about 66 KB
     cudaError_t e = once_per_device((const void*)oz_pack_kernel, [] {
@@ -718,16 +727,25 @@ cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kp
     });
     if (e != cudaSuccess) return e;
   }
+  const PackSet s0 = a.count > 0 ? a : b;
+  PackSet s1 = a.count > 0 ? b : PackSet{};
+  if (s1.count < 0) s1.count = 0;
   const int kc = kpad < PKC ? kpad : PKC;
   // rows per CTA: about 33 KB of staged entries, 8..64 rows (rows_pad is a
   // multiple of 64), so that four CTAs share an SM
   int rpc = (PR / 2) * (PKC / kc);
   rpc = rpc > PMAXR ? PMAXR : rpc;
-  if (rows_pad % rpc) rpc = PR;
+  if (s0.rows_pad % rpc || (s1.count > 0 && s1.rows_pad % rpc)) rpc = PR;
   if ((size_t)rpc * (kc + 1) * sizeof(double) > (size_t)kPackSmemMax) return cudaErrorInvalidValue;
-  dim3 grid(rows_pad / rpc, count);
-  oz_pack_kernel<<<grid, 256, rpc * (kc + 1) * sizeof(double), s>>>(d_descs, rows_pad, kpad, rpc, dst, exps);
+  const int rows = s1.count > 0 && s1.rows_pad > s0.rows_pad ? s1.rows_pad : s0.rows_pad;
+  dim3 grid(rows / rpc, s0.count + s1.count);
+  oz_pack_kernel<<<grid, 256, rpc * (kc + 1) * sizeof(double), s>>>(s0, s1, kpad, rpc);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kpad, __nv_bfloat16* dst, int* exps,
+                        cudaStream_t s) {
+  return launch_pack2(PackSet{d_descs, count, rows_pad, dst, exps}, PackSet{}, kpad, s);
 }
 
 cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, const __nv_bfloat16* bpk, int b_slabs,

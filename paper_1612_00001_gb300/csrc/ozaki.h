@@ -76,6 +76,18 @@ size_t smem_bytes();
 // Rows and columns beyond the source are written as zeros.
 cudaError_t launch_pack(const PackDesc* d_descs, int count, int rows_pad, int kpad, __nv_bfloat16* dst, int* exps,
                         cudaStream_t s);
+
+// One set of slabs to pack (the arguments of launch_pack).
+struct PackSet {
+  const PackDesc* descs;
+  int count;
+  int rows_pad;
+  __nv_bfloat16* dst;
+  int* exps;
+};
+// Two sets of the same inner length kpad (the two operands of one product)
+// in one launch; a set with count 0 is skipped.
+cudaError_t launch_pack2(const PackSet& a, const PackSet& b, int kpad, cudaStream_t s);
 // a_rows_pad is a multiple of tile_m(), b_rows_pad of tile_n().
 cudaError_t launch_gemm(const __nv_bfloat16* apk, int a_slabs, int a_rows_pad, const __nv_bfloat16* bpk, int b_slabs,
                         int b_rows_pad, const Params& P, const Problem* d_probs, int count, cudaStream_t s);
