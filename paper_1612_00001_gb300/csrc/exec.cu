@@ -819,6 +819,22 @@ mbinv_status run_jobs(Env& E, const std::vector<Job>& jobs) {
           ++E.gemm_launches;
           break;
         case Launch::OZPACK:
+          if (q + 1 < L.size() && L[q + 1].kind == Launch::OZPACK && L[q + 1].kpad == l.kpad) {
+            // two adjacent packs (the two operands of a product) in one launch
+            const Launch& l2 = L[q + 1];
+            CUE(oz::launch_pack2(oz::PackSet{(const oz::PackDesc*)(dbase + l.off), l.count, l.rows_pad, l.dst, l.exps},
+                                 oz::PackSet{(const oz::PackDesc*)(dbase + l2.off), l2.count, l2.rows_pad, l2.dst,
+                                             l2.exps},
+                                 l.kpad, E.stream));
+            ++E.launches;
+            if (E.profile) {
+              // the second pack's time is inside the first's interval
+              CUE(cudaEventRecord(E.events[2 * q + 1], E.stream));
+              CUE(cudaEventRecord(E.events[2 * q + 2], E.stream));
+            }
+            ++q;
+            break;
+          }
           CUE(oz::launch_pack((const oz::PackDesc*)(dbase + l.off), l.count, l.rows_pad, l.kpad, l.dst, l.exps,
                               E.stream));
           ++E.launches;
