@@ -730,6 +730,11 @@ cudaError_t launch_pack2(const PackSet& a, const PackSet& b, int kpad, cudaStrea
   const PackSet s0 = a.count > 0 ? a : b;
   PackSet s1 = a.count > 0 ? b : PackSet{};
   if (s1.count < 0) s1.count = 0;
+  if (s0.count + s1.count > 65535 && s1.count > 0) {
+    // beyond the grid's y extent together: one launch each
+    cudaError_t e = launch_pack2(s0, PackSet{}, kpad, s);
+    return e != cudaSuccess ? e : launch_pack2(s1, PackSet{}, kpad, s);
+  }
   const int kc = kpad < PKC ? kpad : PKC;
   // rows per CTA: about 33 KB of staged entries, 8..64 rows (rows_pad is a
   // multiple of 64), so that four CTAs share an SM
