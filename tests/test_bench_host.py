@@ -97,3 +97,14 @@ def test_reference_arm_line():
     assert d["higher_is_better"] is True and d["value"] > 0 and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "blocks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_single_thread():
+    """`--cpu-threads 1` runs the oracle on one host thread and says so."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "256", "--k",
+                          "4", "--steps", "1", "--warmup", "0", "--cpu-threads", "1"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT, check=True).stdout
+    d = json.loads([l for l in out.splitlines() if l.startswith("{")][0])
+    assert d["cpu_baseline"]["cores"] == 1 and d["value"] > 0
