@@ -110,3 +110,15 @@ def test_binding_structs_match_header(cname, pyname):
             want = want * count
         assert ctypes.sizeof(ftype) == ctypes.sizeof(want) and getattr(ftype, "_type_", None) == getattr(
             want, "_type_", None), (cname, fname, ftype, htype)
+
+
+def test_product_library_exports_no_test_hooks(libpath):
+    """The C-ABI symbols of libmbinv.so are the header's entry points; the
+    test hooks live in libmbinv_test.so beside it."""
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.split() and l.split()[-1].startswith("mbinv_")}
+    assert exported == set(declared()), sorted(exported ^ set(declared()))
+    test_lib = os.path.join(os.path.dirname(libpath), "libmbinv_test.so")
+    hooks = subprocess.run(["nm", "-D", "--defined-only", test_lib], capture_output=True, text=True,
+                           check=True).stdout
+    assert "mbinv_debug_oz_gemm" in hooks
